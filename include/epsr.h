@@ -1,0 +1,258 @@
+/*
+ * epsr.h -- C ABI of libepsr, the GB300 (sm_103a) implementation of the data-parallel
+ * hot path of empirical potential structure refinement (EPSR) as described in
+ * NeuDATool (arXiv:1904.08756):
+ *
+ *   - Metropolis Monte Carlo moves of molecules or atoms, each decided by the energy
+ *     change dU of the moved molecule against all atoms of a periodic box
+ *     (Sec. 2.2 item III, Sec. 2.3);
+ *   - the all-pair partial histograms N_ab(r) and the pair distribution functions
+ *     g_ab(r) (Sec. 2.3);
+ *   - the structure factor S(Q) of Eq. (1), the weighted sine transform of g_ab(r);
+ *   - the empirical-potential update from Delta S(Q) with a Poisson basis (Sec. 2.1,
+ *     Eq. 2).
+ *
+ * Conventions (apply to every call):
+ *   - Every function returns an int status (EPSR_OK on success). No C++ exception
+ *     crosses this boundary. epsr_strerror() names a status; epsr_last_error_detail()
+ *     copies a one-line description of the last failure on the calling host thread.
+ *   - Work is enqueued on the caller's CUDA stream (`stream`, NULL = legacy default
+ *     stream) and is asynchronous unless a function says it synchronises.
+ *   - Device pointers are caller-owned device memory (for example torch tensors);
+ *     host pointers are ordinary host memory. The library owns the opaque handles and
+ *     the device memory behind them.
+ *   - Coordinates are integers on a grid of 2^-scale_log2 Angstrom (scale_log2 = 20
+ *     in all shipped workloads), in [0, L_fx) for a cubic box of side L_fx grid units.
+ *     Squared distances are exact 64-bit integers, so histogram bins are exact.
+ *   - Units: Angstrom, kJ/mol, elementary charge, fm (scattering lengths), K, 1/A (Q).
+ *     S(Q) is in barn per steradian per atom.
+ *   - A handle must not be used from two streams at the same time.
+ */
+#ifndef EPSR_H
+#define EPSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *epsr_stream_t; /* same object as cudaStream_t */
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define EPSR_OK 0
+#define EPSR_EINVAL 1   /* an argument is out of range or inconsistent */
+#define EPSR_ENOMEM 2   /* a device or host allocation failed */
+#define EPSR_ECUDA 3    /* a CUDA runtime call failed */
+#define EPSR_ELAUNCH 4  /* the persistent kernel's CTAs cannot all be resident at once */
+#define EPSR_ETIMEOUT 5 /* a device-side wait gave up (the kernel exited cleanly) */
+#define EPSR_ENUMERIC 6 /* a non-finite energy or structure factor was produced */
+
+#define EPSR_MAX_TYPES 8       /* atom types per box */
+#define EPSR_MAX_MOL_ATOMS 8   /* atoms per molecule moved as a rigid body */
+#define EPSR_MAX_BINS 4096     /* histogram bins per pair */
+#define EPSR_SQ_MAX_COLS 512   /* partial g(r) columns in one S(Q) call */
+
+#define EPSR_MOVE_ATOM 0            /* translate one atom (single-atom molecules) */
+#define EPSR_MOVE_RIGID_MOLECULE 1  /* rotate then translate one rigid molecule */
+
+#define EPSR_SQ_FP32 0    /* CUDA-core FP32 contraction */
+#define EPSR_SQ_TF32X3 1  /* tensor cores (tcgen05), TF32 hi/lo split, 3 products */
+#define EPSR_SQ_BF16X3 2  /* tensor cores (tcgen05), BF16 hi/lo split, 3 products */
+#define EPSR_SQ_BF16X6 3  /* tensor cores (tcgen05), BF16 three-way split, 6 products */
+
+/* ---- box description ------------------------------------------------------------------
+ * One periodic cubic box. Force field (Sec. 2.1 reference potential; the paper names
+ * MD force fields only, this library takes): Lennard-Jones 12-6 with Lorentz-Berthelot
+ * mixing over every minimum-image pair, plus Coulomb k_e q_a q_b / r for
+ * r < r_coul (plain truncation, k_e from SI constants), plus the empirical potential
+ * table (per type pair, piecewise constant on the histogram bins, zero beyond).
+ * Bins have width bin_p / bin_q Angstrom (an exact rational) and there are n_bins.  */
+typedef struct {
+    int64_t n_atoms;
+    int64_t n_mol;            /* molecules are contiguous atom ranges (mol_start) */
+    int64_t L_fx;             /* box side in grid units, < 2^31 */
+    int32_t scale_log2;       /* grid is 2^-scale_log2 Angstrom; 10 .. 24 */
+    int32_t n_types;          /* 1 .. EPSR_MAX_TYPES */
+    double q[EPSR_MAX_TYPES];      /* charge per type (e) */
+    double sigma[EPSR_MAX_TYPES];  /* LJ sigma per type (A) */
+    double eps[EPSR_MAX_TYPES];    /* LJ epsilon per type (kJ/mol); 0 = no LJ */
+    double b[EPSR_MAX_TYPES];      /* coherent scattering length per type (fm) */
+    double r_coul;            /* Coulomb cutoff (A) */
+    int32_t bin_p, bin_q;     /* bin width = bin_p / bin_q Angstrom */
+    int32_t n_bins;           /* 1 .. EPSR_MAX_BINS */
+    int32_t move_kind;        /* EPSR_MOVE_ATOM or EPSR_MOVE_RIGID_MOLECULE */
+    double temperature;       /* K */
+    double max_translation;   /* A, per axis */
+    double max_rotation_deg;  /* rigid-molecule rotation limit */
+} epsr_box_desc;
+
+typedef struct epsr_box epsr_box;   /* opaque: one box or a batch of boxes */
+
+/* Running Monte Carlo statistics of one box, accumulated over every sweep since the
+ * box was created. */
+typedef struct {
+    int64_t attempted;
+    int64_t accepted;
+    int64_t nonfinite;   /* moves whose dU was not finite (rejected) */
+    double sum_dU;       /* sum of accepted dU (kJ/mol), FP64 */
+} epsr_mc_stats;
+
+/* One logged move (for replay against an independent implementation). */
+typedef struct {
+    int32_t mol;         /* moved molecule (index within its box) */
+    int32_t accepted;
+    float dU;            /* the FP32 energy change that decided the move */
+    int32_t n_atoms;     /* atoms of the molecule (rows of trial used) */
+    double u_acc;        /* the uniform variate of the Metropolis test */
+    int32_t trial[EPSR_MAX_MOL_ATOMS][3];  /* trial grid coordinates */
+    int32_t pad[2];
+} epsr_move_log;         /* 128 bytes */
+
+/* ---- errors ------------------------------------------------------------------------- */
+const char *epsr_strerror(int status);
+/* Copies the last failure message of this host thread into buf (NUL-terminated,
+ * truncated to len). Returns the status of that failure (EPSR_OK if none). */
+int epsr_last_error_detail(char *buf, size_t len);
+int epsr_version(void);   /* major * 10000 + minor * 100 + patch */
+
+/* ---- boxes ---------------------------------------------------------------------------
+ * epsr_box_create: one box. Host inputs are copied (the caller keeps ownership):
+ *   xyz       int32 [n_atoms][3] grid coordinates in [0, L_fx)
+ *   type      int32 [n_atoms], 0 .. n_types-1
+ *   mol_start int64 [n_mol+1], mol_start[0] = 0, strictly increasing,
+ *             mol_start[n_mol] = n_atoms; with EPSR_MOVE_RIGID_MOLECULE each molecule
+ *             has at most EPSR_MAX_MOL_ATOMS atoms, with EPSR_MOVE_ATOM exactly one.
+ * Builds the exact bin-threshold table, the pair-parameter table and a zero empirical
+ * potential. Synchronises `stream` before returning. Errors: EINVAL (any inconsistent
+ * field or array), ENOMEM, ECUDA.
+ *
+ * epsr_batch_create: n_boxes independent boxes (replicas) advanced together by one
+ * persistent kernel. descs[n_boxes]; xyz and type concatenated over the boxes in
+ * order; mol_start concatenated as n_boxes arrays of n_mol_b+1 entries, each starting
+ * at 0 (box-local atom indices).                                                       */
+int epsr_box_create(const epsr_box_desc *desc, const int32_t *xyz, const int32_t *type,
+                    const int64_t *mol_start, epsr_stream_t stream, epsr_box **out);
+int epsr_batch_create(const epsr_box_desc *descs, int32_t n_boxes, const int32_t *xyz,
+                      const int32_t *type, const int64_t *mol_start, epsr_stream_t stream,
+                      epsr_box **out);
+/* Frees the handle and its device memory (synchronises the device). NULL is a no-op. */
+int epsr_box_destroy(epsr_box *box);
+
+/* Sizes: number of boxes, total atoms, and the length in elements of the histogram
+ * buffer epsr_partial_gr expects (sum over boxes of n_pairs_b * n_bins_b). Any output
+ * pointer may be NULL. Host only, no CUDA call. */
+int epsr_box_info(const epsr_box *box, int32_t *n_boxes, int64_t *n_atoms_total,
+                  int64_t *hist_len);
+/* Offset (elements) of box b's block in the histogram / g buffers, and of its first
+ * atom in the coordinate arrays. Host only. */
+int epsr_box_offsets(const epsr_box *box, int32_t b, int64_t *hist_offset, int64_t *atom_offset);
+
+/* Copies the current coordinates to host int32 [n_atoms_total][3] (synchronises). */
+int epsr_box_get_coords(epsr_box *box, int32_t *xyz, epsr_stream_t stream);
+/* Replaces the coordinates from host int32 [n_atoms_total][3] (validated, in [0, L)).
+ * Enqueued on `stream`; the host array must stay valid until the stream reaches it. */
+int epsr_box_set_coords(epsr_box *box, const int32_t *xyz, epsr_stream_t stream);
+/* Same from a device int32 [n_atoms_total][3] (not validated; caller guarantees range). */
+int epsr_box_set_coords_device(epsr_box *box, const int32_t *xyz_dev, epsr_stream_t stream);
+/* Copies the current coordinates to device int32 [n_atoms_total][3]. */
+int epsr_box_get_coords_device(epsr_box *box, int32_t *xyz_dev, epsr_stream_t stream);
+
+/* Replaces box b's empirical potential from host FP32 [n_pairs][n_bins] (kJ/mol),
+ * pair order (0,0),(0,1),..,(1,1),.. (synchronises). */
+int epsr_box_set_ep(epsr_box *box, int32_t b, const float *ep, epsr_stream_t stream);
+int epsr_box_get_ep(epsr_box *box, int32_t b, float *ep, epsr_stream_t stream);
+
+/* Total potential energy of every box from scratch (Sec. 2.2 item III defines dU as
+ * U_after - U_before; this is U): sum over all pairs of atoms in different molecules
+ * of the pair energy, FP32 per pair, FP64 accumulation. U_host [n_boxes]. Synchronises. */
+int epsr_box_total_energy(epsr_box *box, double *U_host, epsr_stream_t stream);
+
+/* ---- Monte Carlo (Sec. 2.2 item III; Sec. 2.3: dU from the moved molecule against
+ * all atoms after every step) ----------------------------------------------------------
+ * Runs moves move0 .. move0+n_moves-1 on every box of the handle. Move t of box b
+ * draws three Philox4x32-10 blocks with counter (t lo, t hi, b, lane 0..2) and key
+ * (seed lo, seed hi): the molecule, a translation of at most max_translation per axis
+ * and (rigid molecules) a rotation of at most max_rotation_deg about the molecule's
+ * centre, then accepts with the Metropolis rule (dU <= 0, else with probability
+ * exp(-dU/kT)). The result is a deterministic function of (coordinates, seed, move0).
+ *   stats  host [n_boxes] or NULL: overwritten with the running totals.
+ *   log    device [n_boxes][n_moves] or NULL: one epsr_move_log per move.
+ * One cooperative persistent launch; synchronises `stream` to read its status.
+ * Errors: EINVAL, ELAUNCH (the CTAs cannot be co-resident), ETIMEOUT (a grid barrier
+ * wait exceeded its limit; coordinates are then unspecified), ECUDA.                 */
+int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
+                  epsr_mc_stats *stats, epsr_move_log *log, epsr_stream_t stream);
+/* Reads the running statistics without running moves (synchronises). */
+int epsr_mc_stats_get(epsr_box *box, epsr_mc_stats *stats, epsr_stream_t stream);
+/* Moves per speculative batch (1 .. 16, default 16): the sweep evaluates up to this many
+ * consecutive moves with distinct molecules per grid barrier and resolves them in order
+ * with exact pairwise corrections, so every value gives the sequential Metropolis chain
+ * (up to FP32 rounding of dU). Host only. */
+int epsr_mc_set_batch(epsr_box *box, int32_t batch_k);
+/* CTAs per box of the sweep (0 = automatic). For a batch of boxes, a total budget split
+ * in proportion to the atom counts. Host only; takes effect at the next sweep. */
+int epsr_mc_set_ctas(epsr_box *box, int32_t ctas);
+/* Test hook: CTA `cta` of the following sweeps skips its barrier arrival and every
+ * barrier wait is limited to timeout_ms, so the bounded wait expires and the sweep
+ * returns EPSR_ETIMEOUT with the GPU context intact. cta = -1 restores normal operation
+ * and the default limit (2000 ms). Host only. */
+int epsr_debug_barrier_fault(epsr_box *box, int32_t cta, double timeout_ms);
+
+/* ---- pair histograms and g(r) (Sec. 2.3: N(r), O(N^2) per evaluation) -----------------
+ * For every unordered pair i < j of each box (intra-molecular pairs included), the
+ * exact squared minimum-image distance selects bin k = floor(r / dr); if k < n_bins the
+ * pair's count hist[pair(t_i, t_j)][k] is incremented. Pair order is (0,0), (0,1), ..,
+ * (1,1), ... (upper triangle, row major); boxes are concatenated (epsr_box_offsets).
+ *   hist  device uint64 [hist_len], ACCUMULATED (not cleared), so repeated calls
+ *         accumulate statistics over configurations (Sec. 2.2 item VI).
+ *   g     device float [hist_len] or NULL: g_ab(k) = hist V / (n_configs P_ab shell_k),
+ *         P_ab = N_a N_b (a != b) or N_a (N_a - 1)/2, shell_k = 4 pi/3 (r_{k+1}^3 - r_k^3).
+ *   n_configs  number of configurations accumulated in hist (>= 1) for g.
+ * Asynchronous. Errors: EINVAL, ECUDA.                                                 */
+int epsr_partial_gr(epsr_box *box, uint64_t *hist, float *g, int64_t n_configs,
+                    epsr_stream_t stream);
+/* The same over a sub-range [pair_begin, pair_end) of the handle's pair-tile work list
+ * (for splitting one evaluation across devices or calls; the union of disjoint ranges
+ * covering [0, n_tiles) equals one full call). epsr_partial_gr_tiles reports n_tiles. */
+int epsr_partial_gr_tiles(const epsr_box *box, int64_t *n_tiles);
+int epsr_partial_gr_range(epsr_box *box, int64_t tile_begin, int64_t tile_end, uint64_t *hist,
+                          epsr_stream_t stream);
+/* g from an accumulated histogram only (no pair scan). */
+int epsr_normalize_g(epsr_box *box, const uint64_t *hist, float *g, int64_t n_configs,
+                     epsr_stream_t stream);
+
+/* Eq. (1) weight factors of box b: w[p] = 4 pi rho (2 - delta_ab) c_a c_b b_a b_b per
+ * pair (b in 1e-12 cm so S is in barn) and flat = sum_a c_a b_a^2. Host only. */
+int epsr_sq_weights(const epsr_box *box, int32_t b, double *w, double *flat);
+
+/* ---- S(Q) by Eq. (1) ---------------------------------------------------------------------
+ * Midpoint rule on bin centres r_k = (k + 1/2) dr:
+ *   S_partial[c](Q_i) = w[c] sum_k K[i][k] (g[c][k] - 1),  K[i][k] = r_k^2 dr sin(Q_i r_k)/(Q_i r_k)
+ *   S_total[s](Q_i)   = flat[s] + sum_{c in set s} S_partial[c](Q_i),
+ * sets being consecutive groups of cols_per_set columns. A plan caches K for one
+ * (Q grid, n_bins, dr, mode). mode EPSR_SQ_FP32 contracts on CUDA cores in FP32; the
+ * split modes contract on tcgen05 tensor cores with FP32 accumulation in TMEM, K and G
+ * split into hi + lo parts (lo = residual of hi) and the small cross terms kept.
+ *   Q          host float [nQ] (> 0)
+ *   g          device float [n_cols][n_bins]
+ *   w, flat    host double [n_cols], [n_cols / cols_per_set]
+ *   S_partial  device float [n_cols][nQ] or NULL;  S_total device float [n_sets][nQ] or NULL
+ * epsr_sq_plan_create synchronises; epsr_sq_exec is asynchronous and allocates nothing
+ * (graph-capturable). epsr_sq is a one-shot convenience (plan, exec, free).            */
+typedef struct epsr_sq_plan epsr_sq_plan;
+int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, double dr, int32_t mode,
+                        int32_t max_cols, epsr_stream_t stream, epsr_sq_plan **out);
+int epsr_sq_plan_destroy(epsr_sq_plan *plan);
+int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, const double *w,
+                 int32_t cols_per_set, const double *flat, float *S_partial, float *S_total,
+                 epsr_stream_t stream);
+int epsr_sq(const float *g, int32_t n_cols, int32_t n_bins, double dr, const float *Q,
+            int32_t nQ, const double *w, int32_t cols_per_set, const double *flat,
+            float *S_partial, float *S_total, int32_t mode, epsr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPSR_H */

@@ -1,0 +1,805 @@
+// epsr_api.cu -- host side of the libepsr C ABI: validation, exact tables, work lists,
+// device buffers and kernel launches. No exception crosses the boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "epsr.h"
+#include "epsr_device.cuh"
+#include "epsr_internal.h"
+#include "k_sq.h"
+
+using namespace epsr;
+
+// ---- errors ------------------------------------------------------------------------------
+static thread_local int g_last_status = EPSR_OK;
+static thread_local char g_last_msg[512] = "";
+
+int epsr::set_error(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_msg, sizeof(g_last_msg), fmt, ap);
+    va_end(ap);
+    g_last_status = status;
+    return status;
+}
+
+int epsr::set_cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(EPSR_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return set_cuda_error(e_, #call);   \
+    } while (0)
+
+extern "C" const char *epsr_strerror(int status)
+{
+    switch (status) {
+    case EPSR_OK: return "success";
+    case EPSR_EINVAL: return "invalid argument";
+    case EPSR_ENOMEM: return "out of memory";
+    case EPSR_ECUDA: return "CUDA runtime error";
+    case EPSR_ELAUNCH: return "persistent kernel cannot be co-resident";
+    case EPSR_ETIMEOUT: return "device-side wait timed out";
+    case EPSR_ENUMERIC: return "non-finite result";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int epsr_last_error_detail(char *buf, size_t len)
+{
+    if (buf && len) {
+        strncpy(buf, g_last_msg, len - 1);
+        buf[len - 1] = '\0';
+    }
+    return g_last_status;
+}
+
+extern "C" int epsr_version(void) { return 10000; }
+
+// ---- physical constants (SI exact values; eps0 CODATA 2018) --------------------------------
+static double coulomb_k()   // e^2 N_A / (4 pi eps0), kJ A / mol / e^2
+{
+    const double e = 1.602176634e-19, NA = 6.02214076e23, eps0 = 8.8541878128e-12;
+    const double pi = 3.14159265358979323846;
+    return e * e * NA / (4.0 * pi * eps0) * 1e10 * 1e-3;
+}
+
+static double gas_r() { return 1.380649e-23 * 6.02214076e23 * 1e-3; }   // kJ / mol / K
+
+// ---- handle -------------------------------------------------------------------------------
+template <class T>
+static int dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(EPSR_ENOMEM, "cudaMalloc of %zu bytes failed", n * sizeof(T));
+    }
+    return EPSR_OK;
+}
+
+struct epsr_box {
+    int n_boxes = 0;
+    long long n_atoms = 0;
+    long long hist_len = 0;
+    std::vector<epsr_box_desc> desc;
+    std::vector<BoxDev> hb;              // host copy of per-box parameters
+    std::vector<long long> hist_box_h;   // hist_off per box (ascending)
+    std::vector<int> mol_h;              // concatenated mol_start (box-local, int32)
+    std::vector<int> type_h;
+    std::vector<GrTile> tiles_h;
+    int sms = 0;
+    int mc_batch = 16;
+    int mc_ctas = 0;
+    int fault_cta = -1;
+    double timeout_ms = 2000.0;
+    // device
+    BoxDev *boxes = nullptr;
+    int4 *coords = nullptr;
+    uint4 *scaled = nullptr;
+    int *mol_start = nullptr;
+    int *atom_box = nullptr;
+    int *atom_mol = nullptr;
+    long long *thresholds = nullptr;
+    float *ep = nullptr;
+    GrTile *tiles = nullptr;
+    long long *hist_box = nullptr;
+    int *cta_box = nullptr;
+    int cta_box_len = 0;
+    float *slots = nullptr;
+    unsigned *flags = nullptr;
+    epsr_mc_stats *stats = nullptr;
+    int *status = nullptr;
+    double *U = nullptr;
+    int tbl_cap = 0, ep_cap = 0;
+
+    ~epsr_box()
+    {
+        void *ptrs[] = {boxes, coords, scaled, mol_start, atom_box, atom_mol, thresholds, ep,
+                        tiles, hist_box, cta_box, slots, flags, stats, status, U};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+};
+
+static int validate_desc(const epsr_box_desc &d, int b)
+{
+    if (d.n_atoms < 1 || d.n_atoms > (1LL << 30))
+        return set_error(EPSR_EINVAL, "box %d: n_atoms %lld out of range", b, (long long)d.n_atoms);
+    if (d.n_mol < 1 || d.n_mol > d.n_atoms)
+        return set_error(EPSR_EINVAL, "box %d: n_mol %lld out of range", b, (long long)d.n_mol);
+    if (d.L_fx < 2 || d.L_fx >= (1LL << 31))
+        return set_error(EPSR_EINVAL, "box %d: L_fx %lld out of range", b, (long long)d.L_fx);
+    if (d.scale_log2 < 10 || d.scale_log2 > 24)
+        return set_error(EPSR_EINVAL, "box %d: scale_log2 %d out of range", b, d.scale_log2);
+    if (d.n_types < 1 || d.n_types > EPSR_MAX_TYPES)
+        return set_error(EPSR_EINVAL, "box %d: n_types %d out of range", b, d.n_types);
+    if (d.bin_p < 1 || d.bin_q < 1 || d.n_bins < 1 || d.n_bins > EPSR_MAX_BINS)
+        return set_error(EPSR_EINVAL, "box %d: bins (%d/%d, %d) invalid", b, d.bin_p, d.bin_q, d.n_bins);
+    if (d.move_kind != EPSR_MOVE_ATOM && d.move_kind != EPSR_MOVE_RIGID_MOLECULE)
+        return set_error(EPSR_EINVAL, "box %d: move_kind %d invalid", b, d.move_kind);
+    if (!(d.temperature > 0) || !(d.max_translation >= 0) || !(d.max_rotation_deg >= 0) ||
+        !(d.max_rotation_deg < 180) || !(d.r_coul >= 0))
+        return set_error(EPSR_EINVAL, "box %d: temperature/move/cutoff parameters invalid", b);
+    const double S = std::ldexp(1.0, d.scale_log2);
+    if (d.max_translation * S > 0.25 * (double)d.L_fx)
+        return set_error(EPSR_EINVAL, "box %d: max_translation too large for the box", b);
+    for (int t = 0; t < d.n_types; ++t)
+        if (!std::isfinite(d.q[t]) || !std::isfinite(d.sigma[t]) || !(d.eps[t] >= 0) ||
+            !std::isfinite(d.eps[t]) || !(d.sigma[t] >= 0) || !std::isfinite(d.b[t]))
+            return set_error(EPSR_EINVAL, "box %d: force field of type %d invalid", b, t);
+    // the table edge r_max must map to a 63-bit squared distance
+    const double rmax_fx = (double)d.n_bins * d.bin_p / d.bin_q * S;
+    if (rmax_fx * rmax_fx > 4.0e18)
+        return set_error(EPSR_EINVAL, "box %d: bin range too large", b);
+    return EPSR_OK;
+}
+
+// Exact threshold table: T[k] = ceil((k p S / q)^2), k = 0..n_bins, so that
+// d2 >= T[k] <=> sqrt(d2) >= k dr (d2 integer).
+static void build_thresholds(const epsr_box_desc &d, long long *T)
+{
+    const unsigned __int128 q2 = (unsigned __int128)d.bin_q * d.bin_q;
+    for (int k = 0; k <= d.n_bins; ++k) {
+        const unsigned __int128 num = ((unsigned __int128)k * k * d.bin_p * d.bin_p) << (2 * d.scale_log2);
+        T[k] = (long long)((num + q2 - 1) / q2);
+    }
+}
+
+static void fill_boxdev(const epsr_box_desc &d, const int *type, BoxDev &b)
+{
+    memset(&b, 0, sizeof(b));
+    const double S = std::ldexp(1.0, d.scale_log2);
+    b.n_atoms = (int)d.n_atoms;
+    b.n_mol = (int)d.n_mol;
+    b.L = (int)d.L_fx;
+    b.n_types = d.n_types;
+    b.n_pairs = d.n_types * (d.n_types + 1) / 2;
+    b.n_bins = d.n_bins;
+    b.move_kind = d.move_kind;
+    b.max_shift = (int)std::llround(d.max_translation * S);
+    const long long rc = std::llround(d.r_coul * S);
+    b.rc2 = rc * rc;
+    const double pi = 3.14159265358979323846;
+    b.h_rot = std::tan(0.5 * d.max_rotation_deg * pi / 180.0) / std::sqrt(3.0);
+    b.kT = gas_r() * d.temperature;
+    const double LA = (double)d.L_fx / S;
+    b.volume = LA * LA * LA;
+    b.dr_A = (double)d.bin_p / (double)d.bin_q;
+    b.inv_s2 = (float)std::ldexp(1.0, -2 * d.scale_log2);
+    b.inv_dr_fx = (float)((double)d.bin_q / ((double)d.bin_p * S));
+    for (long long i = 0; i < d.n_atoms; ++i) b.count[type[i]]++;
+    const double ke = coulomb_k();
+    for (int a = 0; a < kMaxTypes; ++a)
+        for (int c = 0; c < kMaxTypes; ++c) {
+            PairRow &r = b.row[a * kMaxTypes + c];
+            r.c12 = r.c6 = r.kqq = 0.f;
+            r.pair = 0;
+            if (a >= d.n_types || c >= d.n_types) continue;
+            const double eps = std::sqrt(d.eps[a] * d.eps[c]);
+            const double sig = 0.5 * (d.sigma[a] + d.sigma[c]);
+            if (eps > 0.0) {
+                const double s6 = std::pow(sig, 6.0);
+                r.c12 = (float)(4.0 * eps * s6 * s6);
+                r.c6 = (float)(4.0 * eps * s6);
+            }
+            r.kqq = (float)(ke * d.q[a] * d.q[c]);
+            r.pair = pair_index(a, c, d.n_types);
+        }
+}
+
+static void plan_mc_groups(epsr_box *h)
+{
+    // CTAs per box: a single box uses up to one CTA per SM, at least ~512 partner atoms
+    // per CTA; a batch splits the budget in proportion to the atom counts.
+    const int nb = h->n_boxes;
+    const int budget = h->mc_ctas > 0 ? h->mc_ctas : h->sms;
+    std::vector<int> G(nb, 1);
+    if (nb == 1) {
+        long long want = (h->hb[0].n_atoms + 511) / 512;
+        G[0] = (int)std::max(1LL, std::min<long long>(want, budget));
+    } else {
+        long long tot = 0;
+        for (auto &b : h->hb) tot += b.n_atoms;
+        int used = 0;
+        for (int i = 0; i < nb; ++i) {
+            G[i] = std::max(1, (int)((double)budget * h->hb[i].n_atoms / (double)tot));
+            used += G[i];
+        }
+        // trim the largest groups if rounding up overshot the budget
+        while (used > std::max(budget, nb)) {
+            int imax = (int)(std::max_element(G.begin(), G.end()) - G.begin());
+            if (G[imax] <= 1) break;
+            --G[imax];
+            --used;
+        }
+    }
+    int c0 = 0;
+    for (int i = 0; i < nb; ++i) {
+        h->hb[i].cta0 = c0;
+        h->hb[i].n_cta = G[i];
+        h->hb[i].chunk = (h->hb[i].n_atoms + G[i] - 1) / G[i];
+        c0 += G[i];
+    }
+    h->cta_box_len = c0;
+}
+
+static int upload_mc_groups(epsr_box *h)
+{
+    std::vector<int> cb;
+    for (int i = 0; i < h->n_boxes; ++i)
+        for (int k = 0; k < h->hb[i].n_cta; ++k) cb.push_back(i);
+    if (h->cta_box) cudaFree(h->cta_box);
+    if (h->slots) cudaFree(h->slots);
+    if (h->flags) cudaFree(h->flags);
+    h->cta_box = nullptr; h->slots = nullptr; h->flags = nullptr;
+    int rc;
+    if ((rc = dalloc(&h->cta_box, cb.size())) || (rc = dalloc(&h->slots, 2 * cb.size() * mc_batch_max())) ||
+        (rc = dalloc(&h->flags, cb.size())))
+        return rc;
+    CK(cudaMemcpy(h->cta_box, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->boxes, h->hb.data(), h->hb.size() * sizeof(BoxDev), cudaMemcpyHostToDevice));
+    return EPSR_OK;
+}
+
+static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *xyz,
+                       const int32_t *type, const int64_t *mol_start, cudaStream_t stream,
+                       epsr_box **out)
+{
+    if (!out) return set_error(EPSR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!descs || !xyz || !type || !mol_start || n_boxes < 1 || n_boxes > 65536)
+        return set_error(EPSR_EINVAL, "NULL array or n_boxes out of range");
+    epsr_box *h = new (std::nothrow) epsr_box();
+    if (!h) return set_error(EPSR_ENOMEM, "host allocation failed");
+    h->n_boxes = n_boxes;
+    h->desc.assign(descs, descs + n_boxes);
+    h->hb.resize(n_boxes);
+    long long atom0 = 0, mol0 = 0, hist0 = 0;
+    int tbl0 = 0, ep0 = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        const epsr_box_desc &d = descs[b];
+        int rc = validate_desc(d, b);
+        if (rc) { delete h; return rc; }
+        const int32_t *ty = type + atom0;
+        for (long long i = 0; i < d.n_atoms; ++i)
+            if (ty[i] < 0 || ty[i] >= d.n_types) { delete h; return set_error(EPSR_EINVAL, "box %d: type[%lld] = %d out of range", b, i, ty[i]); }
+        for (long long i = 0; i < 3 * d.n_atoms; ++i) {
+            const int32_t v = xyz[3 * atom0 + i];
+            if (v < 0 || v >= d.L_fx) { delete h; return set_error(EPSR_EINVAL, "box %d: coordinate %lld = %d outside [0, L_fx)", b, i, v); }
+        }
+        const int64_t *ms = mol_start + mol0;
+        if (ms[0] != 0 || ms[d.n_mol] != d.n_atoms) { delete h; return set_error(EPSR_EINVAL, "box %d: mol_start must run from 0 to n_atoms", b); }
+        for (long long m = 0; m < d.n_mol; ++m) {
+            const long long sz = ms[m + 1] - ms[m];
+            if (sz < 1) { delete h; return set_error(EPSR_EINVAL, "box %d: mol_start not strictly increasing at %lld", b, m); }
+            if (d.move_kind == EPSR_MOVE_ATOM && sz != 1) { delete h; return set_error(EPSR_EINVAL, "box %d: atom moves need single-atom molecules", b); }
+            if (sz > EPSR_MAX_MOL_ATOMS) { delete h; return set_error(EPSR_EINVAL, "box %d: molecule %lld has %lld > %d atoms", b, m, sz, EPSR_MAX_MOL_ATOMS); }
+        }
+        BoxDev &bx = h->hb[b];
+        fill_boxdev(d, ty, bx);
+        bx.atom0 = atom0;
+        bx.mol0 = mol0;
+        bx.hist_off = hist0;
+        bx.tbl_off = tbl0;
+        bx.ep_off = ep0;
+        h->hist_box_h.push_back(hist0);
+        for (long long m = 0; m <= d.n_mol; ++m) h->mol_h.push_back((int)ms[m]);
+        atom0 += d.n_atoms;
+        mol0 += d.n_mol + 1;
+        hist0 += (long long)bx.n_pairs * bx.n_bins;
+        tbl0 += bx.n_bins + 1;
+        ep0 += bx.n_pairs * bx.n_bins;
+        h->tbl_cap = std::max(h->tbl_cap, bx.n_bins + 1);
+        h->ep_cap = std::max(h->ep_cap, bx.n_pairs * bx.n_bins);
+    }
+    h->n_atoms = atom0;
+    h->hist_len = hist0;
+    // thresholds, prefilter widths
+    std::vector<long long> T(tbl0);
+    for (int b = 0; b < n_boxes; ++b) {
+        BoxDev &bx = h->hb[b];
+        build_thresholds(descs[b], &T[bx.tbl_off]);
+        bx.tmax = T[bx.tbl_off + bx.n_bins];
+        const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
+        const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
+        bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
+    }
+    // g(r) work list: upper triangle of tile pairs per box
+    for (int b = 0; b < n_boxes; ++b) {
+        const int nt = (h->hb[b].n_atoms + kGrTile - 1) / kGrTile;
+        for (int i = 0; i < nt; ++i)
+            for (int j = i; j < nt; ++j) h->tiles_h.push_back(GrTile{b, i, j, 0});
+    }
+    // per-atom arrays
+    std::vector<int4> c4(atom0);
+    std::vector<int> abox(atom0), amol(atom0);
+    long long a = 0, mo = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        const epsr_box_desc &d = descs[b];
+        for (long long m = 0; m < d.n_mol; ++m)
+            for (long long i = mol_start[mo + m]; i < mol_start[mo + m + 1]; ++i) amol[a + i] = (int)m;
+        for (long long i = 0; i < d.n_atoms; ++i, ++a) {
+            c4[a] = make_int4(xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], type[a]);
+            abox[a] = b;
+        }
+        mo += d.n_mol + 1;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+    int rc;
+    if ((rc = dalloc(&h->boxes, n_boxes)) || (rc = dalloc(&h->coords, atom0)) ||
+        (rc = dalloc(&h->scaled, atom0)) || (rc = dalloc(&h->mol_start, h->mol_h.size())) ||
+        (rc = dalloc(&h->atom_box, atom0)) || (rc = dalloc(&h->atom_mol, atom0)) ||
+        (rc = dalloc(&h->thresholds, T.size())) || (rc = dalloc(&h->ep, (size_t)ep0)) ||
+        (rc = dalloc(&h->tiles, h->tiles_h.size())) || (rc = dalloc(&h->hist_box, n_boxes)) ||
+        (rc = dalloc(&h->stats, n_boxes)) || (rc = dalloc(&h->status, 1)) ||
+        (rc = dalloc(&h->U, n_boxes))) {
+        delete h;
+        return rc;
+    }
+#define CKD(call)                                                            \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) { int r_ = set_cuda_error(e_, #call); delete h; return r_; } \
+    } while (0)
+    CKD(cudaMemcpyAsync(h->coords, c4.data(), atom0 * sizeof(int4), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemcpyAsync(h->mol_start, h->mol_h.data(), h->mol_h.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemcpyAsync(h->atom_box, abox.data(), atom0 * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemcpyAsync(h->atom_mol, amol.data(), atom0 * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemcpyAsync(h->thresholds, T.data(), T.size() * sizeof(long long), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemsetAsync(h->ep, 0, (size_t)std::max(ep0, 1) * sizeof(float), stream));
+    CKD(cudaMemcpyAsync(h->tiles, h->tiles_h.data(), h->tiles_h.size() * sizeof(GrTile), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemcpyAsync(h->hist_box, h->hist_box_h.data(), n_boxes * sizeof(long long), cudaMemcpyHostToDevice, stream));
+    CKD(cudaMemsetAsync(h->stats, 0, n_boxes * sizeof(epsr_mc_stats), stream));
+    CKD(cudaMemsetAsync(h->status, 0, sizeof(int), stream));
+    CKD(cudaStreamSynchronize(stream));
+    plan_mc_groups(h);
+    if ((rc = upload_mc_groups(h))) { delete h; return rc; }
+    *out = h;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_create(const epsr_box_desc *desc, const int32_t *xyz, const int32_t *type,
+                               const int64_t *mol_start, epsr_stream_t stream, epsr_box **out)
+{
+    return create_impl(desc, 1, xyz, type, mol_start, (cudaStream_t)stream, out);
+}
+
+extern "C" int epsr_batch_create(const epsr_box_desc *descs, int32_t n_boxes, const int32_t *xyz,
+                                 const int32_t *type, const int64_t *mol_start, epsr_stream_t stream,
+                                 epsr_box **out)
+{
+    return create_impl(descs, n_boxes, xyz, type, mol_start, (cudaStream_t)stream, out);
+}
+
+extern "C" int epsr_box_destroy(epsr_box *box)
+{
+    if (!box) return EPSR_OK;
+    cudaDeviceSynchronize();
+    delete box;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_info(const epsr_box *box, int32_t *n_boxes, int64_t *n_atoms_total,
+                             int64_t *hist_len)
+{
+    if (!box) return set_error(EPSR_EINVAL, "box is NULL");
+    if (n_boxes) *n_boxes = box->n_boxes;
+    if (n_atoms_total) *n_atoms_total = box->n_atoms;
+    if (hist_len) *hist_len = box->hist_len;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_offsets(const epsr_box *box, int32_t b, int64_t *hist_offset,
+                                int64_t *atom_offset)
+{
+    if (!box || b < 0 || b >= box->n_boxes) return set_error(EPSR_EINVAL, "bad box or index");
+    if (hist_offset) *hist_offset = box->hb[b].hist_off;
+    if (atom_offset) *atom_offset = box->hb[b].atom0;
+    return EPSR_OK;
+}
+
+// int4 {x,y,z,type} <-> int32 [n][3]
+__global__ static void pack_xyz_kernel(const int4 *c, int *xyz, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int4 v = c[i];
+        xyz[3 * i] = v.x; xyz[3 * i + 1] = v.y; xyz[3 * i + 2] = v.z;
+    }
+}
+
+__global__ static void unpack_xyz_kernel(const int *xyz, int4 *c, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int4 v = c[i];
+        v.x = xyz[3 * i]; v.y = xyz[3 * i + 1]; v.z = xyz[3 * i + 2];
+        c[i] = v;
+    }
+}
+
+static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+
+extern "C" int epsr_box_get_coords_device(epsr_box *box, int32_t *xyz_dev, epsr_stream_t stream)
+{
+    if (!box || !xyz_dev) return set_error(EPSR_EINVAL, "NULL argument");
+    pack_xyz_kernel<<<grid_for(box->n_atoms), 256, 0, (cudaStream_t)stream>>>(box->coords, xyz_dev, box->n_atoms);
+    CK(cudaGetLastError());
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_set_coords_device(epsr_box *box, const int32_t *xyz_dev, epsr_stream_t stream)
+{
+    if (!box || !xyz_dev) return set_error(EPSR_EINVAL, "NULL argument");
+    unpack_xyz_kernel<<<grid_for(box->n_atoms), 256, 0, (cudaStream_t)stream>>>(xyz_dev, box->coords, box->n_atoms);
+    CK(cudaGetLastError());
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_get_coords(epsr_box *box, int32_t *xyz, epsr_stream_t stream)
+{
+    if (!box || !xyz) return set_error(EPSR_EINVAL, "NULL argument");
+    std::vector<int4> c(box->n_atoms);
+    CK(cudaMemcpyAsync(c.data(), box->coords, box->n_atoms * sizeof(int4), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    for (long long i = 0; i < box->n_atoms; ++i) {
+        xyz[3 * i] = c[i].x; xyz[3 * i + 1] = c[i].y; xyz[3 * i + 2] = c[i].z;
+    }
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_set_coords(epsr_box *box, const int32_t *xyz, epsr_stream_t stream)
+{
+    if (!box || !xyz) return set_error(EPSR_EINVAL, "NULL argument");
+    std::vector<int4> c(box->n_atoms);
+    CK(cudaMemcpyAsync(c.data(), box->coords, box->n_atoms * sizeof(int4), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int b = 0; b < box->n_boxes; ++b) {
+        const BoxDev &bx = box->hb[b];
+        for (long long i = bx.atom0; i < bx.atom0 + bx.n_atoms; ++i)
+            for (int a = 0; a < 3; ++a) {
+                const int v = xyz[3 * i + a];
+                if (v < 0 || v >= bx.L) return set_error(EPSR_EINVAL, "coordinate %lld outside [0, L_fx)", 3 * i + a);
+            }
+    }
+    for (long long i = 0; i < box->n_atoms; ++i) {
+        c[i].x = xyz[3 * i]; c[i].y = xyz[3 * i + 1]; c[i].z = xyz[3 * i + 2];
+    }
+    CK(cudaMemcpyAsync(box->coords, c.data(), box->n_atoms * sizeof(int4), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_set_ep(epsr_box *box, int32_t b, const float *ep, epsr_stream_t stream)
+{
+    if (!box || !ep || b < 0 || b >= box->n_boxes) return set_error(EPSR_EINVAL, "bad argument");
+    BoxDev &bx = box->hb[b];
+    const int n = bx.n_pairs * bx.n_bins;
+    int nz = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(ep[i])) return set_error(EPSR_EINVAL, "empirical potential not finite");
+        nz |= ep[i] != 0.f;
+    }
+    CK(cudaMemcpyAsync(box->ep + bx.ep_off, ep, n * sizeof(float), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    bx.has_ep = nz;
+    CK(cudaMemcpyAsync(box->boxes + b, &bx, sizeof(BoxDev), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_get_ep(epsr_box *box, int32_t b, float *ep, epsr_stream_t stream)
+{
+    if (!box || !ep || b < 0 || b >= box->n_boxes) return set_error(EPSR_EINVAL, "bad argument");
+    const BoxDev &bx = box->hb[b];
+    CK(cudaMemcpyAsync(ep, box->ep + bx.ep_off, bx.n_pairs * bx.n_bins * sizeof(float), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_total_energy(epsr_box *box, double *U_host, epsr_stream_t stream)
+{
+    if (!box || !U_host) return set_error(EPSR_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(box->U, 0, box->n_boxes * sizeof(double), s));
+    int rc = launch_total_energy(box->boxes, box->coords, box->atom_mol, box->thresholds, box->ep,
+                                 box->tiles, (long long)box->tiles_h.size(), box->U, box->sms * 2, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(U_host, box->U, box->n_boxes * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return EPSR_OK;
+}
+
+// ---- Monte Carlo ------------------------------------------------------------------------------
+extern "C" int epsr_mc_set_batch(epsr_box *box, int32_t batch_k)
+{
+    if (!box || batch_k < 1 || batch_k > mc_batch_max()) return set_error(EPSR_EINVAL, "batch_k out of range");
+    box->mc_batch = batch_k;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_mc_set_ctas(epsr_box *box, int32_t ctas)
+{
+    if (!box || ctas < 0 || ctas > 65536) return set_error(EPSR_EINVAL, "ctas out of range");
+    box->mc_ctas = ctas;
+    plan_mc_groups(box);
+    return upload_mc_groups(box);
+}
+
+extern "C" int epsr_debug_barrier_fault(epsr_box *box, int32_t cta, double timeout_ms)
+{
+    if (!box || !(timeout_ms > 0)) return set_error(EPSR_EINVAL, "bad argument");
+    box->fault_cta = cta;
+    box->timeout_ms = cta < 0 ? 2000.0 : timeout_ms;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_mc_stats_get(epsr_box *box, epsr_mc_stats *stats, epsr_stream_t stream)
+{
+    if (!box || !stats) return set_error(EPSR_EINVAL, "NULL argument");
+    CK(cudaMemcpyAsync(stats, box->stats, box->n_boxes * sizeof(epsr_mc_stats), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EPSR_OK;
+}
+
+extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
+                             epsr_mc_stats *stats, epsr_move_log *log, epsr_stream_t stream)
+{
+    if (!box || n_moves < 0) return set_error(EPSR_EINVAL, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_moves > 0) {
+        int slice_cap = 0;
+        for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
+        size_t smem = (size_t)slice_cap * sizeof(int4) + (size_t)box->tbl_cap * sizeof(long long) +
+                      (size_t)box->ep_cap * sizeof(float);
+        smem = (smem + 15) & ~(size_t)15;
+        if (smem > kMcMaxDynSmem)
+            return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of shared memory per CTA needed (limit %zu); "
+                             "give the sweep more CTAs", smem, kMcMaxDynSmem);
+        McArgs a;
+        memset(&a, 0, sizeof(a));
+        a.boxes = box->boxes;
+        a.coords = box->coords;
+        a.mol_start = box->mol_start;
+        a.thresholds = box->thresholds;
+        a.ep = box->ep;
+        a.cta_box = box->cta_box;
+        a.slots = box->slots;
+        a.flags = box->flags;
+        a.stats = box->stats;
+        a.log = log;
+        a.status = box->status;
+        a.n_moves = n_moves;
+        a.seed = seed;
+        a.move0 = move0;
+        a.log_stride = n_moves;
+        a.max_spin = 1LL << 40;
+        a.timeout_ns = (unsigned long long)(box->timeout_ms * 1e6);
+        a.grid = box->cta_box_len;
+        a.batch_k = box->mc_batch;
+        a.slice_cap = slice_cap;
+        a.tbl_cap = box->tbl_cap;
+        a.skip_arrival_cta = box->fault_cta;
+        CK(cudaMemsetAsync(box->flags, 0, box->cta_box_len * sizeof(unsigned), s));
+        CK(cudaMemsetAsync(box->status, 0, sizeof(int), s));
+        int rc = launch_mc_sweep(a, box->cta_box_len, smem, s);
+        if (rc) return rc;
+    }
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, box->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (stats) CK(cudaMemcpyAsync(stats, box->stats, box->n_boxes * sizeof(epsr_mc_stats), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st & kStatusTimeout) return set_error(EPSR_ETIMEOUT, "mc sweep: a grid barrier wait exceeded %.0f ms", box->timeout_ms);
+    return EPSR_OK;
+}
+
+// ---- pair histograms --------------------------------------------------------------------------
+extern "C" int epsr_partial_gr_tiles(const epsr_box *box, int64_t *n_tiles)
+{
+    if (!box || !n_tiles) return set_error(EPSR_EINVAL, "NULL argument");
+    *n_tiles = (int64_t)box->tiles_h.size();
+    return EPSR_OK;
+}
+
+static int gr_range(epsr_box *box, long long t0, long long t1, uint64_t *hist, cudaStream_t s)
+{
+    if (!box || !hist) return set_error(EPSR_EINVAL, "NULL argument");
+    const long long nt = (long long)box->tiles_h.size();
+    if (t0 < 0 || t1 > nt || t0 > t1) return set_error(EPSR_EINVAL, "tile range [%lld, %lld) outside [0, %lld)", t0, t1, nt);
+    int rc = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
+    if (rc) return rc;
+    GrArgs a;
+    a.boxes = box->boxes;
+    a.coords = box->coords;
+    a.scaled = box->scaled;
+    a.thresholds = box->thresholds;
+    a.tiles = box->tiles;
+    a.tile_begin = t0;
+    a.tile_end = t1;
+    a.hist = (unsigned long long *)hist;
+    a.max_pairs_bins = box->ep_cap;
+    a.max_bins1 = box->tbl_cap;
+    const int grid = (int)std::min<long long>(t1 - t0, (long long)box->sms * 2);
+    return launch_partial_gr(a, std::max(grid, 1), s);
+}
+
+extern "C" int epsr_partial_gr_range(epsr_box *box, int64_t tile_begin, int64_t tile_end,
+                                     uint64_t *hist, epsr_stream_t stream)
+{
+    return gr_range(box, tile_begin, tile_end, hist, (cudaStream_t)stream);
+}
+
+extern "C" int epsr_normalize_g(epsr_box *box, const uint64_t *hist, float *g, int64_t n_configs,
+                                epsr_stream_t stream)
+{
+    if (!box || !hist || !g || n_configs < 1) return set_error(EPSR_EINVAL, "bad argument");
+    return launch_normalize_g(box->boxes, box->n_boxes, (const unsigned long long *)hist, g, n_configs,
+                              box->hist_len, box->hist_box, (cudaStream_t)stream);
+}
+
+extern "C" int epsr_partial_gr(epsr_box *box, uint64_t *hist, float *g, int64_t n_configs,
+                               epsr_stream_t stream)
+{
+    if (!box || !hist) return set_error(EPSR_EINVAL, "NULL argument");
+    if (g && n_configs < 1) return set_error(EPSR_EINVAL, "n_configs must be >= 1");
+    int rc = gr_range(box, 0, (long long)box->tiles_h.size(), hist, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (g) return epsr_normalize_g(box, hist, g, n_configs, stream);
+    return EPSR_OK;
+}
+
+extern "C" int epsr_sq_weights(const epsr_box *box, int32_t b, double *w, double *flat)
+{
+    if (!box || b < 0 || b >= box->n_boxes || !w || !flat) return set_error(EPSR_EINVAL, "bad argument");
+    const epsr_box_desc &d = box->desc[b];
+    const BoxDev &bx = box->hb[b];
+    const double N = (double)d.n_atoms;
+    const double rho = N / bx.volume;
+    const double pi = 3.14159265358979323846;
+    double fl = 0.0;
+    for (int a = 0; a < d.n_types; ++a) {
+        const double ca = (double)bx.count[a] / N, ba = d.b[a] * 0.1;
+        fl += ca * ba * ba;
+        for (int c = a; c < d.n_types; ++c) {
+            const double cc = (double)bx.count[c] / N, bc = d.b[c] * 0.1;
+            w[pair_index(a, c, d.n_types)] = 4.0 * pi * rho * (a == c ? 1.0 : 2.0) * ca * cc * ba * bc;
+        }
+    }
+    *flat = fl;
+    return EPSR_OK;
+}
+
+// ---- S(Q) -----------------------------------------------------------------------------------
+struct epsr_sq_plan {
+    int nQ = 0, n_bins = 0, mode = 0, max_cols = 0;
+    double dr = 0;
+    float *Q = nullptr;
+    float *Kt = nullptr;
+    float *Sp_scratch = nullptr;
+    ~epsr_sq_plan()
+    {
+        if (Q) cudaFree(Q);
+        if (Kt) cudaFree(Kt);
+        if (Sp_scratch) cudaFree(Sp_scratch);
+    }
+};
+
+extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, double dr, int32_t mode,
+                                   int32_t max_cols, epsr_stream_t stream, epsr_sq_plan **out)
+{
+    if (!out) return set_error(EPSR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!Q || nQ < 1 || nQ > (1 << 20) || n_bins < 1 || n_bins > EPSR_MAX_BINS || !(dr > 0) ||
+        max_cols < 1 || max_cols > EPSR_SQ_MAX_COLS)
+        return set_error(EPSR_EINVAL, "sq plan: argument out of range");
+    if (mode != EPSR_SQ_FP32) return set_error(EPSR_EINVAL, "sq plan: mode %d not available", mode);
+    for (int i = 0; i < nQ; ++i)
+        if (!(Q[i] > 0) || !std::isfinite(Q[i])) return set_error(EPSR_EINVAL, "sq plan: Q[%d] must be > 0", i);
+    epsr_sq_plan *p = new (std::nothrow) epsr_sq_plan();
+    if (!p) return set_error(EPSR_ENOMEM, "host allocation failed");
+    p->nQ = nQ; p->n_bins = n_bins; p->mode = mode; p->max_cols = max_cols; p->dr = dr;
+    int rc;
+    if ((rc = dalloc(&p->Q, nQ)) || (rc = dalloc(&p->Kt, (size_t)nQ * n_bins)) ||
+        (rc = dalloc(&p->Sp_scratch, (size_t)max_cols * nQ))) {
+        delete p;
+        return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(p->Q, Q, nQ * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { delete p; return set_cuda_error(e, "sq plan upload"); }
+    if ((rc = sq_build_kt(p->Q, nQ, n_bins, dr, p->Kt, s))) { delete p; return rc; }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { delete p; return set_cuda_error(e, "sq plan sync"); }
+    *out = p;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_sq_plan_destroy(epsr_sq_plan *plan)
+{
+    if (!plan) return EPSR_OK;
+    cudaDeviceSynchronize();
+    delete plan;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, const double *w,
+                            int32_t cols_per_set, const double *flat, float *S_partial, float *S_total,
+                            epsr_stream_t stream)
+{
+    if (!plan || !g || !w || n_cols < 1 || n_cols > plan->max_cols || cols_per_set < 1 ||
+        n_cols % cols_per_set != 0)
+        return set_error(EPSR_EINVAL, "sq exec: bad argument");
+    if (S_total && !flat) return set_error(EPSR_EINVAL, "sq exec: flat is NULL");
+    if (!S_partial && !S_total) return EPSR_OK;
+    SqArgs *a = new (std::nothrow) SqArgs();
+    if (!a) return set_error(EPSR_ENOMEM, "host allocation failed");
+    a->g = g;
+    a->Kt = plan->Kt;
+    a->S_partial = S_partial ? S_partial : plan->Sp_scratch;
+    a->nQ = plan->nQ;
+    a->n_bins = plan->n_bins;
+    a->n_cols = n_cols;
+    for (int c = 0; c < n_cols; ++c) a->w[c] = w[c];
+    int rc = sq_exec_fp32(*a, (cudaStream_t)stream);
+    if (!rc && S_total) {
+        SqWeights *W = new (std::nothrow) SqWeights();
+        if (!W) { delete a; return set_error(EPSR_ENOMEM, "host allocation failed"); }
+        for (int s = 0; s < n_cols / cols_per_set; ++s) W->flat[s] = flat[s];
+        rc = sq_totals(a->S_partial, n_cols / cols_per_set, cols_per_set, plan->nQ, *W, S_total,
+                       (cudaStream_t)stream);
+        delete W;
+    }
+    delete a;
+    return rc;
+}
+
+extern "C" int epsr_sq(const float *g, int32_t n_cols, int32_t n_bins, double dr, const float *Q,
+                       int32_t nQ, const double *w, int32_t cols_per_set, const double *flat,
+                       float *S_partial, float *S_total, int32_t mode, epsr_stream_t stream)
+{
+    epsr_sq_plan *p = nullptr;
+    int rc = epsr_sq_plan_create(Q, nQ, n_bins, dr, mode, n_cols, stream, &p);
+    if (rc) return rc;
+    rc = epsr_sq_exec(p, g, n_cols, w, cols_per_set, flat, S_partial, S_total, stream);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) rc = set_cuda_error(e, "sq sync");
+    }
+    epsr_sq_plan_destroy(p);
+    return rc;
+}

@@ -1,0 +1,84 @@
+// epsr_internal.h -- host-side declarations shared by libepsr's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "epsr.h"
+
+namespace epsr {
+
+struct BoxDev;
+
+// ---- errors (thread-local last error, see epsr_last_error_detail) -------------------------
+int set_error(int status, const char *fmt, ...);
+int set_cuda_error(cudaError_t e, const char *what);
+
+// ---- Monte Carlo kernel ----------------------------------------------------------------------
+constexpr size_t kMcMaxDynSmem = 200 * 1024;
+
+struct McArgs {
+    const BoxDev *boxes;
+    int4 *coords;                 // [n_atoms_total] {x, y, z, type}
+    const int *mol_start;         // concatenated box-local molecule starts
+    const long long *thresholds;  // concatenated [n_bins + 1] per box
+    const float *ep;              // concatenated [n_pairs * n_bins] per box
+    const int *cta_box;           // [grid]
+    float *slots;                 // [2][grid][batch max] partial dU per CTA
+    unsigned *flags;              // [grid] arrival sequence numbers (zeroed per launch)
+    epsr_mc_stats *stats;         // [n_boxes] running totals (device)
+    epsr_move_log *log;           // nullable [n_boxes][log_stride]
+    int *status;                  // device status word
+    long long n_moves;
+    unsigned long long seed, move0;
+    long long log_stride;
+    long long max_spin;           // iteration limit of one barrier wait
+    unsigned long long timeout_ns;// time limit of one barrier wait
+    int grid;
+    int batch_k;
+    int slice_cap;                // int4 capacity of the shared partner slice
+    int tbl_cap;                  // capacity (entries) of the shared threshold table
+    int skip_arrival_cta;         // test hook: this CTA never arrives (-1: none)
+};
+
+int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stream);
+int mc_threads();
+int mc_batch_max();
+
+// ---- pair histogram kernels ---------------------------------------------------------------
+struct GrTile {           // one (i-tile, j-tile) pair of one box
+    int box;
+    int ti, tj;
+    int pad;
+};
+
+struct GrArgs {
+    const BoxDev *boxes;
+    const int4 *coords;          // [n_atoms_total]
+    const uint4 *scaled;         // [n_atoms_total] {x', y', z', type} on the 2^32-periodic grid
+    const long long *thresholds;
+    const GrTile *tiles;
+    long long tile_begin, tile_end;
+    unsigned long long *hist;    // accumulated output
+    int max_pairs_bins;          // max over boxes of n_pairs * n_bins (shared histogram size)
+    int max_bins1;               // max over boxes of n_bins + 1
+};
+
+constexpr int kGrTile = 1024;    // atoms per tile (both sides)
+
+int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *coords,
+                        uint4 *scaled, long long n, cudaStream_t stream);
+int launch_partial_gr(const GrArgs &args, int grid, cudaStream_t stream);
+int launch_normalize_g(const BoxDev *boxes, int n_boxes, const unsigned long long *hist,
+                       float *g, long long n_configs, long long hist_len, const long long *hist_box,
+                       cudaStream_t stream);
+int launch_total_energy(const BoxDev *boxes, const int4 *coords, const int *atom_mol,
+                        const long long *thresholds, const float *ep, const GrTile *tiles,
+                        long long n_tiles, double *U, int grid, cudaStream_t stream);
+
+// ---- S(Q) --------------------------------------------------------------------------------
+int sq_build_kernel_matrix(const float *Q, int nQ, int n_bins, double dr, int mode, float *K32,
+                           void *Ksplit, int ld_split, cudaStream_t stream);
+
+}  // namespace epsr

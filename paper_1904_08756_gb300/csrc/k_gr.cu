@@ -1,0 +1,302 @@
+// k_gr.cu -- all-pair partial histograms N_ab(r) (Sec. 2.3, O(N^2) per evaluation),
+// g_ab(r) normalisation, and the O(N^2) total energy, on sm_103a.
+//
+// Work list: (box, i-tile, j-tile) with i-tile <= j-tile over tiles of kGrTile atoms,
+// processed by a persistent grid. A CTA stages the j-tile in shared memory (coalesced
+// 128-bit loads) and each thread keeps kGrR i-atoms in registers, so one broadcast
+// shared load serves kGrR pair tests.
+//
+// Prefilter: a second copy of the coordinates is scaled so that the box side maps to
+// 2^32 (x' = floor(x 2^32 / L)). Differences then wrap modulo 2^32 exactly as minimum
+// images wrap modulo L, and |min-image dx| <= R implies |x'_i - x'_j| < R' with
+// R' = ceil(R 2^32 / L) + 2. The test per axis is one add and one unsigned compare:
+// (x'_i + R') - x'_j < 2 R'. Pairs that pass take the exact path: integer minimum
+// image on the true grid coordinates, exact 64-bit squared distance, bin from the
+// threshold table. Counts go to a per-CTA shared-memory histogram (32-bit) and are
+// flushed to the caller's 64-bit histogram with one atomic per non-empty bin.
+#include "epsr_device.cuh"
+#include "epsr_internal.h"
+
+namespace epsr {
+
+constexpr int kGrThreads = 256;
+constexpr int kGrR = kGrTile / kGrThreads;   // i-atoms per thread
+
+__global__ void scale_coords_kernel(const BoxDev *boxes, const int *atom_box, const int4 *coords,
+                                    uint4 *scaled, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int4 c = coords[i];
+        const unsigned long long L = (unsigned long long)boxes[atom_box[i]].L;
+        uint4 s;
+        s.x = (unsigned)(((unsigned long long)c.x << 32) / L);
+        s.y = (unsigned)(((unsigned long long)c.y << 32) / L);
+        s.z = (unsigned)(((unsigned long long)c.z << 32) / L);
+        s.w = (unsigned)c.w;
+        scaled[i] = s;
+    }
+}
+
+int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *coords,
+                        uint4 *scaled, long long n, cudaStream_t stream)
+{
+    if (n == 0) return EPSR_OK;
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    scale_coords_kernel<<<grid, 256, 0, stream>>>(boxes, atom_box, coords, scaled, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "scale_coords");
+}
+
+__device__ __forceinline__ void flush_hist(unsigned *sh_hist, int n, unsigned long long *out)
+{
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const unsigned v = sh_hist[k];
+        if (v) {
+            atomicAdd(out + k, (unsigned long long)v);
+            sh_hist[k] = 0u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kGrThreads, 2) partial_gr_kernel(GrArgs A)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    uint4 *s_scaled = reinterpret_cast<uint4 *>(dyn);
+    int4 *s_true = reinterpret_cast<int4 *>(s_scaled + kGrTile);
+    long long *s_T = reinterpret_cast<long long *>(s_true + kGrTile);
+    unsigned *s_hist = reinterpret_cast<unsigned *>(s_T + A.max_bins1);
+    __shared__ BoxDev bx;
+    __shared__ int cur_box;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) cur_box = -1;
+    for (int k = tid; k < A.max_pairs_bins; k += kGrThreads) s_hist[k] = 0u;
+    __syncthreads();
+
+    for (long long w = A.tile_begin + blockIdx.x; w < A.tile_end; w += gridDim.x) {
+        const GrTile tl = A.tiles[w];
+        __syncthreads();   // the previous tile's counting is complete before any flush
+        if (tl.box != cur_box) {
+            // flush the previous box's counts, then load this box's parameters and table
+            if (cur_box >= 0) {
+                const BoxDev &pb = bx;
+                flush_hist(s_hist, pb.n_pairs * pb.n_bins, A.hist + pb.hist_off);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                bx = A.boxes[tl.box];
+                cur_box = tl.box;
+            }
+            __syncthreads();
+            for (int k = tid; k <= bx.n_bins; k += kGrThreads) s_T[k] = A.thresholds[bx.tbl_off + k];
+        }
+        const int L = bx.L;
+        const int N = bx.n_atoms;
+        const unsigned R = bx.pre_r, R2 = 2u * bx.pre_r;
+        const long long tmax = bx.tmax;
+        const int nb = bx.n_bins, nt = bx.n_types;
+        const float inv = bx.inv_dr_fx;
+        // stage the j-tile
+        const int j0 = tl.tj * kGrTile;
+        const int nj = min(kGrTile, N - j0);
+        __syncthreads();
+        for (int j = tid; j < nj; j += kGrThreads) {
+            s_scaled[j] = A.scaled[bx.atom0 + j0 + j];
+            s_true[j] = A.coords[bx.atom0 + j0 + j];
+        }
+        // i-atoms in registers: thread t holds tile rows t, t + 256, ...
+        const int i0 = tl.ti * kGrTile;
+        uint32_t xi[kGrR], yi[kGrR], zi[kGrR];
+        int il[kGrR];
+#pragma unroll
+        for (int r = 0; r < kGrR; ++r) {
+            il[r] = tid + r * kGrThreads;
+            const int ig = i0 + il[r];
+            if (ig < N) {
+                const uint4 s = A.scaled[bx.atom0 + ig];
+                xi[r] = s.x + R; yi[r] = s.y + R; zi[r] = s.z + R;
+            } else {
+                il[r] = -1;
+                xi[r] = yi[r] = zi[r] = 0u;
+            }
+        }
+        const bool diag = tl.ti == tl.tj;
+        __syncthreads();
+        for (int j = 0; j < nj; ++j) {
+            const uint4 sj = s_scaled[j];
+#pragma unroll
+            for (int r = 0; r < kGrR; ++r) {
+                const bool hit = (xi[r] - sj.x < R2) & (yi[r] - sj.y < R2) & (zi[r] - sj.z < R2);
+                if (hit) {
+                    if (il[r] < 0 || (diag && j <= il[r])) continue;
+                    const int4 pi = A.coords[bx.atom0 + i0 + il[r]];
+                    const int4 pj = s_true[j];
+                    const long long d2 = dist2(pi, pj, L);
+                    if (d2 < tmax) {
+                        const int k = bin_of(d2, s_T, nb, inv);
+                        const int p = pair_index(pi.w, pj.w, nt);
+                        atomicAdd(&s_hist[p * nb + k], 1u);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (cur_box >= 0) flush_hist(s_hist, bx.n_pairs * bx.n_bins, A.hist + bx.hist_off);
+}
+
+int launch_partial_gr(const GrArgs &args, int grid, cudaStream_t stream)
+{
+    if (args.tile_end <= args.tile_begin) return EPSR_OK;
+    const size_t smem = (size_t)kGrTile * (sizeof(uint4) + sizeof(int4)) +
+                        (size_t)args.max_bins1 * sizeof(long long) +
+                        (size_t)args.max_pairs_bins * sizeof(unsigned);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(partial_gr_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(gr)");
+        attr_set = true;
+    }
+    if (smem > 200 * 1024)
+        return set_error(EPSR_EINVAL, "partial_gr: n_pairs*n_bins too large for shared memory");
+    partial_gr_kernel<<<grid, kGrThreads, smem, stream>>>(args);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "partial_gr launch");
+}
+
+// g_ab(k) = H V / (n_configs P_ab (4 pi / 3)(r_{k+1}^3 - r_k^3)), r_k = k dr.
+__global__ void normalize_g_kernel(const BoxDev *boxes, int n_boxes, const unsigned long long *hist,
+                                   float *g, double inv_configs, long long hist_len,
+                                   const long long *hist_box)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hist_len;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_boxes;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (hist_box[mid] <= i) lo = mid; else hi = mid;
+        }
+        const BoxDev &b = boxes[lo];
+        const long long e = i - b.hist_off;
+        const int p = (int)(e / b.n_bins), k = (int)(e % b.n_bins);
+        int a = 0, rem = p;                      // pair index p -> types (a, c), a <= c
+        while (rem >= b.n_types - a) { rem -= b.n_types - a; ++a; }
+        const int c = a + rem;
+        const double Pab = a == c ? 0.5 * (double)b.count[a] * (double)(b.count[a] - 1)
+                                  : (double)b.count[a] * (double)b.count[c];
+        const double r0 = (double)k * b.dr_A, r1 = (double)(k + 1) * b.dr_A;
+        const double shell = 4.18879020478639098462 * (r1 * r1 * r1 - r0 * r0 * r0);
+        const double denom = Pab * shell;
+        g[i] = denom > 0.0 ? (float)((double)hist[i] * b.volume * inv_configs / denom) : 0.f;
+    }
+}
+
+int launch_normalize_g(const BoxDev *boxes, int n_boxes, const unsigned long long *hist,
+                       float *g, long long n_configs, long long hist_len, const long long *hist_box,
+                       cudaStream_t stream)
+{
+    if (hist_len == 0) return EPSR_OK;
+    const int grid = (int)((hist_len + 255) / 256 < 2048 ? (hist_len + 255) / 256 : 2048);
+    normalize_g_kernel<<<grid, 256, 0, stream>>>(boxes, n_boxes, hist, g, 1.0 / (double)n_configs,
+                                                 hist_len, hist_box);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "normalize_g");
+}
+
+// ---- total potential energy: pairs i < j in different molecules -----------------------------
+constexpr int kUThreads = 256;
+constexpr int kUR = kGrTile / kUThreads;
+
+__global__ void __launch_bounds__(kUThreads, 2)
+total_energy_kernel(const BoxDev *boxes, const int4 *coords, const int *atom_mol,
+                    const long long *thresholds, const float *ep_all, const GrTile *tiles,
+                    long long n_tiles, double *U)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    int4 *s_j = reinterpret_cast<int4 *>(dyn);
+    int *s_mol = reinterpret_cast<int *>(s_j + kGrTile);
+    long long *s_T = reinterpret_cast<long long *>(s_mol + kGrTile);
+    __shared__ BoxDev bx;
+    __shared__ int cur_box;
+    __shared__ double s_red[kUThreads / 32];
+    const int tid = threadIdx.x;
+    if (tid == 0) cur_box = -1;
+    __syncthreads();
+    for (long long w = blockIdx.x; w < n_tiles; w += gridDim.x) {
+        const GrTile tl = tiles[w];
+        __syncthreads();
+        if (tl.box != cur_box) {
+            if (tid == 0) { bx = boxes[tl.box]; cur_box = tl.box; }
+            __syncthreads();
+            for (int k = tid; k <= bx.n_bins; k += kUThreads) s_T[k] = thresholds[bx.tbl_off + k];
+        }
+        const float *ep = ep_all + bx.ep_off;
+        const int L = bx.L, N = bx.n_atoms;
+        const int j0 = tl.tj * kGrTile, nj = min(kGrTile, N - j0);
+        for (int j = tid; j < nj; j += kUThreads) {
+            s_j[j] = coords[bx.atom0 + j0 + j];
+            s_mol[j] = atom_mol[bx.atom0 + j0 + j];
+        }
+        const int i0 = tl.ti * kGrTile;
+        int4 pi[kUR];
+        int mi[kUR], il[kUR];
+#pragma unroll
+        for (int r = 0; r < kUR; ++r) {
+            il[r] = tid + r * kUThreads;
+            if (i0 + il[r] < N) {
+                pi[r] = coords[bx.atom0 + i0 + il[r]];
+                mi[r] = atom_mol[bx.atom0 + i0 + il[r]];
+            } else {
+                il[r] = -1;
+                pi[r] = make_int4(0, 0, 0, 0);
+                mi[r] = -1;
+            }
+        }
+        const bool diag = tl.ti == tl.tj;
+        __syncthreads();
+        float acc = 0.f;
+        for (int j = 0; j < nj; ++j) {
+            const int4 pj = s_j[j];
+            const int mj = s_mol[j];
+#pragma unroll
+            for (int r = 0; r < kUR; ++r) {
+                if (il[r] < 0 || mi[r] == mj || (diag && j <= il[r])) continue;
+                const PairRow pr = bx.row[pi[r].w * kMaxTypes + pj.w];
+                acc += pair_u(dist2(pi[r], pj, L), pr, bx, s_T, ep);
+            }
+        }
+        double v = (double)acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int i = 0; i < kUThreads / 32; ++i) t += s_red[i];
+            atomicAdd(&U[tl.box], t);
+        }
+    }
+}
+
+int launch_total_energy(const BoxDev *boxes, const int4 *coords, const int *atom_mol,
+                        const long long *thresholds, const float *ep, const GrTile *tiles,
+                        long long n_tiles, double *U, int grid, cudaStream_t stream)
+{
+    const size_t smem = (size_t)kGrTile * (sizeof(int4) + sizeof(int)) +
+                        (size_t)(EPSR_MAX_BINS + 1) * sizeof(long long);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(total_energy_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(U)");
+        attr_set = true;
+    }
+    total_energy_kernel<<<grid, kUThreads, smem, stream>>>(boxes, coords, atom_mol, thresholds, ep,
+                                                           tiles, n_tiles, U);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "total_energy launch");
+}
+
+}  // namespace epsr

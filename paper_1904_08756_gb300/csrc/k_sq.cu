@@ -1,0 +1,112 @@
+// k_sq.cu -- S(Q) by Eq. (1) as a contraction of the sine-transform matrix
+// K[i][k] = r_k^2 dr sin(Q_i r_k) / (Q_i r_k) (midpoint rule, r_k = (k + 1/2) dr) with the
+// weighted columns G[c][k] = w_c (g_c(k) - 1).
+//
+// FP32 path (this file): K is built once per plan in FP64 and stored transposed,
+// K_t[k][i], so that a warp reading one k row reads 32 consecutive Q values; the G
+// columns of a block are staged in shared memory and each thread accumulates
+// S_partial[c][i] for its Q value with compensated (Kahan) FP32 summation.
+#include "epsr_device.cuh"
+#include "epsr_internal.h"
+#include "k_sq.h"
+
+namespace epsr {
+
+__global__ void build_sine_matrix_kernel(const float *Q, int nQ, int n_bins, double dr, float *Kt)
+{
+    const long long n = (long long)nQ * n_bins;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / nQ), i = (int)(e % nQ);
+        const double r = ((double)k + 0.5) * dr;
+        const double x = (double)Q[i] * r;
+        Kt[e] = (float)(r * r * dr * sin(x) / x);
+    }
+}
+
+int sq_build_kt(const float *Q_dev, int nQ, int n_bins, double dr, float *Kt, cudaStream_t stream)
+{
+    const long long n = (long long)nQ * n_bins;
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    build_sine_matrix_kernel<<<grid, 256, 0, stream>>>(Q_dev, nQ, n_bins, dr, Kt);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "build_sine_matrix");
+}
+
+constexpr int kSqThreads = 128;
+constexpr int kSqCols = 8;     // columns per block
+
+// S_partial[c][i] = w_c sum_k K_t[k][i] (g[c][k] - 1) for c in [c0, c0 + kSqCols).
+__global__ void __launch_bounds__(kSqThreads) sq_fp32_kernel(SqArgs A)
+{
+    extern __shared__ float s_g[];      // [kSqCols][n_bins] of (g - 1)
+    const int c0 = blockIdx.y * kSqCols;
+    const int nc = min(kSqCols, A.n_cols - c0);
+    const int nb = A.n_bins;
+    for (int e = threadIdx.x; e < nc * nb; e += kSqThreads)
+        s_g[e] = A.g[(long long)(c0 + e / nb) * nb + e % nb] - 1.0f;
+    __syncthreads();
+    const int i = blockIdx.x * kSqThreads + threadIdx.x;
+    if (i >= A.nQ) return;
+    float sum[kSqCols], comp[kSqCols];
+#pragma unroll
+    for (int c = 0; c < kSqCols; ++c) sum[c] = comp[c] = 0.f;
+    for (int k = 0; k < nb; ++k) {
+        const float kv = A.Kt[(long long)k * A.nQ + i];
+#pragma unroll
+        for (int c = 0; c < kSqCols; ++c) {
+            if (c < nc) {
+                const float y = kv * s_g[c * nb + k] - comp[c];
+                const float t = sum[c] + y;
+                comp[c] = (t - sum[c]) - y;
+                sum[c] = t;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kSqCols; ++c)
+        if (c < nc) A.S_partial[(long long)(c0 + c) * A.nQ + i] = (float)((double)sum[c] * A.w[c0 + c]);
+}
+
+// S_total[s][i] = flat[s] + sum over the set's columns (in column order, FP64).
+__global__ void sq_total_kernel(const float *S_partial, int n_sets, int cols_per_set, int nQ,
+                                SqWeights W, float *S_total)
+{
+    const long long n = (long long)n_sets * nQ;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / nQ), i = (int)(e % nQ);
+        double t = W.flat[s];
+        for (int c = 0; c < cols_per_set; ++c)
+            t += (double)S_partial[(long long)(s * cols_per_set + c) * nQ + i];
+        S_total[e] = (float)t;
+    }
+}
+
+int sq_exec_fp32(const SqArgs &A, cudaStream_t stream)
+{
+    dim3 grid((A.nQ + kSqThreads - 1) / kSqThreads, (A.n_cols + kSqCols - 1) / kSqCols);
+    const size_t smem = (size_t)kSqCols * A.n_bins * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sq_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kSqCols * EPSR_MAX_BINS * sizeof(float)));
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(sq)");
+        attr = true;
+    }
+    sq_fp32_kernel<<<grid, kSqThreads, smem, stream>>>(A);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_fp32");
+}
+
+int sq_totals(const float *S_partial, int n_sets, int cols_per_set, int nQ, const SqWeights &W,
+              float *S_total, cudaStream_t stream)
+{
+    const long long n = (long long)n_sets * nQ;
+    const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    sq_total_kernel<<<grid, 256, 0, stream>>>(S_partial, n_sets, cols_per_set, nQ, W, S_total);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_total");
+}
+
+}  // namespace epsr

@@ -1,0 +1,333 @@
+"""Python binding of libepsr (ctypes): argument marshalling only.
+
+Every function here has the name of the C entry point it calls (include/epsr.h) and
+takes torch tensors for device buffers (passed as raw pointers) and NumPy arrays or
+Python numbers for host data. All computation happens in the CUDA library; there is no
+CPU fallback: if libepsr.so is missing or CUDA is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libepsr.so")
+
+EPSR_OK, EPSR_EINVAL, EPSR_ENOMEM, EPSR_ECUDA, EPSR_ELAUNCH, EPSR_ETIMEOUT, EPSR_ENUMERIC = range(7)
+MAX_TYPES = 8
+MAX_MOL_ATOMS = 8
+MOVE_ATOM, MOVE_RIGID_MOLECULE = 0, 1
+SQ_FP32, SQ_TF32X3, SQ_BF16X3, SQ_BF16X6 = 0, 1, 2, 3
+
+# Every symbol include/epsr.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "epsr_strerror", "epsr_last_error_detail", "epsr_version",
+    "epsr_box_create", "epsr_batch_create", "epsr_box_destroy", "epsr_box_info",
+    "epsr_box_offsets", "epsr_box_get_coords", "epsr_box_set_coords",
+    "epsr_box_set_coords_device", "epsr_box_get_coords_device", "epsr_box_set_ep",
+    "epsr_box_get_ep", "epsr_box_total_energy", "epsr_mc_sweep", "epsr_mc_stats_get",
+    "epsr_mc_set_batch", "epsr_mc_set_ctas", "epsr_debug_barrier_fault",
+    "epsr_partial_gr", "epsr_partial_gr_tiles", "epsr_partial_gr_range", "epsr_normalize_g",
+    "epsr_sq_weights", "epsr_sq_plan_create", "epsr_sq_plan_destroy", "epsr_sq_exec", "epsr_sq",
+]
+
+
+class BoxDesc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("n_mol", C.c_int64), ("L_fx", C.c_int64),
+                ("scale_log2", C.c_int32), ("n_types", C.c_int32),
+                ("q", C.c_double * MAX_TYPES), ("sigma", C.c_double * MAX_TYPES),
+                ("eps", C.c_double * MAX_TYPES), ("b", C.c_double * MAX_TYPES),
+                ("r_coul", C.c_double), ("bin_p", C.c_int32), ("bin_q", C.c_int32),
+                ("n_bins", C.c_int32), ("move_kind", C.c_int32), ("temperature", C.c_double),
+                ("max_translation", C.c_double), ("max_rotation_deg", C.c_double)]
+
+
+class McStats(C.Structure):
+    _fields_ = [("attempted", C.c_int64), ("accepted", C.c_int64), ("nonfinite", C.c_int64),
+                ("sum_dU", C.c_double)]
+
+
+MOVE_LOG_DTYPE = np.dtype([("mol", np.int32), ("accepted", np.int32), ("dU", np.float32),
+                           ("n_atoms", np.int32), ("u_acc", np.float64),
+                           ("trial", np.int32, (MAX_MOL_ATOMS, 3)), ("pad", np.int32, (2,))])
+assert MOVE_LOG_DTYPE.itemsize == 128
+
+
+class EpsrError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail or 'error'} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libepsr.so (built in-tree by __graft_entry__.build or build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libepsr.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        P = C.POINTER
+        sig = {
+            "epsr_strerror": ([C.c_int], C.c_char_p),
+            "epsr_last_error_detail": ([C.c_char_p, C.c_size_t], C.c_int),
+            "epsr_version": ([], C.c_int),
+            "epsr_box_create": ([P(BoxDesc), vp, vp, vp, vp, P(vp)], C.c_int),
+            "epsr_batch_create": ([P(BoxDesc), i32, vp, vp, vp, vp, P(vp)], C.c_int),
+            "epsr_box_destroy": ([vp], C.c_int),
+            "epsr_box_info": ([vp, P(i32), P(i64), P(i64)], C.c_int),
+            "epsr_box_offsets": ([vp, i32, P(i64), P(i64)], C.c_int),
+            "epsr_box_get_coords": ([vp, vp, vp], C.c_int),
+            "epsr_box_set_coords": ([vp, vp, vp], C.c_int),
+            "epsr_box_set_coords_device": ([vp, vp, vp], C.c_int),
+            "epsr_box_get_coords_device": ([vp, vp, vp], C.c_int),
+            "epsr_box_set_ep": ([vp, i32, vp, vp], C.c_int),
+            "epsr_box_get_ep": ([vp, i32, vp, vp], C.c_int),
+            "epsr_box_total_energy": ([vp, vp, vp], C.c_int),
+            "epsr_mc_sweep": ([vp, i64, u64, u64, vp, vp, vp], C.c_int),
+            "epsr_mc_stats_get": ([vp, vp, vp], C.c_int),
+            "epsr_mc_set_batch": ([vp, i32], C.c_int),
+            "epsr_mc_set_ctas": ([vp, i32], C.c_int),
+            "epsr_debug_barrier_fault": ([vp, i32, dbl], C.c_int),
+            "epsr_partial_gr": ([vp, vp, vp, i64, vp], C.c_int),
+            "epsr_partial_gr_tiles": ([vp, P(i64)], C.c_int),
+            "epsr_partial_gr_range": ([vp, i64, i64, vp, vp], C.c_int),
+            "epsr_normalize_g": ([vp, vp, vp, i64, vp], C.c_int),
+            "epsr_sq_weights": ([vp, i32, vp, vp], C.c_int),
+            "epsr_sq_plan_create": ([vp, i32, i32, dbl, i32, i32, vp, P(vp)], C.c_int),
+            "epsr_sq_plan_destroy": ([vp], C.c_int),
+            "epsr_sq_exec": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], C.c_int),
+            "epsr_sq": ([vp, i32, i32, dbl, vp, i32, vp, i32, vp, vp, vp, i32, vp], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != EPSR_OK:
+        buf = C.create_string_buffer(512)
+        lib().epsr_last_error_detail(buf, 512)
+        raise EpsrError(status, where, buf.value.decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def box_desc(system) -> BoxDesc:
+    """epsr_box_desc of a synth.System (plain field copy)."""
+    d = BoxDesc()
+    d.n_atoms = system.n_atoms
+    d.n_mol = system.n_mol
+    d.L_fx = system.L_fx
+    d.scale_log2 = 20
+    d.n_types = system.n_types
+    for i in range(system.n_types):
+        d.q[i], d.sigma[i], d.eps[i], d.b[i] = (system.q[i], system.sigma[i], system.eps[i],
+                                                system.b[i])
+    d.r_coul = system.r_coul
+    d.bin_p, d.bin_q, d.n_bins = system.bin_p, system.bin_q, system.n_bins
+    d.move_kind = MOVE_RIGID_MOLECULE if system.rigid_molecules else MOVE_ATOM
+    d.temperature = system.temperature
+    d.max_translation = system.max_translation
+    d.max_rotation_deg = system.max_rotation_deg
+    return d
+
+
+def epsr_strerror(status: int) -> str:
+    return lib().epsr_strerror(status).decode()
+
+
+def epsr_version() -> int:
+    return lib().epsr_version()
+
+
+class Box:
+    """Owner of an epsr_box handle (one box or a batch of replicas)."""
+
+    def __init__(self, systems, stream=None):
+        systems = systems if isinstance(systems, (list, tuple)) else [systems]
+        self.systems = list(systems)
+        descs = (BoxDesc * len(systems))(*[box_desc(s) for s in systems])
+        xyz = np.ascontiguousarray(np.concatenate([s.xyz for s in systems]), np.int32)
+        typ = np.ascontiguousarray(np.concatenate([s.type for s in systems]), np.int32)
+        ms = np.ascontiguousarray(np.concatenate([s.mol_start for s in systems]), np.int64)
+        h = C.c_void_p()
+        if len(systems) == 1:
+            st = lib().epsr_box_create(descs, _np_ptr(xyz), _np_ptr(typ), _np_ptr(ms),
+                                       _stream(stream), C.byref(h))
+            _check(st, "epsr_box_create")
+        else:
+            st = lib().epsr_batch_create(descs, len(systems), _np_ptr(xyz), _np_ptr(typ),
+                                         _np_ptr(ms), _stream(stream), C.byref(h))
+            _check(st, "epsr_batch_create")
+        self.h = h
+        nb, na, hl = C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().epsr_box_info(h, C.byref(nb), C.byref(na), C.byref(hl)), "epsr_box_info")
+        self.n_boxes, self.n_atoms, self.hist_len = nb.value, na.value, hl.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().epsr_box_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout ------------------------------------------------------------------------
+    def epsr_box_offsets(self, b: int):
+        ho, ao = C.c_int64(), C.c_int64()
+        _check(lib().epsr_box_offsets(self.h, b, C.byref(ho), C.byref(ao)), "epsr_box_offsets")
+        return ho.value, ao.value
+
+    # -- coordinates and tables ------------------------------------------------------------
+    def epsr_box_get_coords(self, stream=None) -> np.ndarray:
+        out = np.zeros((self.n_atoms, 3), np.int32)
+        _check(lib().epsr_box_get_coords(self.h, _np_ptr(out), _stream(stream)), "epsr_box_get_coords")
+        return out
+
+    def epsr_box_set_coords(self, xyz: np.ndarray, stream=None):
+        x = np.ascontiguousarray(xyz, np.int32)
+        _check(lib().epsr_box_set_coords(self.h, _np_ptr(x), _stream(stream)), "epsr_box_set_coords")
+
+    def epsr_box_set_coords_device(self, xyz_dev, stream=None):
+        _check(lib().epsr_box_set_coords_device(self.h, _dev_ptr(xyz_dev), _stream(stream)),
+               "epsr_box_set_coords_device")
+
+    def epsr_box_get_coords_device(self, xyz_dev, stream=None):
+        _check(lib().epsr_box_get_coords_device(self.h, _dev_ptr(xyz_dev), _stream(stream)),
+               "epsr_box_get_coords_device")
+
+    def epsr_box_set_ep(self, b: int, ep: np.ndarray, stream=None):
+        e = np.ascontiguousarray(ep, np.float32)
+        _check(lib().epsr_box_set_ep(self.h, b, _np_ptr(e), _stream(stream)), "epsr_box_set_ep")
+
+    def epsr_box_get_ep(self, b: int, shape, stream=None) -> np.ndarray:
+        e = np.zeros(shape, np.float32)
+        _check(lib().epsr_box_get_ep(self.h, b, _np_ptr(e), _stream(stream)), "epsr_box_get_ep")
+        return e
+
+    def epsr_box_total_energy(self, stream=None) -> np.ndarray:
+        U = np.zeros(self.n_boxes, np.float64)
+        _check(lib().epsr_box_total_energy(self.h, _np_ptr(U), _stream(stream)),
+               "epsr_box_total_energy")
+        return U
+
+    # -- Monte Carlo ----------------------------------------------------------------------------
+    def epsr_mc_sweep(self, n_moves: int, seed: int, move0: int = 0, log=None, stream=None):
+        stats = (McStats * self.n_boxes)()
+        _check(lib().epsr_mc_sweep(self.h, n_moves, seed, move0, stats, _dev_ptr(log),
+                                   _stream(stream)), "epsr_mc_sweep")
+        return [(s.attempted, s.accepted, s.nonfinite, s.sum_dU) for s in stats]
+
+    def epsr_mc_stats_get(self, stream=None):
+        stats = (McStats * self.n_boxes)()
+        _check(lib().epsr_mc_stats_get(self.h, stats, _stream(stream)), "epsr_mc_stats_get")
+        return [(s.attempted, s.accepted, s.nonfinite, s.sum_dU) for s in stats]
+
+    def epsr_mc_set_batch(self, k: int):
+        _check(lib().epsr_mc_set_batch(self.h, k), "epsr_mc_set_batch")
+
+    def epsr_mc_set_ctas(self, n: int):
+        _check(lib().epsr_mc_set_ctas(self.h, n), "epsr_mc_set_ctas")
+
+    def epsr_debug_barrier_fault(self, cta: int, timeout_ms: float):
+        _check(lib().epsr_debug_barrier_fault(self.h, cta, timeout_ms), "epsr_debug_barrier_fault")
+
+    # -- histograms -------------------------------------------------------------------------------
+    def epsr_partial_gr(self, hist, g=None, n_configs: int = 1, stream=None):
+        _check(lib().epsr_partial_gr(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
+                                     _stream(stream)), "epsr_partial_gr")
+
+    def epsr_partial_gr_tiles(self) -> int:
+        n = C.c_int64()
+        _check(lib().epsr_partial_gr_tiles(self.h, C.byref(n)), "epsr_partial_gr_tiles")
+        return n.value
+
+    def epsr_partial_gr_range(self, t0: int, t1: int, hist, stream=None):
+        _check(lib().epsr_partial_gr_range(self.h, t0, t1, _dev_ptr(hist), _stream(stream)),
+               "epsr_partial_gr_range")
+
+    def epsr_normalize_g(self, hist, g, n_configs: int = 1, stream=None):
+        _check(lib().epsr_normalize_g(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
+                                      _stream(stream)), "epsr_normalize_g")
+
+    def epsr_sq_weights(self, b: int):
+        P = self.systems[b].n_types * (self.systems[b].n_types + 1) // 2
+        w = np.zeros(P, np.float64)
+        flat = np.zeros(1, np.float64)
+        _check(lib().epsr_sq_weights(self.h, b, _np_ptr(w), _np_ptr(flat)), "epsr_sq_weights")
+        return w, float(flat[0])
+
+
+class SqPlan:
+    """Owner of an epsr_sq_plan (cached sine-transform matrix for one Q grid)."""
+
+    def __init__(self, Q: np.ndarray, n_bins: int, dr: float, mode: int = SQ_FP32,
+                 max_cols: int = 64, stream=None):
+        q = np.ascontiguousarray(Q, np.float32)
+        h = C.c_void_p()
+        _check(lib().epsr_sq_plan_create(_np_ptr(q), len(q), n_bins, dr, mode, max_cols,
+                                         _stream(stream), C.byref(h)), "epsr_sq_plan_create")
+        self.h, self.nQ, self.n_bins, self.mode = h, len(q), n_bins, mode
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().epsr_sq_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def epsr_sq_exec(self, g, w: np.ndarray, cols_per_set: int, flat: np.ndarray,
+                     S_partial=None, S_total=None, stream=None):
+        w = np.ascontiguousarray(w, np.float64)
+        flat = np.ascontiguousarray(np.atleast_1d(flat), np.float64)
+        n_cols = g.shape[0]
+        _check(lib().epsr_sq_exec(self.h, _dev_ptr(g), n_cols, _np_ptr(w), cols_per_set,
+                                  _np_ptr(flat), _dev_ptr(S_partial), _dev_ptr(S_total),
+                                  _stream(stream)), "epsr_sq_exec")
+
+
+def epsr_sq(g, dr: float, Q: np.ndarray, w: np.ndarray, cols_per_set: int, flat: np.ndarray,
+            S_partial=None, S_total=None, mode: int = SQ_FP32, stream=None):
+    q = np.ascontiguousarray(Q, np.float32)
+    w = np.ascontiguousarray(w, np.float64)
+    flat = np.ascontiguousarray(np.atleast_1d(flat), np.float64)
+    _check(lib().epsr_sq(_dev_ptr(g), g.shape[0], g.shape[1], dr, _np_ptr(q), len(q), _np_ptr(w),
+                         cols_per_set, _np_ptr(flat), _dev_ptr(S_partial), _dev_ptr(S_total),
+                         mode, _stream(stream)), "epsr_sq")

@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol include/epsr.h
+declares, and rejects bad arguments on the host before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1904_08756_gb300 import epsr, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "epsr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(epsr_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_08756_gb300 import build
+    build.build()
+    return epsr.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(epsr.EXPORTS) == names
+
+
+def test_status_strings(lib):
+    assert epsr.epsr_strerror(0) == "success"
+    assert "timed out" in epsr.epsr_strerror(epsr.EPSR_ETIMEOUT)
+    assert epsr.epsr_version() >= 10000
+
+
+def _create(lib, desc, xyz, typ, ms):
+    h = C.c_void_p()
+    st = lib.epsr_box_create(C.byref(desc), xyz.ctypes.data, typ.ctypes.data, ms.ctypes.data,
+                             None, C.byref(h))
+    return st, h
+
+
+def test_create_rejects_bad_input_on_host(lib):
+    s = synth.water_box(10, seed=1, L_A=10.0)
+    xyz = np.ascontiguousarray(s.xyz, np.int32)
+    typ = np.ascontiguousarray(s.type, np.int32)
+    ms = np.ascontiguousarray(s.mol_start, np.int64)
+    bad = []
+    d = epsr.box_desc(s); d.n_types = 0; bad.append((d, xyz, typ, ms))
+    d = epsr.box_desc(s); d.n_bins = 0; bad.append((d, xyz, typ, ms))
+    d = epsr.box_desc(s); d.move_kind = 7; bad.append((d, xyz, typ, ms))
+    d = epsr.box_desc(s); d.temperature = -1; bad.append((d, xyz, typ, ms))
+    d = epsr.box_desc(s); bad.append((d, xyz, typ + 5, ms))               # type out of range
+    x2 = xyz.copy(); x2[3, 1] = s.L_fx; bad.append((epsr.box_desc(s), x2, typ, ms))
+    m2 = ms.copy(); m2[2] = m2[1]; bad.append((epsr.box_desc(s), xyz, typ, m2))
+    d = epsr.box_desc(s); d.move_kind = epsr.MOVE_ATOM; bad.append((d, xyz, typ, ms))
+    for d, x, t, m in bad:
+        st, h = _create(lib, d, x, t, m)
+        assert st == epsr.EPSR_EINVAL and not h.value
+        buf = C.create_string_buffer(256)
+        assert lib.epsr_last_error_detail(buf, 256) == epsr.EPSR_EINVAL
+        assert len(buf.value) > 0
+
+
+def test_null_handles_are_rejected(lib):
+    n = C.c_int64()
+    assert lib.epsr_box_info(None, None, C.byref(n), None) == epsr.EPSR_EINVAL
+    assert lib.epsr_box_destroy(None) == epsr.EPSR_OK
+    assert lib.epsr_mc_set_batch(None, 4) == epsr.EPSR_EINVAL
+    assert lib.epsr_sq_plan_destroy(None) == epsr.EPSR_OK

@@ -1,0 +1,271 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: histograms bit-exact; MC trial coordinates bit-exact and dU within 1e-5 of the
+condition scale C = sum |u(r') - u(r)| (FP32 against FP64; decisions may differ only
+inside that band and are then replayed with the GPU's choice, after which final
+coordinates are bit-exact); g(r) to FP32 rounding; S(Q) within 1e-4 barn.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_08756_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1904_08756_gb300 import epsr  # noqa: E402
+
+DEV = torch.device("cuda:0")
+DU_REL = 1e-5          # of the condition scale C
+DU_ABS = 1e-4          # kJ/mol floor for moves whose C is tiny
+
+
+def gpu_hist(box: epsr.Box, n_repeat: int = 1):
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    for _ in range(n_repeat):
+        box.epsr_partial_gr(H)
+    torch.cuda.synchronize()
+    return H.cpu().numpy().astype(np.uint64)
+
+
+# --------------------------------------------------------------------------------------
+# pair histograms: bit-exact
+# --------------------------------------------------------------------------------------
+
+def test_histogram_bit_exact_small_water(small_water):
+    box = epsr.Box(small_water)
+    H = gpu_hist(box).reshape(3, small_water.n_bins)
+    ref = oracle.Box(small_water).histogram()
+    assert np.array_equal(H, ref)
+
+
+@pytest.mark.parametrize("n,L,types", [(1, 5.0, 1), (2, 5.0, 2), (1023, 14.0, 2),
+                                       (1025, 14.0, 3), (2500, 19.0, 2), (3073, 20.0, 4)])
+def test_histogram_bit_exact_ragged_tiles(n, L, types):
+    s = synth.uniform_gas(n, L, seed=n, n_types=types)
+    s.bin_p, s.bin_q, s.n_bins = 1, 25, 200      # 0.04 A bins to 8 A (beyond L/2 for some)
+    H = gpu_hist(epsr.Box(s)).reshape(-1, 200)
+    assert np.array_equal(H, oracle.Box(s).histogram(threads=8))
+
+
+def test_histogram_lattice_closed_form():
+    S = 1 << 20
+    s = synth.lattice_box(8, S, n_bins=80, bin_p=1, bin_q=20)
+    H = gpu_hist(epsr.Box(s))
+    assert np.array_equal(H, oracle.Box(s).histogram()[0])
+
+
+def test_histogram_accumulates_and_translation_invariant(small_water):
+    box = epsr.Box(small_water)
+    H2 = gpu_hist(box, n_repeat=2)
+    shift = np.array([7777777, 1, small_water.L_fx - 3])
+    s2 = synth.System(**{**small_water.__dict__,
+                         "xyz": ((small_water.xyz.astype(np.int64) + shift) % small_water.L_fx)
+                         .astype(np.int32)})
+    H1 = gpu_hist(epsr.Box(s2))
+    assert np.array_equal(H2, 2 * H1)
+
+
+def test_histogram_tile_ranges_sum_to_full():
+    s = synth.water_box(1100, seed=41, L_A=32.0)
+    box = epsr.Box(s)
+    nt = box.epsr_partial_gr_tiles()
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    cut = nt // 2
+    box.epsr_partial_gr_range(0, cut, H)
+    box.epsr_partial_gr_range(cut, nt, H)
+    torch.cuda.synchronize()
+    assert np.array_equal(H.cpu().numpy().astype(np.uint64), gpu_hist(epsr.Box(s)))
+
+
+@pytest.mark.parametrize("which", ["water", "silica"])
+def test_histogram_bit_exact_paper_size(which):
+    s = synth.paper_water() if which == "water" else synth.paper_silica()
+    H = gpu_hist(epsr.Box(s)).reshape(3, s.n_bins)
+    ref = oracle.Box(s).histogram(threads=0)
+    assert np.array_equal(H, ref)
+
+
+def test_g_normalisation(small_water):
+    box = epsr.Box(small_water)
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    g = torch.zeros(box.hist_len, dtype=torch.float32, device=DEV)
+    box.epsr_partial_gr(H, g, 1)
+    box.epsr_partial_gr(H, g, 2)
+    torch.cuda.synchronize()
+    ob = oracle.Box(small_water)
+    ref = ob.normalize_g(H.cpu().numpy().astype(np.uint64).reshape(3, -1), 2)
+    assert np.allclose(g.cpu().numpy().reshape(3, -1), ref, rtol=2e-7, atol=0)
+
+
+# --------------------------------------------------------------------------------------
+# energies and MC replay
+# --------------------------------------------------------------------------------------
+
+def test_total_energy(small_water):
+    box = epsr.Box(small_water)
+    U = box.epsr_box_total_energy()[0]
+    ref = oracle.Box(small_water).total_energy()
+    assert abs(U - ref) <= 1e-5 * abs(ref)
+
+
+def run_logged(box: epsr.Box, n_moves: int, seed: int, move0: int = 0):
+    log = torch.zeros((box.n_boxes * n_moves * 128,), dtype=torch.uint8, device=DEV)
+    stats = box.epsr_mc_sweep(n_moves, seed, move0, log=log)
+    torch.cuda.synchronize()
+    return stats, log.cpu().numpy().view(epsr.MOVE_LOG_DTYPE).reshape(box.n_boxes, n_moves)
+
+
+def replay(system, start_xyz, log, seed, move0=0, box_index=0, check_every=1, ep=None):
+    """Replay a GPU move log on the oracle. Returns (n_checked, max_err_over_C, flips)."""
+    ob = oracle.Box(system, xyz=start_xyz, ep=ep)
+    kT = oracle.gas_constant() * system.temperature
+    worst, flips, checked = 0.0, 0, 0
+    for t, e in enumerate(log):
+        mol, trial, u = ob.propose(seed, move0 + t, box_index)
+        m = len(trial)
+        assert e["mol"] == mol and e["n_atoms"] == m, (t, e["mol"], mol)
+        assert np.array_equal(e["trial"][:m], trial), (t, e["trial"][:m], trial)
+        assert e["u_acc"] == u
+        if t % check_every == 0:
+            dU, C = ob.delta_u(mol, trial)
+            err = abs(float(e["dU"]) - dU)
+            tol = DU_REL * C + DU_ABS
+            assert err <= tol, (t, float(e["dU"]), dU, C)
+            worst = max(worst, err / max(C, 1e-30))
+            checked += 1
+            ref_acc = oracle.accept(dU, u, system.temperature)
+            if bool(e["accepted"]) != ref_acc:
+                flips += 1
+                assert abs(dU + kT * math.log(u)) <= tol, (t, dU, u)
+        if e["accepted"]:
+            ob.apply(mol, trial)
+    return ob, checked, worst, flips
+
+
+@pytest.mark.parametrize("batch", [16, 5, 1])
+def test_mc_replay_small_water(small_water, batch):
+    box = epsr.Box(small_water)
+    box.epsr_mc_set_batch(batch)
+    stats, log = run_logged(box, 2000, seed=12345)
+    att, acc, nonfin, sdu = stats[0]
+    assert att == 2000 and nonfin == 0 and 0 < acc < 2000
+    ob, checked, worst, flips = replay(small_water, small_water.xyz, log[0], 12345)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+    assert flips <= 2
+    assert abs(sdu - float(log[0]["dU"][log[0]["accepted"] == 1].astype(np.float64).sum())) < 1e-6 * max(1, abs(sdu))
+
+
+def test_mc_replay_multi_cta_water():
+    """A box split over several CTAs exercises the grid barrier and the gathered sums."""
+    s = synth.water_box(3000, seed=42, density=0.1)
+    box = epsr.Box(s)
+    box.epsr_mc_set_ctas(12)
+    stats, log = run_logged(box, 3000, seed=777, move0=100)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 777, move0=100, check_every=3)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
+def test_mc_replay_silica_atom_moves_with_ep():
+    s = synth.silica_box(700, seed=43)
+    rng = np.random.default_rng(1)
+    ep = (rng.normal(size=(3, s.n_bins)) * 0.3).astype(np.float32)
+    box = epsr.Box(s)
+    box.epsr_box_set_ep(0, ep)
+    box.epsr_mc_set_ctas(4)
+    stats, log = run_logged(box, 3000, seed=99)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 99, ep=ep.astype(np.float64))
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
+def test_mc_replay_paper_water_sampled():
+    """99,999-atom water on the full grid of CTAs: trial coordinates of every move
+    bit-exact, dU checked on a sample of moves, final coordinates bit-exact."""
+    s = synth.paper_water()
+    box = epsr.Box(s)
+    n = 4000
+    stats, log = run_logged(box, n, seed=2024)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 2024, check_every=40)
+    assert checked == n // 40
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
+def test_mc_batched_replicas_replay():
+    systems = [synth.water_box(400, seed=61), synth.silica_box(500, seed=62),
+               synth.water_box(900, seed=63, n_bins=600, bin_p=2, bin_q=100)]
+    box = epsr.Box(systems)
+    stats, log = run_logged(box, 1500, seed=5)
+    xyz = box.epsr_box_get_coords()
+    for b, s in enumerate(systems):
+        _, a0 = box.epsr_box_offsets(b)
+        ob, _, _, _ = replay(s, s.xyz, log[b], 5, box_index=b, check_every=5)
+        assert np.array_equal(xyz[a0:a0 + s.n_atoms], ob.xyz)
+
+
+def test_mc_energy_drift(small_water):
+    box = epsr.Box(small_water)
+    U0 = box.epsr_box_total_energy()[0]
+    stats = box.epsr_mc_sweep(5000, seed=3, move0=0)
+    U1 = box.epsr_box_total_energy()[0]
+    assert abs((U1 - U0) - stats[0][3]) < 1e-4 * abs(U0) + 1.0
+
+
+def test_mc_deterministic(small_water):
+    a = epsr.Box(small_water)
+    b = epsr.Box(small_water)
+    a.epsr_mc_sweep(1000, seed=8)
+    b.epsr_mc_sweep(600, seed=8)
+    b.epsr_mc_sweep(400, seed=8, move0=600)
+    assert np.array_equal(a.epsr_box_get_coords(), b.epsr_box_get_coords())
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    s = synth.water_box(2000, seed=44)
+    box = epsr.Box(s)
+    box.epsr_mc_set_ctas(4)
+    box.epsr_debug_barrier_fault(2, 200.0)
+    with pytest.raises(epsr.EpsrError) as ei:
+        box.epsr_mc_sweep(100, seed=1)
+    assert ei.value.status == epsr.EPSR_ETIMEOUT
+    box.epsr_debug_barrier_fault(-1, 2000.0)
+    # the context is still usable
+    H = gpu_hist(epsr.Box(synth.small_water()))
+    assert H.sum() > 0
+
+
+# --------------------------------------------------------------------------------------
+# S(Q)
+# --------------------------------------------------------------------------------------
+
+def test_sq_fp32_against_oracle(small_water):
+    box = epsr.Box(small_water)
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    g = torch.zeros(box.hist_len, dtype=torch.float32, device=DEV)
+    box.epsr_partial_gr(H, g, 1)
+    w, flat = box.epsr_sq_weights(0)
+    S_p = torch.zeros((3, len(small_water.Q)), dtype=torch.float32, device=DEV)
+    S_t = torch.zeros((1, len(small_water.Q)), dtype=torch.float32, device=DEV)
+    epsr.epsr_sq(g.view(3, -1), small_water.dr, small_water.Q, w, 3, np.array([flat]), S_p, S_t)
+    torch.cuda.synchronize()
+    ob = oracle.Box(small_water)
+    gref = ob.normalize_g(H.cpu().numpy().astype(np.uint64).reshape(3, -1))
+    Sp_ref, St_ref = oracle.sq_of_box(ob, gref, Q=small_water.Q.astype(np.float32).astype(np.float64))
+    W, fl = oracle.eq1_weights(small_water)
+    assert abs(fl - flat) < 1e-15
+    assert np.abs(S_t.cpu().numpy()[0] - St_ref).max() < 1e-4
+    assert np.abs(S_p.cpu().numpy() - Sp_ref).max() < 1e-4
+
+
+def test_sq_flat_background_gpu():
+    Q = 0.3 + np.arange(2000) * (39.7 / 1999)
+    g = torch.ones((6, 600), dtype=torch.float32, device=DEV)
+    S_t = torch.zeros((2, 2000), dtype=torch.float32, device=DEV)
+    epsr.epsr_sq(g, 0.02, Q, np.ones(6), 3, np.array([0.25, 0.5]), None, S_t)
+    torch.cuda.synchronize()
+    assert torch.all(S_t[0] == 0.25) and torch.all(S_t[1] == 0.5)
