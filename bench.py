@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Benchmark of the EPSR hot path on GB300: Monte Carlo moves/s and g(r) pair distances/s
+at 100k atoms.
+
+Workload (one step): the paper-scale water box (33,333 rigid 3-site molecules, 99,999
+atoms, 0.1 atoms/A^3, seed 1): 10,000 Metropolis moves (each with dU of the moved
+molecule against all atoms), then one full all-pair partial histogram g_ab(r) (333 x
+0.03 A bins) and S(Q) on 1000 Q points by Eq. (1). This is one "g(r)/S(Q) every 10,000
+moves" cycle of the 1e6-move run. Inputs are synthetic (seeded random sequential
+addition), resident in HBM when the timed region starts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank advances its own replica box (seed 1 + rank), no
+data-path collective (weak scaling); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MOVES_PER_STEP = 10_000
+METRIC = "MC moves/s and g(r) pair-distances/s at 100k atoms on 1 GB300, % of roofline"
+OPS_PER_PAIR_EVAL = 26     # algorithmic FP32+INT32 lane operations per (moved atom, partner, position)
+OPS_PER_PAIR_DIST = 12     # algorithmic INT32 lane operations per g(r) pair distance
+LANES_PER_SM = 128
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+
+def oracle_step_estimate(system, n_moves_sample: int, n_rows_sample: int, seed: int = 1):
+    """Time the FP64 oracle on a bounded sample of one step and scale to the full step.
+    Returns (seconds per full step, description, threads used)."""
+    import oracle
+    ob = oracle.Box(system)
+    t0 = time.perf_counter()
+    ob.mc_sweep(n_moves_sample, seed=seed, move0=0)
+    t_move = (time.perf_counter() - t0) / n_moves_sample
+    N = system.n_atoms
+    t0 = time.perf_counter()
+    ob.histogram(0, n_rows_sample)
+    t_hist = time.perf_counter() - t0
+    pairs_sample = sum(N - 1 - i for i in range(n_rows_sample))
+    t_pair = t_hist / pairs_sample
+    pairs = N * (N - 1) // 2
+    g = ob.normalize_g(np.zeros((3, system.n_bins), np.uint64) + 1)
+    t0 = time.perf_counter()
+    oracle.sq_of_box(ob, g)
+    t_sq = time.perf_counter() - t0
+    t_step = MOVES_PER_STEP * t_move + pairs * t_pair + t_sq
+    desc = (f"{n_moves_sample} moves + {pairs_sample:.3g} of {pairs:.3g} pair distances + 1 S(Q) "
+            f"timed, scaled to {MOVES_PER_STEP} moves + all pairs; 1 thread")
+    return t_step, desc, 1, t_move, t_pair
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1904_08756_gb300 import synth
+    system = synth.paper_water()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t_step, desc, cores, _, _ = oracle_step_estimate(system, 20, 200, seed=1 + i)
+        if i >= args.warmup:
+            times.append(t_step)
+    t = sum(times) / len(times)
+    v = MOVES_PER_STEP / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "paper-scale water, 99,999 atoms, 10,000 moves + g(r) + S(Q) per step"},
+            "cpu_baseline": {"value": v, "unit": "moves/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
+                    help="moves per step (profiling runs only; the benchmark uses 10,000)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1904_08756_gb300 import build, epsr, synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if not os.path.exists(epsr.LIB_PATH):
+        build.build()
+
+    system = synth.paper_water(seed=1 + rank)
+    N = system.n_atoms
+    stream = torch.cuda.current_stream(dev)
+    box = epsr.Box(system)
+    P = 3
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=dev)
+    g = torch.zeros(box.hist_len, dtype=torch.float32, device=dev)
+    S_t = torch.zeros((1, len(system.Q)), dtype=torch.float32, device=dev)
+    w, flat = box.epsr_sq_weights(0)
+    plan = epsr.SqPlan(system.Q, system.n_bins, system.dr, epsr.SQ_FP32, max_cols=P)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n_cfg = [0]
+    move0 = [0]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        box.epsr_mc_sweep(args.moves, 2024 + rank, move0[0])
+        move0[0] += args.moves
+        if ev is not None:
+            ev[1].record(stream)
+        n_cfg[0] += 1
+        box.epsr_partial_gr(H, g, n_cfg[0])
+        if ev is not None:
+            ev[2].record(stream)
+        plan.epsr_sq_exec(g.view(P, -1), w, P, np.array([flat]), None, S_t)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                 # L2 flush, outside the events
+            step(evs[k])
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t_mc = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    t_gr = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    t_sq = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+    t_step = t_mc + t_gr + t_sq
+    if ws > 1:
+        tt = torch.tensor([t_step, t_mc, t_gr, t_sq], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step, t_mc, t_gr, t_sq = tt.tolist()
+    moves_per_s = ws * MOVES_PER_STEP / (t_step * 1e-3)
+    pairs = N * (N - 1) // 2
+    gr_pairs_per_s = pairs / (t_gr * 1e-3)
+
+    # ---- end to end through the public API with host buffers --------------------------------
+    xyz_host = torch.from_numpy(np.ascontiguousarray(box.epsr_box_get_coords())).pin_memory()
+    xyz_dev = torch.empty((N, 3), dtype=torch.int32, device=dev)
+    S_host = torch.empty((1, len(system.Q)), dtype=torch.float32).pin_memory()
+    e2e_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e2e_ev[k][0].record(stream)
+        xyz_dev.copy_(xyz_host, non_blocking=True)
+        box.epsr_box_set_coords_device(xyz_dev)
+        step()
+        S_host.copy_(S_t, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_e2e = sum(e[0].elapsed_time(e[1]) for e in e2e_ev) / args.steps
+    if ws > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = tt.item()
+
+    if rank == 0:
+        peaks, src = measured_peaks()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        clock = clk.summary()
+        alu_peak = sms * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6   # lane-ops/s
+        m_atoms = 3
+        evals_per_move = 2 * m_atoms * (N - m_atoms)
+        mc_ops = MOVES_PER_STEP * evals_per_move * OPS_PER_PAIR_EVAL
+        mc_achieved = mc_ops / (t_mc * 1e-3)
+        gr_achieved = pairs * OPS_PER_PAIR_DIST / (t_gr * 1e-3)
+        traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+        traffic = None
+        if os.path.exists(traffic_file):
+            traffic = json.load(open(traffic_file)).get("mc_sweep_kernel_bytes_per_launch")
+        line = {
+            "metric": METRIC, "value": moves_per_s, "unit": "moves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32+int64", "data": "synthetic",
+            "config": {"workload": "paper-scale water, 99,999 atoms (33,333 rigid molecules), "
+                                   "10,000 MC moves + full g_ab(r) (333 x 0.03 A) + S(Q) (1000 Q) per step",
+                       "n_atoms": N, "moves_per_step": MOVES_PER_STEP,
+                       "l2": "flushed before every step by a 256 MiB write outside the timed events",
+                       "parallelism": f"replicas x{ws}"},
+            "gr_pair_distances_per_s": gr_pairs_per_s,
+            "mc_moves_per_s_kernel": MOVES_PER_STEP / (t_mc * 1e-3),
+            "ms_breakdown": {"mc_sweep": t_mc, "partial_gr": t_gr, "sq": t_sq},
+            "roofline": {"bound": "alu", "achieved": mc_achieved / 1e12, "peak": alu_peak / 1e12,
+                         "unit": "Tops/s", "frac": mc_achieved / alu_peak, "traffic": traffic,
+                         "kernel": "mc_sweep_kernel",
+                         "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src} max clock)"},
+            "roofline_gr": {"bound": "alu", "achieved": gr_achieved / 1e12, "peak": alu_peak / 1e12,
+                            "unit": "Tops/s", "frac": gr_achieved / alu_peak, "kernel": "partial_gr_kernel"},
+            "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
+                       "reasons": clock["reasons"]},
+            "e2e": {"value": ws * MOVES_PER_STEP / (t_e2e * 1e-3), "unit": "moves/s",
+                    "h2d_bytes_per_step": N * 3 * 4, "d2h_bytes_per_step": len(system.Q) * 4},
+            "gpu_launches": args.steps * 6,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            t_cpu, desc, cores, t_move, t_pair = oracle_step_estimate(system, 300, 3000)
+            line["cpu_baseline"] = {"value": MOVES_PER_STEP / t_cpu, "unit": "moves/s",
+                                    "cores": cores, "kind": "oracle", "sample": desc,
+                                    "moves_per_s": 1.0 / t_move, "pair_distances_per_s": 1.0 / t_pair}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    box.close()
+    plan.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

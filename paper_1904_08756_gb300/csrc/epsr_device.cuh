@@ -104,26 +104,33 @@ __device__ __forceinline__ float pair_u(long long d2, const PairRow &pr, const B
     return u;
 }
 
-// u(d2n) - u(d2o) for one partner seen from a moved atom's new and old positions. The
-// Coulomb difference uses the exact integer d2o - d2n so that it carries no
-// cancellation: 1/r' - 1/r = (r^2 - r'^2) (a a')^2 / (a + a'), a = 1/r, a' = 1/r'.
+// u(d2n) - u(d2o) for one partner seen from a moved atom's new and old positions,
+// written so that neither the Lennard-Jones nor the Coulomb difference cancels: both
+// are proportional to the exact integer difference r^2 - r'^2 = (d2o - d2n) S^-2.
+//   Coulomb: 1/r' - 1/r = (r^2 - r'^2) (a a')^2 / (a + a'),        a = 1/r, a' = 1/r'
+//   LJ:      s' - s = (r^2 - r'^2)(r^4 + r^2 r'^2 + r'^4) s s',      s = r^-6, s' = r'^-6
+//            c12 (s'^2 - s^2) - c6 (s' - s) = (s' - s)(c12 (s' + s) - c6)
+// so the FP32 error is a few ulp of |u(r') - u(r)|, not of |u|.
 __device__ __forceinline__ float pair_du(long long d2n, long long d2o, const PairRow &pr,
                                          const BoxDev &bx, const long long *T, const float *ep)
 {
     if (d2n == 0) return __int_as_float(0x7f800000);
     const float r2n = (float)d2n * bx.inv_s2;
     const float r2o = (float)d2o * bx.inv_s2;
+    const float dr2 = (float)(d2o - d2n) * bx.inv_s2;       // r^2 - r'^2 (exact integer)
     const float an = rsqrtf(r2n), ao = rsqrtf(r2o);
     float du = 0.f;
     if (pr.c12 != 0.f || pr.c6 != 0.f) {
         const float in = an * an, io = ao * ao;
         const float sn = in * in * in, so = io * io * io;
-        du = fmaf(pr.c12, sn, -pr.c6) * sn - fmaf(pr.c12, so, -pr.c6) * so;
+        const float poly = fmaf(r2o, r2o, fmaf(r2o, r2n, r2n * r2n));
+        const float ds = ((dr2 * poly) * sn) * so;
+        du = ds * fmaf(pr.c12, sn + so, -pr.c6);
     }
     const bool cn = d2n < bx.rc2, co = d2o < bx.rc2;
     if (cn && co) {
         const float p = an * ao;
-        du = fmaf(pr.kqq * ((float)(d2o - d2n) * bx.inv_s2), p * p / (an + ao), du);
+        du = fmaf(pr.kqq * dr2, p * p / (an + ao), du);
     } else if (cn) {
         du = fmaf(pr.kqq, an, du);
     } else if (co) {

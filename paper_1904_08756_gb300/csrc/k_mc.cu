@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     const int4 na = sh.newp[k][a], oa = sh.oldp[k][a];
                     const int4 nb_ = sh.newp[k1][b], ob = sh.oldp[k1][b];
                     const PairRow pr = bx.row[na.w * kMaxTypes + nb_.w];
-                    c += (pair_u(dist2(na, nb_, L), pr, bx, T, ep) - pair_u(dist2(oa, nb_, L), pr, bx, T, ep)) -
-                         (pair_u(dist2(na, ob, L), pr, bx, T, ep) - pair_u(dist2(oa, ob, L), pr, bx, T, ep));
+                    c += pair_du(dist2(na, nb_, L), dist2(oa, nb_, L), pr, bx, T, ep) -
+                         pair_du(dist2(na, ob, L), dist2(oa, ob, L), pr, bx, T, ep);
                 }
             sh.corr[k1][k] = c;
         }
