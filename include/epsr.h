@@ -123,7 +123,9 @@ int epsr_version(void);   /* major * 10000 + minor * 100 + patch */
  *   type      int32 [n_atoms], 0 .. n_types-1
  *   mol_start int64 [n_mol+1], mol_start[0] = 0, strictly increasing,
  *             mol_start[n_mol] = n_atoms; with EPSR_MOVE_RIGID_MOLECULE each molecule
- *             has at most EPSR_MAX_MOL_ATOMS atoms, with EPSR_MOVE_ATOM exactly one.
+ *             has at most EPSR_MAX_MOL_ATOMS atoms, with EPSR_MOVE_ATOM exactly one;
+ *             every atom lies within 2^25 grid units (32 A at scale_log2 = 20) of its
+ *             molecule's first atom on each axis.
  * Builds the exact bin-threshold table, the pair-parameter table and a zero empirical
  * potential. Synchronises `stream` before returning. Errors: EINVAL (any inconsistent
  * field or array), ENOMEM, ECUDA.

@@ -177,6 +177,13 @@ static int64_t wrap(int64_t x, int64_t L)
     return r < 0 ? r + L : r;
 }
 
+static int64_t floordiv64(int64_t a, int64_t b)    /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
 /* Move proposal (Sec. 2.2 item III: molecules or atoms moved at random; Sec. 3.1:
  * molecule translation and rotation). Random words: three Philox4x32-10 blocks with
  * counter (move lo, move hi, box index, lane), lane = 0, 1, 2, key (seed lo, seed hi).
@@ -185,11 +192,30 @@ static int64_t wrap(int64_t x, int64_t L)
  *   v_c   = h (2 u_c - 1), u_c from the word pairs (w4,w5), (w6,w7), (w8,w9),
  *           h = tan(max_rotation / 2) / sqrt(3) (reading c10)
  *   u_acc from (w10, w11)
- * Rotation (rigid molecules): unit quaternion (1, v) / |(1, v)| about the geometric
- * centre of the molecule unwrapped around its first atom; new position =
- * first atom + rint(centre + R (offset - centre)) + shift, wrapped into the box.
- * Atom moves: position + shift, wrapped. The FP64 sequence is stated in full so that
- * an independent implementation reproduces it bit for bit. */
+ * Rotation (rigid molecules): R is the matrix of the unit quaternion (1, v) / |(1, v)|,
+ * evaluated in FP64 in the order written below and rounded to Rq = rint(R 2^30). It is
+ * applied exactly, in integers, about the geometric centre of the molecule unwrapped
+ * around its first atom: with offsets o_k (minimum image of X_k - X_0), Sum = sum_k o_k,
+ * and e_k = m o_k - Sum, the new offset is the nearest integer (halves rounded up) to
+ * (Sum 2^30 + Rq e_k) / (m 2^30) = c + (Rq / 2^30)(o_k - c), c = Sum / m, computed as
+ * floor(floor((Sum 2^30 + Rq e_k + m 2^29) / 2^30) / m). New position = X_0 + that
+ * offset + shift, wrapped into the box. Atom moves: X + shift, wrapped. Everything
+ * after the FP64 matrix is integer arithmetic, so an independent implementation of the
+ * same definition reproduces the trial coordinates bit for bit. */
+void orc_rotation_fixed(double vx, double vy, double vz, int32_t Rq[9])
+{
+    const double ss = ((1.0 + vx * vx) + vy * vy) + vz * vz;
+    const double nn = sqrt(ss);
+    const double qw = 1.0 / nn, qx = vx / nn, qy = vy / nn, qz = vz / nn;
+    const double xx = qx * qx, yy = qy * qy, zz = qz * qz;
+    const double xy = qx * qy, xz = qx * qz, yz = qy * qz;
+    const double wx = qw * qx, wy = qw * qy, wz = qw * qz;
+    const double R[9] = {1.0 - 2.0 * (yy + zz), 2.0 * (xy - wz), 2.0 * (xz + wy),
+                         2.0 * (xy + wz), 1.0 - 2.0 * (xx + zz), 2.0 * (yz - wx),
+                         2.0 * (xz - wy), 2.0 * (yz + wx), 1.0 - 2.0 * (xx + yy)};
+    for (int i = 0; i < 9; ++i) Rq[i] = (int32_t)llrint(R[i] * 1073741824.0);
+}
+
 void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box_index,
                  int64_t *mol_out, int32_t *trial, double *u_acc)
 {
@@ -210,19 +236,9 @@ void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box
     if (s->rigid) {
         const double pi = 3.14159265358979323846;
         const double h = tan(0.5 * s->max_rotation_deg * pi / 180.0) / sqrt(3.0);
-        const double vx = h * (2.0 * u53(w[4], w[5]) - 1.0);
-        const double vy = h * (2.0 * u53(w[6], w[7]) - 1.0);
-        const double vz = h * (2.0 * u53(w[8], w[9]) - 1.0);
-        const double ss = ((1.0 + vx * vx) + vy * vy) + vz * vz;
-        const double nn = sqrt(ss);
-        const double qw = 1.0 / nn, qx = vx / nn, qy = vy / nn, qz = vz / nn;
-        const double xx = qx * qx, yy = qy * qy, zz = qz * qz;
-        const double xy = qx * qy, xz = qx * qz, yz = qy * qz;
-        const double wx = qw * qx, wy = qw * qy, wz = qw * qz;
-        const double R[3][3] = {
-            {1.0 - 2.0 * (yy + zz), 2.0 * (xy - wz), 2.0 * (xz + wy)},
-            {2.0 * (xy + wz), 1.0 - 2.0 * (xx + zz), 2.0 * (yz - wx)},
-            {2.0 * (xz - wy), 2.0 * (yz + wx), 1.0 - 2.0 * (xx + yy)}};
+        int32_t Rq[9];
+        orc_rotation_fixed(h * (2.0 * u53(w[4], w[5]) - 1.0), h * (2.0 * u53(w[6], w[7]) - 1.0),
+                           h * (2.0 * u53(w[8], w[9]) - 1.0), Rq);
         int64_t off[ORC_MAX_MOL_ATOMS][3];
         int64_t sum[3] = {0, 0, 0};
         for (int64_t k = 0; k < m; ++k)
@@ -231,15 +247,14 @@ void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box
                                           (int64_t)s->xyz[3 * a0 + a], L);
                 sum[a] += off[k][a];
             }
-        double c[3];
-        for (int a = 0; a < 3; ++a) c[a] = (double)sum[a] / (double)m;
         for (int64_t k = 0; k < m; ++k) {
-            double d[3];
-            for (int a = 0; a < 3; ++a) d[a] = (double)off[k][a] - c[a];
+            int64_t e[3];
+            for (int b = 0; b < 3; ++b) e[b] = m * off[k][b] - sum[b];
             for (int a = 0; a < 3; ++a) {
-                const double p = c[a] + ((R[a][0] * d[0] + R[a][1] * d[1]) + R[a][2] * d[2]);
-                trial[3 * k + a] = (int32_t)wrap((int64_t)s->xyz[3 * a0 + a] + llrint(p) +
-                                                 shift[a], L);
+                const int64_t num = sum[a] * 1073741824LL + (int64_t)Rq[3 * a] * e[0] +
+                                    (int64_t)Rq[3 * a + 1] * e[1] + (int64_t)Rq[3 * a + 2] * e[2];
+                const int64_t p = floordiv64(floordiv64(num + m * 536870912LL, 1073741824LL), m);
+                trial[3 * k + a] = (int32_t)wrap((int64_t)s->xyz[3 * a0 + a] + p + shift[a], L);
             }
         }
     } else {

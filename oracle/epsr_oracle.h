@@ -63,6 +63,7 @@ int32_t orc_pair_index(int32_t a, int32_t b, int32_t n_types);
 
 double orc_pair_energy(const orc_system *s, int32_t ta, int32_t tb, int64_t d2);
 double orc_total_energy(const orc_system *s);
+void orc_rotation_fixed(double vx, double vy, double vz, int32_t Rq[9]);
 void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box_index,
                  int64_t *mol, int32_t *trial /* [m][3] */, double *u_acc);
 double orc_delta_u(const orc_system *s, int64_t mol, const int32_t *trial, double *cond);

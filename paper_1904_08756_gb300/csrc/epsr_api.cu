@@ -125,11 +125,21 @@ struct epsr_box {
     int *status = nullptr;
     double *U = nullptr;
     int tbl_cap = 0, ep_cap = 0;
+    // spatial sort of the pair scan
+    int total_cells = 0;
+    SortScratch sort{};
+    uint4 *sorted_scaled = nullptr;
+    int4 *sorted_coords = nullptr;
+    // Monte Carlo move table
+    MoveRec *moves = nullptr;
+    long long moves_cap = 0;
 
     ~epsr_box()
     {
         void *ptrs[] = {boxes, coords, scaled, mol_start, atom_box, atom_mol, thresholds, ep,
-                        tiles, hist_box, cta_box, slots, flags, stats, status, U};
+                        tiles, hist_box, cta_box, slots, flags, stats, status, U,
+                        sort.count, sort.offset, sort.block, sort.key, sort.rank, sort.index,
+                        sorted_scaled, sorted_coords, moves};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -308,6 +318,14 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
             if (sz < 1) { delete h; return set_error(EPSR_EINVAL, "box %d: mol_start not strictly increasing at %lld", b, m); }
             if (d.move_kind == EPSR_MOVE_ATOM && sz != 1) { delete h; return set_error(EPSR_EINVAL, "box %d: atom moves need single-atom molecules", b); }
             if (sz > EPSR_MAX_MOL_ATOMS) { delete h; return set_error(EPSR_EINVAL, "box %d: molecule %lld has %lld > %d atoms", b, m, sz, EPSR_MAX_MOL_ATOMS); }
+            // rigid rotations use 32-bit intermediates: molecule extent below 2^25 grid units
+            for (long long i = ms[m]; i < ms[m + 1]; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    long long dd = (long long)xyz[3 * (atom0 + i) + c] - xyz[3 * (atom0 + ms[m]) + c];
+                    if (2 * dd > d.L_fx) dd -= d.L_fx;
+                    else if (2 * dd <= -d.L_fx) dd += d.L_fx;
+                    if (dd >= (1LL << 25) || dd <= -(1LL << 25)) { delete h; return set_error(EPSR_EINVAL, "box %d: molecule %lld wider than 2^25 grid units", b, m); }
+                }
         }
         BoxDev &bx = h->hb[b];
         fill_boxdev(d, ty, bx);
@@ -334,6 +352,18 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         BoxDev &bx = h->hb[b];
         build_thresholds(descs[b], &T[bx.tbl_off]);
         bx.tmax = T[bx.tbl_off + bx.n_bins];
+        bx.tmax_lo = (float)((double)bx.tmax * (1.0 - 0x1p-20));
+        bx.tmax_hi = (float)((double)bx.tmax * (1.0 + 0x1p-20));
+        bx.rc2_lo = (float)((double)bx.rc2 * (1.0 - 0x1p-20));
+        bx.rc2_hi = (float)((double)bx.rc2 * (1.0 + 0x1p-20));
+        const double LA = (double)bx.L / std::ldexp(1.0, descs[b].scale_log2);
+        int nc = (int)std::floor(LA / 3.0);
+        nc = std::max(1, std::min(nc, 32));
+        int p2 = 1;
+        while (p2 < nc) p2 <<= 1;
+        bx.cells = nc;
+        bx.cell0 = h->total_cells;
+        h->total_cells += p2 * p2 * p2;
         const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
         const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
         bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
@@ -368,7 +398,12 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         (rc = dalloc(&h->thresholds, T.size())) || (rc = dalloc(&h->ep, (size_t)ep0)) ||
         (rc = dalloc(&h->tiles, h->tiles_h.size())) || (rc = dalloc(&h->hist_box, n_boxes)) ||
         (rc = dalloc(&h->stats, n_boxes)) || (rc = dalloc(&h->status, 1)) ||
-        (rc = dalloc(&h->U, n_boxes))) {
+        (rc = dalloc(&h->U, n_boxes)) || (rc = dalloc(&h->sort.count, h->total_cells)) ||
+        (rc = dalloc(&h->sort.offset, h->total_cells)) ||
+        (rc = dalloc(&h->sort.block, (h->total_cells + 1023) / 1024)) ||
+        (rc = dalloc(&h->sort.key, atom0)) || (rc = dalloc(&h->sort.rank, atom0)) ||
+        (rc = dalloc(&h->sort.index, atom0)) ||
+        (rc = dalloc(&h->sorted_scaled, atom0)) || (rc = dalloc(&h->sorted_coords, atom0))) {
         delete h;
         return rc;
     }
@@ -582,6 +617,7 @@ extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint
 {
     if (!box || n_moves < 0) return set_error(EPSR_EINVAL, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(box->status, 0, sizeof(int), s));
     if (n_moves > 0) {
         int slice_cap = 0;
         for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
@@ -591,6 +627,17 @@ extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint
         if (smem > kMcMaxDynSmem)
             return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of shared memory per CTA needed (limit %zu); "
                              "give the sweep more CTAs", smem, kMcMaxDynSmem);
+        // moves per launch: the table holds at most 2^22 moves over all boxes
+        const long long chunk = std::min<long long>(
+            n_moves, std::max<long long>(1024, std::min<long long>(65536, (1LL << 22) / box->n_boxes)));
+        if (box->moves_cap < chunk * box->n_boxes) {
+            if (box->moves) cudaFree(box->moves);
+            box->moves = nullptr;
+            box->moves_cap = 0;
+            int rc = dalloc(&box->moves, (size_t)(chunk * box->n_boxes));
+            if (rc) return rc;
+            box->moves_cap = chunk * box->n_boxes;
+        }
         McArgs a;
         memset(&a, 0, sizeof(a));
         a.boxes = box->boxes;
@@ -604,9 +651,7 @@ extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint
         a.stats = box->stats;
         a.log = log;
         a.status = box->status;
-        a.n_moves = n_moves;
         a.seed = seed;
-        a.move0 = move0;
         a.log_stride = n_moves;
         a.max_spin = 1LL << 40;
         a.timeout_ns = (unsigned long long)(box->timeout_ms * 1e6);
@@ -615,10 +660,20 @@ extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint
         a.slice_cap = slice_cap;
         a.tbl_cap = box->tbl_cap;
         a.skip_arrival_cta = box->fault_cta;
-        CK(cudaMemsetAsync(box->flags, 0, box->cta_box_len * sizeof(unsigned), s));
-        CK(cudaMemsetAsync(box->status, 0, sizeof(int), s));
-        int rc = launch_mc_sweep(a, box->cta_box_len, smem, s);
-        if (rc) return rc;
+        a.moves = box->moves;
+        a.chunk = chunk;
+        for (long long c0 = 0; c0 < n_moves; c0 += chunk) {
+            const long long n = std::min(chunk, n_moves - c0);
+            int rc = launch_mc_moves(box->boxes, box->n_boxes, chunk, n, seed, move0 + (uint64_t)c0,
+                                     box->moves, s);
+            if (rc) return rc;
+            a.n_moves = n;
+            a.move0 = move0 + (uint64_t)c0;
+            a.log_off = c0;
+            CK(cudaMemsetAsync(box->flags, 0, box->cta_box_len * sizeof(unsigned), s));
+            rc = launch_mc_sweep(a, box->cta_box_len, smem, s);
+            if (rc) return rc;
+        }
     }
     int st = 0;
     CK(cudaMemcpyAsync(&st, box->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -643,10 +698,13 @@ static int gr_range(epsr_box *box, long long t0, long long t1, uint64_t *hist, c
     if (t0 < 0 || t1 > nt || t0 > t1) return set_error(EPSR_EINVAL, "tile range [%lld, %lld) outside [0, %lld)", t0, t1, nt);
     int rc = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
     if (rc) return rc;
+    rc = launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
+                             box->total_cells, box->sort, box->sorted_scaled, box->sorted_coords, s);
+    if (rc) return rc;
     GrArgs a;
     a.boxes = box->boxes;
-    a.coords = box->coords;
-    a.scaled = box->scaled;
+    a.coords = box->sorted_coords;
+    a.scaled = box->sorted_scaled;
     a.thresholds = box->thresholds;
     a.tiles = box->tiles;
     a.tile_begin = t0;

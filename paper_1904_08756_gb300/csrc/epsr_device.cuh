@@ -47,7 +47,11 @@ struct BoxDev {
     float inv_s2;         // 2^(-2 scale_log2): grid units^2 -> A^2
     float inv_dr_fx;      // 1 / (bin width in grid units)
     uint32_t pre_r;       // g(r) prefilter half width on the 2^32-periodic scaled grid
-    int32_t pad0;
+    int32_t cells;        // spatial-sort cells per side (g(r) work order)
+    float rc2_lo, rc2_hi; // rc2 * (1 -/+ 2^-20) as floats: the exact test runs only between
+    float tmax_lo, tmax_hi;   // tmax * (1 -/+ 2^-20)
+    int32_t cell0;        // first global cell of this box (spatial sort)
+    int32_t pad1;
     int64_t count[kMaxTypes];   // atoms per type
     PairRow row[kMaxTypes * kMaxTypes];
 };
@@ -65,32 +69,65 @@ __device__ __forceinline__ int mi_abs(int d, int L)
     return min(a, L - a);
 }
 
-__device__ __forceinline__ long long dist2(int4 a, int4 b, int L)
+// Non-negative minimum-image separation components of two grid points (exact int32).
+struct Sep {
+    int x, y, z;
+};
+
+__device__ __forceinline__ Sep sep(int4 a, int4 b, int L)
 {
-    const long long dx = mi_abs(a.x - b.x, L);
-    const long long dy = mi_abs(a.y - b.y, L);
-    const long long dz = mi_abs(a.z - b.z, L);
-    return dx * dx + dy * dy + dz * dz;
+    Sep s;
+    s.x = mi_abs(a.x - b.x, L);
+    s.y = mi_abs(a.y - b.y, L);
+    s.z = mi_abs(a.z - b.z, L);
+    return s;
 }
 
-// Largest k with T[k] <= d2, for d2 < T[n_bins] (exact; the float guess is corrected).
-__device__ __forceinline__ int bin_of(long long d2, const long long *T, int n_bins,
+// Exact squared distance (grid units^2); 64-bit products, used only off the fast path.
+__device__ __forceinline__ long long d2_of(Sep s)
+{
+    return (long long)s.x * s.x + (long long)s.y * s.y + (long long)s.z * s.z;
+}
+
+// Squared distance in grid units^2 as FP32 from the int32 components (32-bit conversions
+// only: a 64-bit integer conversion would run on the FP64 unit). Relative error < 2^-22.
+__device__ __forceinline__ float g2_of(Sep s)
+{
+    const float fx = (float)s.x, fy = (float)s.y, fz = (float)s.z;
+    return fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+}
+
+__device__ __forceinline__ long long dist2(int4 a, int4 b, int L) { return d2_of(sep(a, b, L)); }
+
+// Exact d2 < lim, decided from the FP32 estimate g2 unless it lies within a relative
+// 2^-20 of the limit (lo, hi are lim * (1 -/+ 2^-20)).
+__device__ __forceinline__ bool below(float g2, Sep s, long long lim, float lo, float hi)
+{
+    if (g2 < lo) return true;
+    if (g2 > hi) return false;
+    return d2_of(s) < lim;
+}
+
+// Largest k with T[k] <= d2, for d2 < T[n_bins]: a float guess from g2 ~ d2, corrected
+// against the exact threshold table.
+__device__ __forceinline__ int bin_of(long long d2, float g2, const long long *T, int n_bins,
                                       float inv_dr_fx)
 {
-    int k = (int)(sqrtf((float)d2) * inv_dr_fx);
-    k = min(k, n_bins - 1);
+    int k = (int)(sqrtf(g2) * inv_dr_fx);
+    k = max(0, min(k, n_bins - 1));
     while (k > 0 && T[k] > d2) --k;
     while (T[k + 1] <= d2) ++k;
     return k;
 }
 
-// Pair energy at squared distance d2 (grid units^2), FP32 (Sec. 2.1: reference
-// potential + empirical potential). Coincident points have +inf energy.
-__device__ __forceinline__ float pair_u(long long d2, const PairRow &pr, const BoxDev &bx,
+// Pair energy of a separation (FP32; Sec. 2.1: reference potential + empirical
+// potential). Coincident points have +inf energy.
+__device__ __forceinline__ float pair_u(Sep s, const PairRow &pr, const BoxDev &bx,
                                         const long long *T, const float *ep)
 {
-    if (d2 == 0) return __int_as_float(0x7f800000);
-    const float r2 = (float)d2 * bx.inv_s2;
+    const float g2 = g2_of(s);
+    if (g2 == 0.f) return __int_as_float(0x7f800000);
+    const float r2 = g2 * bx.inv_s2;
     const float a = rsqrtf(r2);
     float u = 0.f;
     if (pr.c12 != 0.f || pr.c6 != 0.f) {
@@ -98,36 +135,42 @@ __device__ __forceinline__ float pair_u(long long d2, const PairRow &pr, const B
         const float s6 = i2 * i2 * i2;
         u = fmaf(pr.c12, s6, -pr.c6) * s6;
     }
-    if (d2 < bx.rc2) u = fmaf(pr.kqq, a, u);
-    if (bx.has_ep && d2 < bx.tmax)
-        u += ep[pr.pair * bx.n_bins + bin_of(d2, T, bx.n_bins, bx.inv_dr_fx)];
+    if (below(g2, s, bx.rc2, bx.rc2_lo, bx.rc2_hi)) u = fmaf(pr.kqq, a, u);
+    if (bx.has_ep && g2 < bx.tmax_hi && below(g2, s, bx.tmax, bx.tmax_lo, bx.tmax_hi))
+        u += ep[pr.pair * bx.n_bins + bin_of(d2_of(s), g2, T, bx.n_bins, bx.inv_dr_fx)];
     return u;
 }
 
-// u(d2n) - u(d2o) for one partner seen from a moved atom's new and old positions,
-// written so that neither the Lennard-Jones nor the Coulomb difference cancels: both
-// are proportional to the exact integer difference r^2 - r'^2 = (d2o - d2n) S^-2.
+// u(r') - u(r) for one partner seen from a moved atom's new (sn) and old (so) positions,
+// written so that neither the Lennard-Jones nor the Coulomb difference cancels: both are
+// proportional to r^2 - r'^2 = sum over axes (|do| - |dn|)(|do| + |dn|), whose factors are
+// exact small integers.
 //   Coulomb: 1/r' - 1/r = (r^2 - r'^2) (a a')^2 / (a + a'),        a = 1/r, a' = 1/r'
 //   LJ:      s' - s = (r^2 - r'^2)(r^4 + r^2 r'^2 + r'^4) s s',      s = r^-6, s' = r'^-6
 //            c12 (s'^2 - s^2) - c6 (s' - s) = (s' - s)(c12 (s' + s) - c6)
 // so the FP32 error is a few ulp of |u(r') - u(r)|, not of |u|.
-__device__ __forceinline__ float pair_du(long long d2n, long long d2o, const PairRow &pr,
-                                         const BoxDev &bx, const long long *T, const float *ep)
+__device__ __forceinline__ float pair_du(Sep sn, Sep so, const PairRow &pr, const BoxDev &bx,
+                                         const long long *T, const float *ep)
 {
-    if (d2n == 0) return __int_as_float(0x7f800000);
-    const float r2n = (float)d2n * bx.inv_s2;
-    const float r2o = (float)d2o * bx.inv_s2;
-    const float dr2 = (float)(d2o - d2n) * bx.inv_s2;       // r^2 - r'^2 (exact integer)
+    const float fxn = (float)sn.x, fyn = (float)sn.y, fzn = (float)sn.z;
+    const float fxo = (float)so.x, fyo = (float)so.y, fzo = (float)so.z;
+    const float g2n = fmaf(fxn, fxn, fmaf(fyn, fyn, fzn * fzn));
+    const float g2o = fmaf(fxo, fxo, fmaf(fyo, fyo, fzo * fzo));
+    if (g2n == 0.f) return __int_as_float(0x7f800000);
+    const float r2n = g2n * bx.inv_s2, r2o = g2o * bx.inv_s2;
+    const float dr2 = fmaf(fxo - fxn, fxo + fxn, fmaf(fyo - fyn, fyo + fyn, (fzo - fzn) * (fzo + fzn))) *
+                      bx.inv_s2;
     const float an = rsqrtf(r2n), ao = rsqrtf(r2o);
     float du = 0.f;
     if (pr.c12 != 0.f || pr.c6 != 0.f) {
         const float in = an * an, io = ao * ao;
-        const float sn = in * in * in, so = io * io * io;
+        const float s6n = in * in * in, s6o = io * io * io;
         const float poly = fmaf(r2o, r2o, fmaf(r2o, r2n, r2n * r2n));
-        const float ds = ((dr2 * poly) * sn) * so;
-        du = ds * fmaf(pr.c12, sn + so, -pr.c6);
+        const float ds = ((dr2 * poly) * s6n) * s6o;
+        du = ds * fmaf(pr.c12, s6n + s6o, -pr.c6);
     }
-    const bool cn = d2n < bx.rc2, co = d2o < bx.rc2;
+    const bool cn = below(g2n, sn, bx.rc2, bx.rc2_lo, bx.rc2_hi);
+    const bool co = below(g2o, so, bx.rc2, bx.rc2_lo, bx.rc2_hi);
     if (cn && co) {
         const float p = an * ao;
         du = fmaf(pr.kqq * dr2, p * p / (an + ao), du);
@@ -136,10 +179,12 @@ __device__ __forceinline__ float pair_du(long long d2n, long long d2o, const Pai
     } else if (co) {
         du = fmaf(-pr.kqq, ao, du);
     }
-    if (bx.has_ep && (d2n < bx.tmax || d2o < bx.tmax)) {
+    if (bx.has_ep && (g2n < bx.tmax_hi || g2o < bx.tmax_hi)) {
         const float *row = ep + pr.pair * bx.n_bins;
-        if (d2n < bx.tmax) du += row[bin_of(d2n, T, bx.n_bins, bx.inv_dr_fx)];
-        if (d2o < bx.tmax) du -= row[bin_of(d2o, T, bx.n_bins, bx.inv_dr_fx)];
+        if (below(g2n, sn, bx.tmax, bx.tmax_lo, bx.tmax_hi))
+            du += row[bin_of(d2_of(sn), g2n, T, bx.n_bins, bx.inv_dr_fx)];
+        if (below(g2o, so, bx.tmax, bx.tmax_lo, bx.tmax_hi))
+            du -= row[bin_of(d2_of(so), g2o, T, bx.n_bins, bx.inv_dr_fx)];
     }
     return du;
 }
@@ -185,12 +230,11 @@ __device__ __forceinline__ long long mi_signed(long long d, long long L)
     return d;
 }
 
-// Trial coordinates of a rigid-molecule move: rotation by the unit quaternion (1, v)/|(1, v)|
-// about the centre of the molecule (unwrapped around its first atom), then the integer
-// shift, wrapped into the box. Explicit round-to-nearest FP64 operations (no contraction)
-// make the sequence exact and reproducible: the same IEEE operations in the same order.
-__device__ inline void rigid_trial(const int4 *old, int m, double vx, double vy, double vz,
-                                   const int *shift, int L, int4 *out)
+// Rotation matrix of the unit quaternion (1, v)/|(1, v)| in FP64, rounded to 2^-30 fixed
+// point. Explicit round-to-nearest operations (no contraction) make the sequence exact:
+// any implementation performing the same IEEE operations in this order gets the same
+// integers.
+__device__ inline void rotation_fixed(double vx, double vy, double vz, int *Rq)
 {
     const double ss = __dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(vx, vx)), __dmul_rn(vy, vy)),
                                 __dmul_rn(vz, vz));
@@ -200,41 +244,27 @@ __device__ inline void rigid_trial(const int4 *old, int m, double vx, double vy,
     const double xx = __dmul_rn(qx, qx), yy = __dmul_rn(qy, qy), zz = __dmul_rn(qz, qz);
     const double xy = __dmul_rn(qx, qy), xz = __dmul_rn(qx, qz), yz = __dmul_rn(qy, qz);
     const double wx = __dmul_rn(qw, qx), wy = __dmul_rn(qw, qy), wz = __dmul_rn(qw, qz);
-    double R[3][3];
-    R[0][0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(yy, zz)));
-    R[0][1] = __dmul_rn(2.0, __dsub_rn(xy, wz));
-    R[0][2] = __dmul_rn(2.0, __dadd_rn(xz, wy));
-    R[1][0] = __dmul_rn(2.0, __dadd_rn(xy, wz));
-    R[1][1] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, zz)));
-    R[1][2] = __dmul_rn(2.0, __dsub_rn(yz, wx));
-    R[2][0] = __dmul_rn(2.0, __dsub_rn(xz, wy));
-    R[2][1] = __dmul_rn(2.0, __dadd_rn(yz, wx));
-    R[2][2] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, yy)));
-    long long off[kMaxMolAtoms][3];
-    long long sum[3] = {0, 0, 0};
-    const int base[3] = {old[0].x, old[0].y, old[0].z};
-    for (int k = 0; k < m; ++k) {
-        const int c[3] = {old[k].x, old[k].y, old[k].z};
-        for (int a = 0; a < 3; ++a) {
-            off[k][a] = mi_signed((long long)c[a] - base[a], L);
-            sum[a] += off[k][a];
-        }
-    }
-    double cen[3];
-    for (int a = 0; a < 3; ++a) cen[a] = __ddiv_rn((double)sum[a], (double)m);
-    for (int k = 0; k < m; ++k) {
-        double d[3];
-        for (int a = 0; a < 3; ++a) d[a] = __dsub_rn((double)off[k][a], cen[a]);
-        int o[3];
-        for (int a = 0; a < 3; ++a) {
-            const double p = __dadd_rn(cen[a], __dadd_rn(__dadd_rn(__dmul_rn(R[a][0], d[0]),
-                                                                   __dmul_rn(R[a][1], d[1])),
-                                                         __dmul_rn(R[a][2], d[2])));
-            o[a] = wrap_coord((long long)base[a] + __double2ll_rn(p) + shift[a], L);
-        }
-        out[k] = make_int4(o[0], o[1], o[2], old[k].w);
-    }
+    double R[9];
+    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(yy, zz)));
+    R[1] = __dmul_rn(2.0, __dsub_rn(xy, wz));
+    R[2] = __dmul_rn(2.0, __dadd_rn(xz, wy));
+    R[3] = __dmul_rn(2.0, __dadd_rn(xy, wz));
+    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, zz)));
+    R[5] = __dmul_rn(2.0, __dsub_rn(yz, wx));
+    R[6] = __dmul_rn(2.0, __dsub_rn(xz, wy));
+    R[7] = __dmul_rn(2.0, __dadd_rn(yz, wx));
+    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, yy)));
+    for (int i = 0; i < 9; ++i) Rq[i] = (int)__double2ll_rn(__dmul_rn(R[i], 1073741824.0));
 }
+
+// Configuration-independent part of one Monte Carlo move (64 bytes).
+struct __align__(16) MoveRec {
+    int mol;
+    int shift[3];
+    int R[9];        // rotation matrix * 2^30, rounded
+    float thr;       // FP32 rounded up from -kT ln u_acc
+    double u_acc;
+};
 
 // ---- device status word ------------------------------------------------------------------
 constexpr int kStatusTimeout = 1;

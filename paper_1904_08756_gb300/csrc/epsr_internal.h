@@ -10,6 +10,7 @@
 namespace epsr {
 
 struct BoxDev;
+struct MoveRec;
 
 // ---- errors (thread-local last error, see epsr_last_error_detail) -------------------------
 int set_error(int status, const char *fmt, ...);
@@ -29,6 +30,9 @@ struct McArgs {
     unsigned *flags;              // [grid] arrival sequence numbers (zeroed per launch)
     epsr_mc_stats *stats;         // [n_boxes] running totals (device)
     epsr_move_log *log;           // nullable [n_boxes][log_stride]
+    const MoveRec *moves;         // [n_boxes][chunk] this launch's moves
+    long long chunk;              // move-table stride per box
+    long long log_off;            // log index of this launch's first move
     int *status;                  // device status word
     long long n_moves;
     unsigned long long seed, move0;
@@ -43,6 +47,9 @@ struct McArgs {
 };
 
 int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stream);
+int launch_mc_moves(const BoxDev *boxes, int n_boxes, long long chunk, long long n,
+                    unsigned long long seed, unsigned long long move0, MoveRec *out,
+                    cudaStream_t stream);
 int mc_threads();
 int mc_batch_max();
 
@@ -70,6 +77,17 @@ constexpr int kGrTile = 1024;    // atoms per tile (both sides)
 int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *coords,
                         uint4 *scaled, long long n, cudaStream_t stream);
 int launch_partial_gr(const GrArgs &args, int grid, cudaStream_t stream);
+
+struct SortScratch {      // device scratch of the spatial sort
+    int *count;           // [total_cells]
+    int *offset;          // [total_cells]
+    int *block;           // [ceil(total_cells / 1024)]
+    int *key, *rank;      // [n_atoms_total]
+    int *index;           // [n_atoms_total] atom index at each sorted position
+};
+int launch_spatial_sort(const BoxDev *boxes, const int *atom_box, const uint4 *scaled,
+                        const int4 *coords, long long n, int total_cells, SortScratch sc,
+                        uint4 *s_scaled, int4 *s_coords, cudaStream_t stream);
 int launch_normalize_g(const BoxDev *boxes, int n_boxes, const unsigned long long *hist,
                        float *g, long long n_configs, long long hist_len, const long long *hist_box,
                        cudaStream_t stream);

@@ -48,6 +48,168 @@ int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *co
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "scale_coords");
 }
 
+// ---- spatial order for the pair scan ---------------------------------------------------------
+// Atoms are counting-sorted by the Morton code of their cell (up to 32 cells per side,
+// about 3 A wide) so that the 32 i-atoms of a warp are neighbours in space: candidate
+// pairs then come in dense runs instead of scattering single lanes into the exact path.
+// Every pair is still tested; the order inside a cell is irrelevant to integer counts.
+__device__ __forceinline__ unsigned spread5(unsigned v)
+{
+    v &= 31u;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void cell_key_kernel(const BoxDev *boxes, const int *atom_box, const uint4 *scaled,
+                                int *key, int *rank, int *count, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const BoxDev &b = boxes[atom_box[i]];
+        const uint4 s = scaled[i];
+        const unsigned nc = (unsigned)b.cells;
+        const unsigned cx = __umulhi(s.x, nc), cy = __umulhi(s.y, nc), cz = __umulhi(s.z, nc);
+        const int k = b.cell0 + (int)(spread5(cx) | (spread5(cy) << 1) | (spread5(cz) << 2));
+        key[i] = k;
+        rank[i] = atomicAdd(&count[k], 1);
+    }
+}
+
+// Exclusive scan of the cell counts in three passes over blocks of kScanBlock cells.
+constexpr int kScanBlock = 1024;
+
+__global__ void scan_block_sums_kernel(const int *count, int n, int *block_sum)
+{
+    __shared__ int red[32];
+    const int b = blockIdx.x, i = b * kScanBlock + threadIdx.x;
+    int v = i < n ? count[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) block_sum[b] = t;
+    }
+}
+
+// Exclusive scan of the block sums in place by one CTA of 1024 threads, each owning a
+// contiguous chunk.
+__global__ void scan_block_offsets_kernel(int *block_sum, int nblocks)
+{
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (nblocks + 1023) / 1024;
+    const int b0 = min(nblocks, t * per), b1 = min(nblocks, b0 + per);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += block_sum[b];
+    int x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int run = x - local + (w > 0 ? wsum[w - 1] : 0);
+    for (int b = b0; b < b1; ++b) {
+        const int v = block_sum[b];
+        block_sum[b] = run;
+        run += v;
+    }
+}
+
+__global__ void scan_finish_kernel(const int *count, int n, const int *block_off, int *offset)
+{
+    __shared__ int wsum[32];
+    const int b = blockIdx.x, i = b * kScanBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = i < n ? count[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    const int excl = x - v + (w > 0 ? wsum[w - 1] : 0) + block_off[b];
+    if (i < n) offset[i] = excl;
+}
+
+__global__ void scatter_index_kernel(const int *key, const int *rank, const int *offset,
+                                     int *sorted_index, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        sorted_index[offset[key[i]] + rank[i]] = (int)i;
+}
+
+// Makes the order deterministic: each cell's segment (a few atoms) is put in atom-index
+// order, then the coordinates are gathered in that order. Ranks from the counting pass
+// depend on atomic timing; the final order depends only on the coordinates.
+__global__ void cell_order_kernel(const int *count, const int *offset, int total_cells,
+                                  int *idx, const uint4 *scaled, const int4 *coords,
+                                  uint4 *s_scaled, int4 *s_coords)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < total_cells; c += gridDim.x * blockDim.x) {
+        const int b = offset[c], n = count[c];
+        for (int a = 1; a < n; ++a) {
+            const int v = idx[b + a];
+            int k = a - 1;
+            while (k >= 0 && idx[b + k] > v) {
+                idx[b + k + 1] = idx[b + k];
+                --k;
+            }
+            idx[b + k + 1] = v;
+        }
+        for (int a = 0; a < n; ++a) {
+            const int i = idx[b + a];
+            s_scaled[b + a] = scaled[i];
+            s_coords[b + a] = coords[i];
+        }
+    }
+}
+
+int launch_spatial_sort(const BoxDev *boxes, const int *atom_box, const uint4 *scaled,
+                        const int4 *coords, long long n, int total_cells, SortScratch sc,
+                        uint4 *s_scaled, int4 *s_coords, cudaStream_t stream)
+{
+    if (n == 0) return EPSR_OK;
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    const int nblk = (total_cells + kScanBlock - 1) / kScanBlock;
+    cudaError_t e = cudaMemsetAsync(sc.count, 0, (size_t)total_cells * sizeof(int), stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "sort memset");
+    cell_key_kernel<<<grid, 256, 0, stream>>>(boxes, atom_box, scaled, sc.key, sc.rank, sc.count, n);
+    scan_block_sums_kernel<<<nblk, kScanBlock, 0, stream>>>(sc.count, total_cells, sc.block);
+    scan_block_offsets_kernel<<<1, 1024, 0, stream>>>(sc.block, nblk);
+    scan_finish_kernel<<<nblk, kScanBlock, 0, stream>>>(sc.count, total_cells, sc.block, sc.offset);
+    scatter_index_kernel<<<grid, 256, 0, stream>>>(sc.key, sc.rank, sc.offset, sc.index, n);
+    const int cgrid = (total_cells + 255) / 256 < 4096 ? (total_cells + 255) / 256 : 4096;
+    cell_order_kernel<<<cgrid, 256, 0, stream>>>(sc.count, sc.offset, total_cells, sc.index, scaled,
+                                                 coords, s_scaled, s_coords);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "spatial sort");
+}
+
 __device__ __forceinline__ void flush_hist(unsigned *sh_hist, int n, unsigned long long *out)
 {
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -95,6 +257,7 @@ __global__ void __launch_bounds__(kGrThreads, 2) partial_gr_kernel(GrArgs A)
         const int N = bx.n_atoms;
         const unsigned R = bx.pre_r, R2 = 2u * bx.pre_r;
         const long long tmax = bx.tmax;
+        const float tmax_hi = bx.tmax_hi;
         const int nb = bx.n_bins, nt = bx.n_types;
         const float inv = bx.inv_dr_fx;
         // stage the j-tile
@@ -132,11 +295,15 @@ __global__ void __launch_bounds__(kGrThreads, 2) partial_gr_kernel(GrArgs A)
                     if (il[r] < 0 || (diag && j <= il[r])) continue;
                     const int4 pi = A.coords[bx.atom0 + i0 + il[r]];
                     const int4 pj = s_true[j];
-                    const long long d2 = dist2(pi, pj, L);
-                    if (d2 < tmax) {
-                        const int k = bin_of(d2, s_T, nb, inv);
-                        const int p = pair_index(pi.w, pj.w, nt);
-                        atomicAdd(&s_hist[p * nb + k], 1u);
+                    const Sep sp = sep(pi, pj, L);
+                    const float g2 = g2_of(sp);
+                    if (g2 < tmax_hi) {
+                        const long long d2 = d2_of(sp);
+                        if (d2 < tmax) {
+                            const int k = bin_of(d2, g2, s_T, nb, inv);
+                            const int p = pair_index(pi.w, pj.w, nt);
+                            atomicAdd(&s_hist[p * nb + k], 1u);
+                        }
                     }
                 }
             }
@@ -264,7 +431,7 @@ total_energy_kernel(const BoxDev *boxes, const int4 *coords, const int *atom_mol
             for (int r = 0; r < kUR; ++r) {
                 if (il[r] < 0 || mi[r] == mj || (diag && j <= il[r])) continue;
                 const PairRow pr = bx.row[pi[r].w * kMaxTypes + pj.w];
-                acc += pair_u(dist2(pi[r], pj, L), pr, bx, s_T, ep);
+                acc += pair_u(sep(pi[r], pj, L), pr, bx, s_T, ep);
             }
         }
         double v = (double)acc;

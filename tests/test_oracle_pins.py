@@ -505,3 +505,19 @@ def test_chi2_gradients_match_finite_differences():
             fm = oracle.chi2_and_grads(oracle.Box(s, xyz=xm), sigma, s.Q, target, C_, 0.5)[0]
             fd = (fp - fm) / (2 * h / S)
             assert abs(fd - gx[i, c]) <= tol, (i, c, fd, gx[i, c])
+
+
+def test_rotation_matrix_against_scipy():
+    """The fixed-point rotation matrix of the move (quaternion (1, v)/|(1, v)|) equals the
+    rotation SciPy builds from the same quaternion, to the 2^-30 rounding."""
+    import ctypes as C
+    Rotation = pytest.importorskip("scipy.spatial.transform").Rotation
+    L = oracle.lib()
+    L.orc_rotation_fixed.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int32)]
+    rng = np.random.default_rng(17)
+    for _ in range(200):
+        v = rng.uniform(-0.3, 0.3, 3)
+        Rq = np.zeros(9, np.int32)
+        L.orc_rotation_fixed(v[0], v[1], v[2], Rq.ctypes.data_as(C.POINTER(C.c_int32)))
+        ref = Rotation.from_quat([v[0], v[1], v[2], 1.0]).as_matrix()   # scalar-last
+        assert np.abs(Rq.reshape(3, 3) / 2.0 ** 30 - ref).max() <= 2.0 ** -30 + 1e-15
