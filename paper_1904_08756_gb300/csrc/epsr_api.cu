@@ -130,16 +130,20 @@ struct epsr_box {
     SortScratch sort{};
     uint4 *sorted_scaled = nullptr;
     int4 *sorted_coords = nullptr;
-    // Monte Carlo move table
+    // Monte Carlo move table and type-major spatial partition
     MoveRec *moves = nullptr;
     long long moves_cap = 0;
+    int total_mc_cells = 0;
+    SortScratch mc_sort{};
+    int *pos_of = nullptr;
 
     ~epsr_box()
     {
         void *ptrs[] = {boxes, coords, scaled, mol_start, atom_box, atom_mol, thresholds, ep,
                         tiles, hist_box, cta_box, slots, flags, stats, status, U,
                         sort.count, sort.offset, sort.block, sort.key, sort.rank, sort.index,
-                        sorted_scaled, sorted_coords, moves};
+                        sorted_scaled, sorted_coords, moves, mc_sort.count, mc_sort.offset,
+                        mc_sort.block, mc_sort.key, mc_sort.rank, mc_sort.index, pos_of};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -147,7 +151,7 @@ struct epsr_box {
 
 static int validate_desc(const epsr_box_desc &d, int b)
 {
-    if (d.n_atoms < 1 || d.n_atoms > (1LL << 30))
+    if (d.n_atoms < 1 || d.n_atoms > (1LL << 28))
         return set_error(EPSR_EINVAL, "box %d: n_atoms %lld out of range", b, (long long)d.n_atoms);
     if (d.n_mol < 1 || d.n_mol > d.n_atoms)
         return set_error(EPSR_EINVAL, "box %d: n_mol %lld out of range", b, (long long)d.n_mol);
@@ -231,12 +235,20 @@ static void fill_boxdev(const epsr_box_desc &d, const int *type, BoxDev &b)
         }
 }
 
+// Radius (grid units) beyond which a pair has no Coulomb and no empirical-potential term.
+static void set_near(BoxDev &bx)
+{
+    const long long lim = std::max<long long>(bx.rc2, bx.has_ep ? bx.tmax : 0LL);
+    bx.near_fx = (int)std::ceil(std::sqrt((double)lim)) + 1;
+}
+
 static void plan_mc_groups(epsr_box *h)
 {
     // CTAs per box: a single box uses up to one CTA per SM, at least ~512 partner atoms
     // per CTA; a batch splits the budget in proportion to the atom counts.
     const int nb = h->n_boxes;
     const int budget = h->mc_ctas > 0 ? h->mc_ctas : h->sms;
+    h->total_mc_cells = 0;
     std::vector<int> G(nb, 1);
     if (nb == 1) {
         long long want = (h->hb[0].n_atoms + 511) / 512;
@@ -259,9 +271,14 @@ static void plan_mc_groups(epsr_box *h)
     }
     int c0 = 0;
     for (int i = 0; i < nb; ++i) {
-        h->hb[i].cta0 = c0;
-        h->hb[i].n_cta = G[i];
-        h->hb[i].chunk = (h->hb[i].n_atoms + G[i] - 1) / G[i];
+        BoxDev &b = h->hb[i];
+        b.cta0 = c0;
+        b.n_cta = G[i];
+        // slice capacity: the most atoms any CTA gets (atom j goes to CTA j mod G)
+        const long long cap = (b.n_atoms + G[i] - 1) / G[i];
+        b.chunk = (int)cap;
+        b.mc_cell0 = h->total_mc_cells;
+        h->total_mc_cells += b.n_types * G[i] * kMcCells;
         c0 += G[i];
     }
     h->cta_box_len = c0;
@@ -279,6 +296,14 @@ static int upload_mc_groups(epsr_box *h)
     int rc;
     if ((rc = dalloc(&h->cta_box, cb.size())) || (rc = dalloc(&h->slots, 2 * cb.size() * mc_batch_max())) ||
         (rc = dalloc(&h->flags, cb.size())))
+        return rc;
+    if (h->mc_sort.count) cudaFree(h->mc_sort.count);
+    if (h->mc_sort.offset) cudaFree(h->mc_sort.offset);
+    if (h->mc_sort.block) cudaFree(h->mc_sort.block);
+    h->mc_sort.count = h->mc_sort.offset = h->mc_sort.block = nullptr;
+    if ((rc = dalloc(&h->mc_sort.count, h->total_mc_cells + 1)) ||
+        (rc = dalloc(&h->mc_sort.offset, h->total_mc_cells + 1)) ||
+        (rc = dalloc(&h->mc_sort.block, (h->total_mc_cells + 1 + 1023) / 1024)))
         return rc;
     CK(cudaMemcpy(h->cta_box, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->boxes, h->hb.data(), h->hb.size() * sizeof(BoxDev), cudaMemcpyHostToDevice));
@@ -362,8 +387,15 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         int p2 = 1;
         while (p2 < nc) p2 <<= 1;
         bx.cells = nc;
+        bx.cells_p3 = p2 * p2 * p2;
         bx.cell0 = h->total_cells;
         h->total_cells += p2 * p2 * p2;
+        long long ts = 0;
+        for (int t = 0; t < bx.n_types; ++t) {
+            bx.type_start[t] = (int)ts;
+            ts += bx.count[t];
+        }
+        set_near(bx);
         const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
         const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
         bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
@@ -403,7 +435,9 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         (rc = dalloc(&h->sort.block, (h->total_cells + 1023) / 1024)) ||
         (rc = dalloc(&h->sort.key, atom0)) || (rc = dalloc(&h->sort.rank, atom0)) ||
         (rc = dalloc(&h->sort.index, atom0)) ||
-        (rc = dalloc(&h->sorted_scaled, atom0)) || (rc = dalloc(&h->sorted_coords, atom0))) {
+        (rc = dalloc(&h->sorted_scaled, atom0)) || (rc = dalloc(&h->sorted_coords, atom0)) ||
+        (rc = dalloc(&h->mc_sort.key, atom0)) || (rc = dalloc(&h->mc_sort.rank, atom0)) ||
+        (rc = dalloc(&h->mc_sort.index, atom0)) || (rc = dalloc(&h->pos_of, atom0))) {
         delete h;
         return rc;
     }
@@ -553,6 +587,7 @@ extern "C" int epsr_box_set_ep(epsr_box *box, int32_t b, const float *ep, epsr_s
     }
     CK(cudaMemcpyAsync(box->ep + bx.ep_off, ep, n * sizeof(float), cudaMemcpyHostToDevice, (cudaStream_t)stream));
     bx.has_ep = nz;
+    set_near(bx);
     CK(cudaMemcpyAsync(box->boxes + b, &bx, sizeof(BoxDev), cudaMemcpyHostToDevice, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     return EPSR_OK;
@@ -638,8 +673,18 @@ extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint
             if (rc) return rc;
             box->moves_cap = chunk * box->n_boxes;
         }
+        // type-major spatial partition of the partners for this sweep
+        int rc0 = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
+        if (!rc0)
+            rc0 = launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
+                                      box->total_mc_cells + 1, 1, box->mc_sort, nullptr, nullptr,
+                                      box->pos_of, s);
+        if (rc0) return rc0;
         McArgs a;
         memset(&a, 0, sizeof(a));
+        a.sorted_index = box->mc_sort.index;
+        a.pos_of = box->pos_of;
+        a.mc_offset = box->mc_sort.offset;
         a.boxes = box->boxes;
         a.coords = box->coords;
         a.mol_start = box->mol_start;
@@ -664,8 +709,8 @@ extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint
         a.chunk = chunk;
         for (long long c0 = 0; c0 < n_moves; c0 += chunk) {
             const long long n = std::min(chunk, n_moves - c0);
-            int rc = launch_mc_moves(box->boxes, box->n_boxes, chunk, n, seed, move0 + (uint64_t)c0,
-                                     box->moves, s);
+            int rc = launch_mc_moves(box->boxes, box->mol_start, box->n_boxes, chunk, n, seed,
+                                     move0 + (uint64_t)c0, box->moves, s);
             if (rc) return rc;
             a.n_moves = n;
             a.move0 = move0 + (uint64_t)c0;
@@ -699,7 +744,8 @@ static int gr_range(epsr_box *box, long long t0, long long t1, uint64_t *hist, c
     int rc = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
     if (rc) return rc;
     rc = launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
-                             box->total_cells, box->sort, box->sorted_scaled, box->sorted_coords, s);
+                             box->total_cells, 0, box->sort, box->sorted_scaled, box->sorted_coords,
+                             nullptr, s);
     if (rc) return rc;
     GrArgs a;
     a.boxes = box->boxes;

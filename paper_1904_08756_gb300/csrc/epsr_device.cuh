@@ -51,7 +51,10 @@ struct BoxDev {
     float rc2_lo, rc2_hi; // rc2 * (1 -/+ 2^-20) as floats: the exact test runs only between
     float tmax_lo, tmax_hi;   // tmax * (1 -/+ 2^-20)
     int32_t cell0;        // first global cell of this box (spatial sort)
-    int32_t pad1;
+    int32_t cells_p3;     // cells per box in the sort key space (power of two cubed)
+    int32_t mc_cell0;     // first key of this box in the type-major sort
+    int32_t near_fx;      // ceil(sqrt(max(rc2, tmax if an EP is set))), grid units
+    int32_t type_start[kMaxTypes];  // first type-major sorted position of each type (box-local)
     int64_t count[kMaxTypes];   // atoms per type
     PairRow row[kMaxTypes * kMaxTypes];
 };
@@ -257,13 +260,15 @@ __device__ inline void rotation_fixed(double vx, double vy, double vz, int *Rq)
     for (int i = 0; i < 9; ++i) Rq[i] = (int)__double2ll_rn(__dmul_rn(R[i], 1073741824.0));
 }
 
-// Configuration-independent part of one Monte Carlo move (64 bytes).
+// Configuration-independent part of one Monte Carlo move (80 bytes).
 struct __align__(16) MoveRec {
     int mol;
     int shift[3];
     int R[9];        // rotation matrix * 2^30, rounded
     float thr;       // FP32 rounded up from -kT ln u_acc
     double u_acc;
+    int a0, m;       // first atom (box-local) and atom count of the molecule
+    int pad[2];
 };
 
 // ---- device status word ------------------------------------------------------------------
@@ -287,6 +292,23 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed_gpu(const int *p)

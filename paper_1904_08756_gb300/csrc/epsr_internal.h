@@ -17,7 +17,7 @@ int set_error(int status, const char *fmt, ...);
 int set_cuda_error(cudaError_t e, const char *what);
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
-constexpr size_t kMcMaxDynSmem = 200 * 1024;
+constexpr size_t kMcMaxDynSmem = 190 * 1024;
 
 struct McArgs {
     const BoxDev *boxes;
@@ -31,6 +31,9 @@ struct McArgs {
     epsr_mc_stats *stats;         // [n_boxes] running totals (device)
     epsr_move_log *log;           // nullable [n_boxes][log_stride]
     const MoveRec *moves;         // [n_boxes][chunk] this launch's moves
+    const int *sorted_index;      // [n_atoms_total] atom at each type-major sorted position
+    const int *pos_of;            // [n_atoms_total] sorted position of each atom
+    const int *mc_offset;         // [total keys + 1] first sorted position of each key
     long long chunk;              // move-table stride per box
     long long log_off;            // log index of this launch's first move
     int *status;                  // device status word
@@ -47,8 +50,8 @@ struct McArgs {
 };
 
 int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stream);
-int launch_mc_moves(const BoxDev *boxes, int n_boxes, long long chunk, long long n,
-                    unsigned long long seed, unsigned long long move0, MoveRec *out,
+int launch_mc_moves(const BoxDev *boxes, const int *mol_start, int n_boxes, long long chunk,
+                    long long n, unsigned long long seed, unsigned long long move0, MoveRec *out,
                     cudaStream_t stream);
 int mc_threads();
 int mc_batch_max();
@@ -73,6 +76,7 @@ struct GrArgs {
 };
 
 constexpr int kGrTile = 1024;    // atoms per tile (both sides)
+constexpr int kMcCells = 512;    // cells per (type, CTA) block of the Monte Carlo order
 
 int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *coords,
                         uint4 *scaled, long long n, cudaStream_t stream);
@@ -86,8 +90,9 @@ struct SortScratch {      // device scratch of the spatial sort
     int *index;           // [n_atoms_total] atom index at each sorted position
 };
 int launch_spatial_sort(const BoxDev *boxes, const int *atom_box, const uint4 *scaled,
-                        const int4 *coords, long long n, int total_cells, SortScratch sc,
-                        uint4 *s_scaled, int4 *s_coords, cudaStream_t stream);
+                        const int4 *coords, long long n, int total_cells, int type_major,
+                        SortScratch sc, uint4 *s_scaled, int4 *s_coords, int *pos_of,
+                        cudaStream_t stream);
 int launch_normalize_g(const BoxDev *boxes, int n_boxes, const unsigned long long *hist,
                        float *g, long long n_configs, long long hist_len, const long long *hist_box,
                        cudaStream_t stream);

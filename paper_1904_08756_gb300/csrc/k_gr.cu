@@ -62,8 +62,11 @@ __device__ __forceinline__ unsigned spread5(unsigned v)
     return v;
 }
 
+// Sort key: the Morton code of the atom's cell, offset by the box's first cell. With
+// type_major the key space of a box is split into one block of cells per atom type, so
+// the sorted order is type by type, each spatially ordered.
 __global__ void cell_key_kernel(const BoxDev *boxes, const int *atom_box, const uint4 *scaled,
-                                int *key, int *rank, int *count, long long n)
+                                int *key, int *rank, int *count, long long n, int type_major)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -71,7 +74,17 @@ __global__ void cell_key_kernel(const BoxDev *boxes, const int *atom_box, const 
         const uint4 s = scaled[i];
         const unsigned nc = (unsigned)b.cells;
         const unsigned cx = __umulhi(s.x, nc), cy = __umulhi(s.y, nc), cz = __umulhi(s.z, nc);
-        const int k = b.cell0 + (int)(spread5(cx) | (spread5(cy) << 1) | (spread5(cz) << 2));
+        int k;
+        if (type_major) {
+            // Monte Carlo partition: atom i of the box goes to CTA (i mod G) of its group;
+            // inside a CTA's share of a type, atoms are ordered by an 8^3 Morton cell.
+            const unsigned c8x = __umulhi(s.x, 8u), c8y = __umulhi(s.y, 8u), c8z = __umulhi(s.z, 8u);
+            const int code8 = (int)(spread5(c8x) | (spread5(c8y) << 1) | (spread5(c8z) << 2));
+            const int r = (int)((i - b.atom0) % b.n_cta);
+            k = b.mc_cell0 + ((int)s.w * b.n_cta + r) * kMcCells + code8;
+        } else {
+            k = b.cell0 + (int)(spread5(cx) | (spread5(cy) << 1) | (spread5(cz) << 2));
+        }
         key[i] = k;
         rank[i] = atomicAdd(&count[k], 1);
     }
@@ -164,11 +177,12 @@ __global__ void scatter_index_kernel(const int *key, const int *rank, const int 
 }
 
 // Makes the order deterministic: each cell's segment (a few atoms) is put in atom-index
-// order, then the coordinates are gathered in that order. Ranks from the counting pass
-// depend on atomic timing; the final order depends only on the coordinates.
+// order, then (optionally) the coordinates are gathered in that order and the inverse map
+// atom -> sorted position is written. Ranks from the counting pass depend on atomic timing;
+// the final order depends only on the coordinates.
 __global__ void cell_order_kernel(const int *count, const int *offset, int total_cells,
                                   int *idx, const uint4 *scaled, const int4 *coords,
-                                  uint4 *s_scaled, int4 *s_coords)
+                                  uint4 *s_scaled, int4 *s_coords, int *pos_of)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < total_cells; c += gridDim.x * blockDim.x) {
         const int b = offset[c], n = count[c];
@@ -183,29 +197,32 @@ __global__ void cell_order_kernel(const int *count, const int *offset, int total
         }
         for (int a = 0; a < n; ++a) {
             const int i = idx[b + a];
-            s_scaled[b + a] = scaled[i];
-            s_coords[b + a] = coords[i];
+            if (s_scaled) s_scaled[b + a] = scaled[i];
+            if (s_coords) s_coords[b + a] = coords[i];
+            if (pos_of) pos_of[i] = b + a;
         }
     }
 }
 
 int launch_spatial_sort(const BoxDev *boxes, const int *atom_box, const uint4 *scaled,
-                        const int4 *coords, long long n, int total_cells, SortScratch sc,
-                        uint4 *s_scaled, int4 *s_coords, cudaStream_t stream)
+                        const int4 *coords, long long n, int total_cells, int type_major,
+                        SortScratch sc, uint4 *s_scaled, int4 *s_coords, int *pos_of,
+                        cudaStream_t stream)
 {
     if (n == 0) return EPSR_OK;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     const int nblk = (total_cells + kScanBlock - 1) / kScanBlock;
     cudaError_t e = cudaMemsetAsync(sc.count, 0, (size_t)total_cells * sizeof(int), stream);
     if (e != cudaSuccess) return set_cuda_error(e, "sort memset");
-    cell_key_kernel<<<grid, 256, 0, stream>>>(boxes, atom_box, scaled, sc.key, sc.rank, sc.count, n);
+    cell_key_kernel<<<grid, 256, 0, stream>>>(boxes, atom_box, scaled, sc.key, sc.rank, sc.count, n,
+                                              type_major);
     scan_block_sums_kernel<<<nblk, kScanBlock, 0, stream>>>(sc.count, total_cells, sc.block);
     scan_block_offsets_kernel<<<1, 1024, 0, stream>>>(sc.block, nblk);
     scan_finish_kernel<<<nblk, kScanBlock, 0, stream>>>(sc.count, total_cells, sc.block, sc.offset);
     scatter_index_kernel<<<grid, 256, 0, stream>>>(sc.key, sc.rank, sc.offset, sc.index, n);
     const int cgrid = (total_cells + 255) / 256 < 4096 ? (total_cells + 255) / 256 : 4096;
     cell_order_kernel<<<cgrid, 256, 0, stream>>>(sc.count, sc.offset, total_cells, sc.index, scaled,
-                                                 coords, s_scaled, s_coords);
+                                                 coords, s_scaled, s_coords, pos_of);
     e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "spatial sort");
 }

@@ -32,10 +32,12 @@ namespace epsr {
 constexpr int kMcThreads = 512;
 constexpr int kMcWarps = kMcThreads / 32;
 constexpr int kBatchMax = kMcWarps;            // one move per warp
+constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
-__global__ void mc_moves_kernel(const BoxDev *boxes, int n_boxes, long long chunk, long long n,
-                                unsigned long long seed, unsigned long long move0, MoveRec *out)
+__global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n_boxes,
+                                long long chunk, long long n, unsigned long long seed,
+                                unsigned long long move0, MoveRec *out)
 {
     const long long total = (long long)n_boxes * chunk;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -55,6 +57,8 @@ __global__ void mc_moves_kernel(const BoxDev *boxes, int n_boxes, long long chun
         }
         MoveRec m;
         m.mol = (int)(((unsigned long long)w[0] * (unsigned long long)bx.n_mol) >> 32);
+        m.a0 = mol_start[bx.mol0 + m.mol];
+        m.m = mol_start[bx.mol0 + m.mol + 1] - m.a0;
         const unsigned span = 2u * (unsigned)bx.max_shift + 1u;
         for (int a = 0; a < 3; ++a) m.shift[a] = (int)(w[1 + a] % span) - bx.max_shift;
         if (bx.move_kind == EPSR_MOVE_RIGID_MOLECULE) {
@@ -74,13 +78,13 @@ __global__ void mc_moves_kernel(const BoxDev *boxes, int n_boxes, long long chun
     }
 }
 
-int launch_mc_moves(const BoxDev *boxes, int n_boxes, long long chunk, long long n,
-                    unsigned long long seed, unsigned long long move0, MoveRec *out,
+int launch_mc_moves(const BoxDev *boxes, const int *mol_start, int n_boxes, long long chunk,
+                    long long n, unsigned long long seed, unsigned long long move0, MoveRec *out,
                     cudaStream_t stream)
 {
     const long long total = (long long)n_boxes * chunk;
     const int grid = (int)((total + 127) / 128 < 8192 ? (total + 127) / 128 : 8192);
-    mc_moves_kernel<<<grid, 128, 0, stream>>>(boxes, n_boxes, chunk, n, seed, move0, out);
+    mc_moves_kernel<<<grid, 128, 0, stream>>>(boxes, mol_start, n_boxes, chunk, n, seed, move0, out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "mc_moves");
 }
@@ -98,11 +102,20 @@ struct McShared {
     int4 oldp[kBatchMax][kMaxMolAtoms];
     int natoms[kBatchMax];
     int a0[kBatchMax];
+    int spos[kBatchMax][kMaxMolAtoms];   // type-major sorted position of each moved atom
+    int hw[kBatchMax];                   // half width of the near cube around old atom 0
+    // this CTA's partners: per type t, sorted positions [rs[t], rs[t] + rl[t]) held at
+    // slice slots [blk[t], blk[t + 1])
+    int rs[kMaxTypes];
+    int rl[kMaxTypes];
+    int blk[kMaxTypes + 1];
     float thr[kBatchMax];
     double u_acc[kBatchMax];
     float part[kBatchMax];
     float base[kBatchMax];
-    float corr_part[kBatchMax][kBatchMax][kMaxMolAtoms];
+    float corr_part[kBatchMax * (kBatchMax - 1) / 2 * kMaxMolAtoms];
+    int mm;                                  // largest molecule of the batch
+    MoveRec mv[kMoveBlock];                  // staged move records [mv_base, mv_base + kMoveBlock)
     float corr[kBatchMax][kBatchMax];
     float dU[kBatchMax];
     int abort_flag;
@@ -125,6 +138,96 @@ __device__ __forceinline__ int floordiv32(int a, int b)   // b > 0
     return q;
 }
 
+// Out-of-line copy of pair_du for code that runs once per batch (keeps the kernel small).
+__device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, const BoxDev &bx,
+                                           const long long *T, const float *ep)
+{
+    return pair_du(sn, so, pr, bx, T, ep);
+}
+
+// Partial dU of one move (atoms np/op, m <= M) against the partners of this CTA, lane-
+// strided. Per partner type the kind of each moved atom's pair row is uniform across the
+// warp: with Lennard-Jones every partner is evaluated (LJ is not cut); without, only
+// partners inside the near cube around old atom 0 (half width hw) can have Coulomb or
+// empirical-potential terms. M is a compile-time bound so the atom loop unrolls into
+// independent dependency chains.
+template <int M>
+__device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int m, int a0, int hw,
+                                             const int4 *slice, const int *blk, const BoxDev &bx,
+                                             const long long *T, const float *ep, int lane)
+{
+    const int L = bx.L;
+    const int4 o0 = op[0];
+    int4 pn[M], po[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < m) { pn[a] = np[a]; po[a] = op[a]; }
+    float acc = 0.f;
+    for (int t = 0; t < bx.n_types; ++t) {
+        unsigned lj = 0u, nr = 0u;
+        PairRow pr[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            if (a >= m) continue;
+            pr[a] = bx.row[pn[a].w * kMaxTypes + t];
+            if (pr[a].c12 != 0.f || pr[a].c6 != 0.f) lj |= 1u << a;
+            else if (pr[a].kqq != 0.f || bx.has_ep) nr |= 1u << a;
+        }
+        if (!(lj | nr)) continue;
+        const int jb = blk[t + 1];
+#pragma unroll 2
+        for (int j = blk[t] + lane; j < jb; j += 32) {
+            int4 pj = slice[j];
+            const int jatom = pj.w >> 3;
+            const bool self = jatom >= a0 && jatom < a0 + m;
+            pj.w = t;
+            const bool near = nr && mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw &&
+                              mi_abs(pj.z - o0.z, L) < hw;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                if (a < m && !self && (((lj >> a) & 1u) || (((nr >> a) & 1u) && near)))
+                    acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), pr[a], bx, T, ep);
+            }
+        }
+    }
+    return acc;
+}
+
+// The same for any molecule size (atoms read from shared memory; out-of-line pair function).
+__device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, int m, int a0, int hw,
+                                              const int4 *slice, const int *blk, const BoxDev &bx,
+                                              const long long *T, const float *ep, int lane)
+{
+    const int L = bx.L;
+    const int4 o0 = op[0];
+    float acc = 0.f;
+    for (int t = 0; t < bx.n_types; ++t) {
+        unsigned lj = 0u, nr = 0u;
+        for (int a = 0; a < m; ++a) {
+            const PairRow &pr = bx.row[np[a].w * kMaxTypes + t];
+            if (pr.c12 != 0.f || pr.c6 != 0.f) lj |= 1u << a;
+            else if (pr.kqq != 0.f || bx.has_ep) nr |= 1u << a;
+        }
+        if (!(lj | nr)) continue;
+        for (int j = blk[t] + lane; j < blk[t + 1]; j += 32) {
+            int4 pj = slice[j];
+            const int jatom = pj.w >> 3;
+            if (jatom >= a0 && jatom < a0 + m) continue;
+            pj.w = t;
+            const bool near = nr && mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw &&
+                              mi_abs(pj.z - o0.z, L) < hw;
+            const unsigned todo = lj | (near ? nr : 0u);
+            for (int a = 0; a < m; ++a) {
+                if ((todo >> a) & 1u) {
+                    const int4 pn = np[a], po = op[a];
+                    acc += pair_du_cold(sep(pn, pj, L), sep(po, pj, L), bx.row[pn.w * kMaxTypes + t], bx, T, ep);
+                }
+            }
+        }
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -142,34 +245,65 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     }
     __syncthreads();
     const BoxDev &bx = sh.bx;
+
     const int G = bx.n_cta;
     const int rank = cta - bx.cta0;
     const int L = bx.L;
-    const int j_begin = min(bx.n_atoms, rank * bx.chunk);
-    const int j_end = min(bx.n_atoms, j_begin + bx.chunk);
-    const int n_slice = j_end - j_begin;
+    const int nt = bx.n_types;
     const bool rigid = bx.move_kind == EPSR_MOVE_RIGID_MOLECULE;
+    // Partners of this CTA: the atoms i of the box with i mod G == rank (an even share of
+    // every region and type), grouped by type and ordered in space within each type.
+    if (tid == 0) {
+        int b = 0;
+        for (int t = 0; t < nt; ++t) {
+            const int key0 = bx.mc_cell0 + (t * G + rank) * kMcCells;
+            const int s0 = A.mc_offset[key0] - (int)bx.atom0;
+            const int s1 = A.mc_offset[key0 + kMcCells] - (int)bx.atom0;
+            sh.rs[t] = s0;
+            sh.rl[t] = s1 - s0;
+            sh.blk[t] = b;
+            b += s1 - s0;
+        }
+        sh.blk[nt] = b;
+    }
+    __syncthreads();
+    const int n_slice = sh.blk[nt];
 
-    // shared memory: partner slice, thresholds, empirical potential
+    // shared memory: partner slice {x, y, z, type | atom << 3}, thresholds, empirical potential
     int4 *slice = reinterpret_cast<int4 *>(dyn);
     long long *T = reinterpret_cast<long long *>(slice + A.slice_cap);
     float *ep = reinterpret_cast<float *>(T + A.tbl_cap);
-    for (int j = tid; j < n_slice; j += kMcThreads) slice[j] = A.coords[bx.atom0 + j_begin + j];
+    for (int t = 0; t < nt; ++t)
+        for (int i = tid; i < sh.rl[t]; i += kMcThreads) {
+            const int atom = A.sorted_index[bx.atom0 + sh.rs[t] + i] - (int)bx.atom0;
+            int4 c = A.coords[bx.atom0 + atom];
+            c.w = c.w | (atom << 3);
+            slice[sh.blk[t] + i] = c;
+        }
     for (int k = tid; k <= bx.n_bins; k += kMcThreads) T[k] = A.thresholds[bx.tbl_off + k];
     if (bx.has_ep)
         for (int k = tid; k < bx.n_pairs * bx.n_bins; k += kMcThreads) ep[k] = A.ep[bx.ep_off + k];
     __syncthreads();
 
-    const int *mol_start = A.mol_start + bx.mol0;
     const MoveRec *moves = A.moves + (size_t)box * A.chunk;
     unsigned seq = 0;
     int par = 0;
 
+    long long mv_base = 0, mv_end = 0;
     for (long long t0 = 0; t0 < A.n_moves; par ^= 1) {
         const int kmax = (int)min((long long)A.batch_k, A.n_moves - t0);
+        if (t0 + kmax > mv_end) {           // stage the next block of move records
+            mv_base = t0;
+            mv_end = min(A.n_moves, t0 + kMoveBlock);
+            const int4 *src = reinterpret_cast<const int4 *>(moves + mv_base);
+            int4 *dst = reinterpret_cast<int4 *>(sh.mv);
+            const int n4 = (int)(mv_end - mv_base) * (int)(sizeof(MoveRec) / sizeof(int4));
+            for (int i = tid; i < n4; i += kMcThreads) dst[i] = src[i];
+            __syncthreads();
+        }
         // ---- A. molecules of the batch; it ends before the first repeated molecule -----------
         if (warp == 0) {
-            const int my = lane < kmax ? moves[t0 + lane].mol : -1 - lane;
+            const int my = lane < kmax ? sh.mv[t0 + lane - mv_base].mol : -1 - lane;
             bool dup = false;
 #pragma unroll
             for (int k1 = 0; k1 < kBatchMax; ++k1) {
@@ -177,7 +311,10 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 dup |= (k1 < lane) && (o == my);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, dup && lane < kmax);
-            if (lane == 0) sh.nb[par] = bal ? __ffs(bal) - 1 : kmax;
+            if (lane == 0) {
+                sh.nb[par] = bal ? __ffs(bal) - 1 : kmax;
+                sh.mm = 0;
+            }
             if (lane < kBatchMax) sh.mol[par][lane] = my;
         }
         __syncthreads();
@@ -185,16 +322,18 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         // ---- B. current and trial coordinates of each moved molecule (integer arithmetic) ----
         if (warp < nb) {
             const int k = warp;
-            const MoveRec &mr = moves[t0 + k];
+            const MoveRec &mr = sh.mv[t0 + k - mv_base];
             const int mol = sh.mol[par][k];
-            const int a0 = mol_start[mol], m = mol_start[mol + 1] - a0;
+            const int a0 = mr.a0, m = mr.m;
             const int q = par ^ 1;
             int pidx = -1;
             for (int p = 0; p < sh.nb[q]; ++p)
                 if (sh.acc[q][p] && sh.mol[q][p] == mol) pidx = p;
-            if (lane < m)
+            if (lane < m) {
                 sh.oldp[k][lane] = pidx >= 0 ? sh.newp[q][pidx][lane]
                                              : __ldcg(&A.coords[bx.atom0 + a0 + lane]);
+                sh.spos[k][lane] = A.pos_of[bx.atom0 + a0 + lane] - (int)bx.atom0;
+            }
             __syncwarp();
             if (lane < 3 * m) {
                 const int kk = lane / 3, a = lane - 3 * kk;
@@ -225,58 +364,68 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 if (a == 0) dst[3] = op[kk].w;
             }
             if (lane == 0) {
+                atomicMax(&sh.mm, m);
                 sh.natoms[k] = m;
                 sh.a0[k] = a0;
                 sh.thr[k] = mr.thr;
                 sh.u_acc[k] = mr.u_acc;
             }
+            __syncwarp();
+            // near cube: every old and new atom position lies within `reach` of old atom 0
+            int reach = 0;
+            if (lane < 2 * m) {
+                const int4 p = lane < m ? sh.oldp[k][lane] : sh.newp[par][k][lane - m];
+                const int4 o = sh.oldp[k][0];
+                reach = max(mi_abs(p.x - o.x, L), max(mi_abs(p.y - o.y, L), mi_abs(p.z - o.z, L)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) reach = max(reach, __shfl_xor_sync(0xffffffffu, reach, o));
+            if (lane == 0) sh.hw[k] = bx.near_fx + reach + 2;
         }
         __syncthreads();
         // ---- C. partial dU of move `warp` against this CTA's slice ---------------------------
         if (warp < nb) {
             const int m = sh.natoms[warp];
-            const int a0 = sh.a0[warp];
-            const int4 *np = sh.newp[par][warp];
-            const int4 *op = sh.oldp[warp];
-            float acc = 0.f;
-            for (int j = lane; j < n_slice; j += 32) {
-                const int jg = j_begin + j;
-                if (jg >= a0 && jg < a0 + m) continue;
-                const int4 pj = slice[j];
-                for (int a = 0; a < m; ++a) {
-                    const int4 pn = np[a], po = op[a];
-                    const PairRow pr = bx.row[pn.w * kMaxTypes + pj.w];
-                    acc += pair_du(sep(pn, pj, L), sep(po, pj, L), pr, bx, T, ep);
-                }
-            }
+            float acc;
+            if (m == 1)
+                acc = partner_sum<1>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
+                                     slice, sh.blk, bx, T, ep, lane);
+            else if (m <= 3)
+                acc = partner_sum<3>(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                                     slice, sh.blk, bx, T, ep, lane);
+            else
+                acc = partner_sum_any(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                                      slice, sh.blk, bx, T, ep, lane);
             acc = warp_sum(acc);
             if (lane == 0) sh.part[warp] = acc;
         }
         __syncthreads();
         // ---- D. gather the partials of the box's CTA group (one bounded grid barrier) -------
+        // Arrival: the partials, then a release add on the group's counter. Wait: one thread
+        // polls the counter with relaxed loads (no serialising acquires), then one acquire
+        // fence orders the reads of the other CTAs' partials after the observed arrivals.
         ++seq;
         if (G > 1) {
-            float *slot = A.slots + ((size_t)(seq & 1u) * A.grid + cta) * kBatchMax;
-            if (tid == 0 && cta != A.skip_arrival_cta) {
-                for (int k = 0; k < nb; ++k) slot[k] = sh.part[k];
-                st_release_gpu(&A.flags[cta], seq);
-            }
-            if (warp == 0) {
+            if (tid == 0) {
+                float *slot = A.slots + ((size_t)(seq & 1u) * A.grid + cta) * kBatchMax;
+                if (cta != A.skip_arrival_cta) {
+                    for (int k = 0; k < nb; ++k) slot[k] = sh.part[k];
+                    red_add_release_gpu(&A.flags[box], 1u);
+                }
+                const unsigned target = seq * (unsigned)G;
                 const uint64_t t_start = globaltimer_ns();
                 long long it = 0;
                 bool timed_out = false;
-                for (;;) {
-                    bool ready = true;
-                    for (int r = lane; r < G; r += 32)
-                        ready &= ld_acquire_gpu(&A.flags[bx.cta0 + r]) >= seq;
-                    if (__all_sync(0xffffffffu, ready)) break;
-                    if ((++it & 63) == 0) {
-                        const bool stop = (globaltimer_ns() - t_start > A.timeout_ns) ||
-                                          it > A.max_spin || ld_relaxed_gpu(A.status) != 0;
-                        if (__any_sync(0xffffffffu, stop)) { timed_out = true; break; }
+                while (ld_relaxed_gpu_u32(&A.flags[box]) < target) {
+                    if ((++it & 255) == 0 &&
+                        ((globaltimer_ns() - t_start > A.timeout_ns) || it > A.max_spin ||
+                         ld_relaxed_gpu(A.status) != 0)) {
+                        timed_out = true;
+                        break;
                     }
                 }
-                if (timed_out && lane == 0) {
+                fence_acq_rel_gpu();
+                if (timed_out) {
                     atomicOr(A.status, kStatusTimeout);
                     sh.abort_flag = 1;
                 }
@@ -294,28 +443,36 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             sh.base[tid] = sh.part[tid];
         }
         // ---- E. pair-energy corrections between the batch's moved molecules -----------------
-        // item (k1, k, a): atom a of move k against the whole molecule of an earlier move k1
-        for (int it = tid; it < nb * nb * kMaxMolAtoms; it += kMcThreads) {
-            const int a = it % kMaxMolAtoms, pq = it / kMaxMolAtoms;
-            const int k1 = pq / nb, k = pq % nb;
-            if (k1 >= k || a >= sh.natoms[k]) continue;
-            const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
-            float c = 0.f;
-            for (int b = 0; b < sh.natoms[k1]; ++b) {
-                const int4 nb1 = sh.newp[par][k1][b], ob1 = sh.oldp[k1][b];
-                const PairRow pr = bx.row[na.w * kMaxTypes + nb1.w];
-                c += pair_du(sep(na, nb1, L), sep(oa, nb1, L), pr, bx, T, ep) -
-                     pair_du(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
+        // item (pair k1 < k, atom a of move k) against the whole molecule of move k1
+        {
+            const int mm = sh.mm;
+            const int npq = nb * (nb - 1) / 2;
+            for (int it = tid; it < npq * mm; it += kMcThreads) {
+                const int pq = it / mm, a = it - pq * mm;
+                int k = 1;
+                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k1 = pq - k * (k - 1) / 2;
+                float c = 0.f;
+                if (a < sh.natoms[k]) {
+                    const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
+                    for (int b = 0; b < sh.natoms[k1]; ++b) {
+                        const int4 nb1 = sh.newp[par][k1][b], ob1 = sh.oldp[k1][b];
+                        const PairRow pr = bx.row[na.w * kMaxTypes + nb1.w];
+                        c += pair_du_cold(sep(na, nb1, L), sep(oa, nb1, L), pr, bx, T, ep) -
+                             pair_du_cold(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
+                    }
+                }
+                sh.corr_part[it] = c;
             }
-            sh.corr_part[k1][k][a] = c;
-        }
-        __syncthreads();
-        for (int pq = tid; pq < nb * nb; pq += kMcThreads) {
-            const int k1 = pq / nb, k = pq % nb;
-            if (k1 >= k) continue;
-            float c = 0.f;
-            for (int a = 0; a < sh.natoms[k]; ++a) c += sh.corr_part[k1][k][a];
-            sh.corr[k1][k] = c;
+            __syncthreads();
+            for (int pq = tid; pq < npq; pq += kMcThreads) {
+                int k = 1;
+                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k1 = pq - k * (k - 1) / 2;
+                float c = 0.f;
+                for (int i = 0; i < mm; ++i) c += sh.corr_part[pq * mm + i];
+                sh.corr[k1][k] = c;
+            }
         }
         __syncthreads();
         // ---- F. Metropolis decisions of the batch, in order (warp 0, lane k = move k) -------
@@ -354,7 +511,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             if (!sh.acc[par][k] || a >= sh.natoms[k]) continue;
             const int ja = sh.a0[k] + a;
             const int4 p = sh.newp[par][k][a];
-            if (ja >= j_begin && ja < j_end) slice[ja - j_begin] = p;
+            const int t = p.w, sp = sh.spos[k][a] - sh.rs[t];
+            if (sp >= 0 && sp < sh.rl[t]) slice[sh.blk[t] + sp] = make_int4(p.x, p.y, p.z, t | (ja << 3));
             if (rank == 0) A.coords[bx.atom0 + ja] = p;
         }
         if (rank == 0 && A.log && tid < nb) {
@@ -372,6 +530,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         __syncthreads();
         t0 += nb;
     }
+
     if (rank == 0 && tid == 0) {
         epsr_mc_stats *st = A.stats + box;
         st->attempted += sh.st_att;
