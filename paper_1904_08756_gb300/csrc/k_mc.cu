@@ -303,12 +303,12 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         }
         // ---- A. molecules of the batch; it ends before the first repeated molecule -----------
         if (warp == 0) {
-            const int my = lane < kmax ? sh.mv[t0 + lane - mv_base].mol : -1 - lane;
+            int my = -1 - lane;
             bool dup = false;
-#pragma unroll
-            for (int k1 = 0; k1 < kBatchMax; ++k1) {
-                const int o = __shfl_sync(0xffffffffu, my, k1);
-                dup |= (k1 < lane) && (o == my);
+            if (lane < kmax) {
+                const MoveRec *mv = sh.mv + (t0 - mv_base);
+                my = mv[lane].mol;
+                for (int k1 = 0; k1 < lane; ++k1) dup |= mv[k1].mol == my;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, dup && lane < kmax);
             if (lane == 0) {
