@@ -229,6 +229,31 @@ int epsr_normalize_g(epsr_box *box, const uint64_t *hist, float *g, int64_t n_co
  * pair (b in 1e-12 cm so S is in barn) and flat = sum_a c_a b_a^2. Host only. */
 int epsr_sq_weights(const epsr_box *box, int32_t b, double *w, double *flat);
 
+/* ---- pair histogram without device allocation -----------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that must not
+ * allocate device memory when they need the counts -- code running while a CUDA graph
+ * is being captured, plug-ins whose host framework's caching allocator owns the device
+ * memory, or real-time loops that may not call cudaMalloc/cudaFree after start-up.
+ *
+ * epsr_partial_gr_noalloc adds to hist the same counts epsr_partial_gr adds for a
+ * one-box handle with the same coordinates, types and bins, and allocates nothing: all
+ * working memory is one fixed __device__ array of epsr_noalloc_scratch_bytes() bytes
+ * (about 12.6 MB) that every GPU loading the library holds until the process exits.
+ *   xyz, type   HOST int32 [n_atoms][3] in [0, L_fx) and [n_atoms] in [0, n_types)
+ *               (validated; copied into the array, so they may be reused on return)
+ *   n_atoms     1 .. EPSR_NOALLOC_MAX_ATOMS; larger boxes are rejected with EPSR_EINVAL
+ *   hist        device uint64 [n_types (n_types + 1) / 2][n_bins], accumulated
+ * The first call on a device, made while that device is current, looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array, so calls whose GPU work overlaps (other streams, other
+ * host threads on the same device) race and corrupt each other's counts: serialise them.
+ * Work is enqueued on `stream`; the host arrays are consumed before the call returns. */
+#define EPSR_NOALLOC_MAX_ATOMS 131072
+size_t epsr_noalloc_scratch_bytes(void);
+int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, int64_t n_atoms,
+                            int64_t L_fx, int32_t scale_log2, int32_t n_types, int32_t bin_p,
+                            int32_t bin_q, int32_t n_bins, uint64_t *hist, epsr_stream_t stream);
+
 /* ---- S(Q) by Eq. (1) ---------------------------------------------------------------------
  * Midpoint rule on bin centres r_k = (k + 1/2) dr:
  *   S_partial[c](Q_i) = w[c] sum_k K[i][k] (g[c][k] - 1),  K[i][k] = r_k^2 dr sin(Q_i r_k)/(Q_i r_k)

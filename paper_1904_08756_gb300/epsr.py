@@ -31,6 +31,7 @@ EXPORTS = [
     "epsr_mc_set_batch", "epsr_mc_set_ctas", "epsr_debug_barrier_fault",
     "epsr_partial_gr", "epsr_partial_gr_tiles", "epsr_partial_gr_range", "epsr_normalize_g",
     "epsr_sq_weights", "epsr_sq_plan_create", "epsr_sq_plan_destroy", "epsr_sq_exec", "epsr_sq",
+    "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc",
 ]
 
 
@@ -103,6 +104,8 @@ def lib():
             "epsr_sq_plan_destroy": ([vp], C.c_int),
             "epsr_sq_exec": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], C.c_int),
             "epsr_sq": ([vp, i32, i32, dbl, vp, i32, vp, i32, vp, vp, vp, i32, vp], C.c_int),
+            "epsr_noalloc_scratch_bytes": ([], C.c_size_t),
+            "epsr_partial_gr_noalloc": ([vp, vp, i64, i64, i32, i32, i32, i32, i32, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -331,3 +334,20 @@ def epsr_sq(g, dr: float, Q: np.ndarray, w: np.ndarray, cols_per_set: int, flat:
     _check(lib().epsr_sq(_dev_ptr(g), g.shape[0], g.shape[1], dr, _np_ptr(q), len(q), _np_ptr(w),
                          cols_per_set, _np_ptr(flat), _dev_ptr(S_partial), _dev_ptr(S_total),
                          mode, _stream(stream)), "epsr_sq")
+
+
+NOALLOC_MAX_ATOMS = 131072
+
+
+def epsr_noalloc_scratch_bytes() -> int:
+    return lib().epsr_noalloc_scratch_bytes()
+
+
+def epsr_partial_gr_noalloc(system, hist, stream=None):
+    """Pair histogram of one box with no device allocation (fixed library scratch); the
+    coordinates and types are taken from host arrays of a synth.System-like object."""
+    xyz = np.ascontiguousarray(system.xyz, np.int32)
+    typ = np.ascontiguousarray(system.type, np.int32)
+    _check(lib().epsr_partial_gr_noalloc(_np_ptr(xyz), _np_ptr(typ), xyz.shape[0], system.L_fx, 20,
+                                         system.n_types, system.bin_p, system.bin_q, system.n_bins,
+                                         _dev_ptr(hist), _stream(stream)), "epsr_partial_gr_noalloc")
