@@ -154,6 +154,76 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------
+# Replicas: 64 boxes of uneven size advanced together, each step captured as a CUDA graph
+# ------------------------------------------------------------------------------------------
+
+def run_replicas(args):
+    import torch
+    from paper_1904_08756_gb300 import build, epsr, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if not os.path.exists(epsr.LIB_PATH):
+        build.build()
+    systems = synth.replica_batch()
+    nb = len(systems)
+    box = epsr.Box(systems)
+    ws = np.concatenate([box.epsr_sq_weights(b)[0] for b in range(nb)])
+    flats = np.array([box.epsr_sq_weights(b)[1] for b in range(nb)])
+    plan = epsr.SqPlan(systems[0].Q, 600, 0.02, epsr.SQ_FP32, max_cols=3 * nb)
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=dev)
+    g = torch.zeros(box.hist_len, dtype=torch.float32, device=dev)
+    S = torch.zeros((nb, len(systems[0].Q)), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream()
+    moves = args.moves
+
+    def enqueue(k, st):
+        box.epsr_mc_sweep_async(moves, 3, k * moves, stream=st)
+        H.zero_()
+        box.epsr_partial_gr(H, g, 1, stream=st)
+        plan.epsr_sq_exec(g.view(-1, 600), ws, 3, flats, None, S, stream=st)
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            enqueue(k, stream.cuda_stream)
+    torch.cuda.synchronize()
+    graphs = []
+    for k in range(args.steps):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=stream):
+            enqueue(args.warmup + k, torch.cuda.current_stream().cuda_stream)
+        graphs.append(gr)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        for k, gr in enumerate(graphs):
+            flush.fill_(float(k))
+            evs[k][0].record()
+            gr.replay()
+            evs[k][1].record()
+        torch.cuda.synchronize()
+    status = box.epsr_mc_status()
+    t = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    n_atoms = [s.n_atoms for s in systems]
+    line = {"metric": METRIC + " (replica batch)", "value": nb * moves / (t * 1e-3),
+            "unit": "moves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32+int64", "data": "synthetic",
+            "config": {"workload": f"{nb} replica boxes (log-uniform 2k-60k atoms, half water, half "
+                                   f"silica, {sum(n_atoms)} atoms), {moves} moves per box + g(r) + "
+                                   f"S(Q) [2000 x 600] x [600 x {3 * nb}] per step, one CUDA graph per step",
+                       "l2": "flushed before every step outside the timed events"},
+            "pair_distances_per_step": sum(n * (n - 1) // 2 for n in n_atoms),
+            "status": status, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    box.close()
+    plan.close()
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
@@ -164,6 +234,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="water", choices=["water", "replicas"],
+                    help="water: the paper-scale box (default line); replicas: 64 uneven boxes")
     ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
                     help="moves per step (profiling runs only; the benchmark uses 10,000)")
     args = ap.parse_args()
@@ -171,6 +243,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "replicas":
+        return run_replicas(args)
 
     import torch
     from paper_1904_08756_gb300 import build, epsr, synth

@@ -186,6 +186,12 @@ int epsr_box_total_energy(epsr_box *box, double *U_host, epsr_stream_t stream);
  * wait exceeded its limit; coordinates are then unspecified), ECUDA.                 */
 int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
                   epsr_mc_stats *stats, epsr_move_log *log, epsr_stream_t stream);
+/* The same sweep enqueued without synchronising and without reading the status back:
+ * it allocates nothing and can be captured in a CUDA graph. Read the status of the last
+ * sweep later with epsr_mc_status (EPSR_OK or EPSR_ETIMEOUT in *status). */
+int epsr_mc_sweep_async(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
+                        epsr_move_log *log, epsr_stream_t stream);
+int epsr_mc_status(epsr_box *box, int32_t *status, epsr_stream_t stream);
 /* Reads the running statistics without running moves (synchronises). */
 int epsr_mc_stats_get(epsr_box *box, epsr_mc_stats *stats, epsr_stream_t stream);
 /* Moves per speculative batch (1 .. 16, default 16): the sweep evaluates up to this many

@@ -245,7 +245,7 @@ static void set_near(BoxDev &bx)
 static void plan_mc_groups(epsr_box *h)
 {
     // CTAs per box: a single box uses up to one CTA per SM, at least ~512 partner atoms
-    // per CTA; a batch splits the budget in proportion to the atom counts.
+    // per CTA; a batch gives each box one CTA, then the rest greedily to the largest slices.
     const int nb = h->n_boxes;
     const int budget = h->mc_ctas > 0 ? h->mc_ctas : h->sms;
     h->total_mc_cells = 0;
@@ -254,19 +254,19 @@ static void plan_mc_groups(epsr_box *h)
         long long want = (h->hb[0].n_atoms + 511) / 512;
         G[0] = (int)std::max(1LL, std::min<long long>(want, budget));
     } else {
-        long long tot = 0;
-        for (auto &b : h->hb) tot += b.n_atoms;
-        int used = 0;
-        for (int i = 0; i < nb; ++i) {
-            G[i] = std::max(1, (int)((double)budget * h->hb[i].n_atoms / (double)tot));
-            used += G[i];
-        }
-        // trim the largest groups if rounding up overshot the budget
-        while (used > std::max(budget, nb)) {
-            int imax = (int)(std::max_element(G.begin(), G.end()) - G.begin());
-            if (G[imax] <= 1) break;
-            --G[imax];
-            --used;
+        // every box starts with one CTA; each further CTA goes to the box whose per-CTA
+        // slice is largest (the slowest group of the persistent kernel)
+        int used = nb;
+        while (used < budget) {
+            int imax = 0;
+            long long worst = -1;
+            for (int i = 0; i < nb; ++i) {
+                const long long c = (h->hb[i].n_atoms + G[i] - 1) / G[i];
+                if (c > worst) { worst = c; imax = i; }
+            }
+            if (worst <= 512) break;          // small slices gain nothing from another CTA
+            ++G[imax];
+            ++used;
         }
     }
     int c0 = 0;
@@ -459,6 +459,9 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
     CKD(cudaStreamSynchronize(stream));
     plan_mc_groups(h);
     if ((rc = upload_mc_groups(h))) { delete h; return rc; }
+    // move table: up to 65,536 moves per box and launch, at most 2^22 moves in total
+    h->moves_cap = std::max<long long>(1024, std::min<long long>(65536, (1LL << 22) / n_boxes)) * n_boxes;
+    if ((rc = dalloc(&h->moves, (size_t)h->moves_cap))) { delete h; return rc; }
     *out = h;
     return EPSR_OK;
 }
@@ -647,84 +650,99 @@ extern "C" int epsr_mc_stats_get(epsr_box *box, epsr_mc_stats *stats, epsr_strea
     return EPSR_OK;
 }
 
+// Enqueues a sweep without synchronising (graph-capturable once the move table exists).
+static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
+                            epsr_move_log *log, cudaStream_t s)
+{
+    if (!box || n_moves < 0) return set_error(EPSR_EINVAL, "bad argument");
+    CK(cudaMemsetAsync(box->status, 0, sizeof(int), s));
+    if (n_moves == 0) return EPSR_OK;
+    int slice_cap = 0;
+    for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
+    size_t smem = (size_t)slice_cap * sizeof(int4) + (size_t)box->tbl_cap * sizeof(long long) +
+                  (size_t)box->ep_cap * sizeof(float);
+    smem = (smem + 15) & ~(size_t)15;
+    if (smem > kMcMaxDynSmem)
+        return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of shared memory per CTA needed (limit %zu); "
+                         "give the sweep more CTAs", smem, kMcMaxDynSmem);
+    // moves per launch: the table (allocated at creation) holds at most 2^22 moves over all boxes
+    const long long chunk = std::min<long long>(n_moves, box->moves_cap / box->n_boxes);
+    // type-major spatial partition of the partners for this sweep
+    int rc0 = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
+    if (!rc0)
+        rc0 = launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
+                                  box->total_mc_cells + 1, 1, box->mc_sort, nullptr, nullptr,
+                                  box->pos_of, s);
+    if (rc0) return rc0;
+    McArgs a;
+    memset(&a, 0, sizeof(a));
+    a.sorted_index = box->mc_sort.index;
+    a.pos_of = box->pos_of;
+    a.mc_offset = box->mc_sort.offset;
+    a.boxes = box->boxes;
+    a.coords = box->coords;
+    a.mol_start = box->mol_start;
+    a.thresholds = box->thresholds;
+    a.ep = box->ep;
+    a.cta_box = box->cta_box;
+    a.slots = box->slots;
+    a.flags = box->flags;
+    a.stats = box->stats;
+    a.log = log;
+    a.status = box->status;
+    a.seed = seed;
+    a.log_stride = n_moves;
+    a.max_spin = 1LL << 40;
+    a.timeout_ns = (unsigned long long)(box->timeout_ms * 1e6);
+    a.grid = box->cta_box_len;
+    a.batch_k = box->mc_batch;
+    a.slice_cap = slice_cap;
+    a.tbl_cap = box->tbl_cap;
+    a.skip_arrival_cta = box->fault_cta;
+    a.moves = box->moves;
+    a.chunk = chunk;
+    for (long long c0 = 0; c0 < n_moves; c0 += chunk) {
+        const long long n = std::min(chunk, n_moves - c0);
+        int rc = launch_mc_moves(box->boxes, box->mol_start, box->n_boxes, chunk, n, seed,
+                                 move0 + (uint64_t)c0, box->moves, s);
+        if (rc) return rc;
+        a.n_moves = n;
+        a.move0 = move0 + (uint64_t)c0;
+        a.log_off = c0;
+        CK(cudaMemsetAsync(box->flags, 0, box->cta_box_len * sizeof(unsigned), s));
+        rc = launch_mc_sweep(a, box->cta_box_len, smem, s);
+        if (rc) return rc;
+    }
+    return EPSR_OK;
+}
+
 extern "C" int epsr_mc_sweep(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
                              epsr_mc_stats *stats, epsr_move_log *log, epsr_stream_t stream)
 {
-    if (!box || n_moves < 0) return set_error(EPSR_EINVAL, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemsetAsync(box->status, 0, sizeof(int), s));
-    if (n_moves > 0) {
-        int slice_cap = 0;
-        for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
-        size_t smem = (size_t)slice_cap * sizeof(int4) + (size_t)box->tbl_cap * sizeof(long long) +
-                      (size_t)box->ep_cap * sizeof(float);
-        smem = (smem + 15) & ~(size_t)15;
-        if (smem > kMcMaxDynSmem)
-            return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of shared memory per CTA needed (limit %zu); "
-                             "give the sweep more CTAs", smem, kMcMaxDynSmem);
-        // moves per launch: the table holds at most 2^22 moves over all boxes
-        const long long chunk = std::min<long long>(
-            n_moves, std::max<long long>(1024, std::min<long long>(65536, (1LL << 22) / box->n_boxes)));
-        if (box->moves_cap < chunk * box->n_boxes) {
-            if (box->moves) cudaFree(box->moves);
-            box->moves = nullptr;
-            box->moves_cap = 0;
-            int rc = dalloc(&box->moves, (size_t)(chunk * box->n_boxes));
-            if (rc) return rc;
-            box->moves_cap = chunk * box->n_boxes;
-        }
-        // type-major spatial partition of the partners for this sweep
-        int rc0 = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
-        if (!rc0)
-            rc0 = launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
-                                      box->total_mc_cells + 1, 1, box->mc_sort, nullptr, nullptr,
-                                      box->pos_of, s);
-        if (rc0) return rc0;
-        McArgs a;
-        memset(&a, 0, sizeof(a));
-        a.sorted_index = box->mc_sort.index;
-        a.pos_of = box->pos_of;
-        a.mc_offset = box->mc_sort.offset;
-        a.boxes = box->boxes;
-        a.coords = box->coords;
-        a.mol_start = box->mol_start;
-        a.thresholds = box->thresholds;
-        a.ep = box->ep;
-        a.cta_box = box->cta_box;
-        a.slots = box->slots;
-        a.flags = box->flags;
-        a.stats = box->stats;
-        a.log = log;
-        a.status = box->status;
-        a.seed = seed;
-        a.log_stride = n_moves;
-        a.max_spin = 1LL << 40;
-        a.timeout_ns = (unsigned long long)(box->timeout_ms * 1e6);
-        a.grid = box->cta_box_len;
-        a.batch_k = box->mc_batch;
-        a.slice_cap = slice_cap;
-        a.tbl_cap = box->tbl_cap;
-        a.skip_arrival_cta = box->fault_cta;
-        a.moves = box->moves;
-        a.chunk = chunk;
-        for (long long c0 = 0; c0 < n_moves; c0 += chunk) {
-            const long long n = std::min(chunk, n_moves - c0);
-            int rc = launch_mc_moves(box->boxes, box->mol_start, box->n_boxes, chunk, n, seed,
-                                     move0 + (uint64_t)c0, box->moves, s);
-            if (rc) return rc;
-            a.n_moves = n;
-            a.move0 = move0 + (uint64_t)c0;
-            a.log_off = c0;
-            CK(cudaMemsetAsync(box->flags, 0, box->cta_box_len * sizeof(unsigned), s));
-            rc = launch_mc_sweep(a, box->cta_box_len, smem, s);
-            if (rc) return rc;
-        }
-    }
+    int rc = mc_sweep_enqueue(box, n_moves, seed, move0, log, s);
+    if (rc) return rc;
     int st = 0;
     CK(cudaMemcpyAsync(&st, box->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (stats) CK(cudaMemcpyAsync(stats, box->stats, box->n_boxes * sizeof(epsr_mc_stats), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (st & kStatusTimeout) return set_error(EPSR_ETIMEOUT, "mc sweep: a grid barrier wait exceeded %.0f ms", box->timeout_ms);
+    return EPSR_OK;
+}
+
+extern "C" int epsr_mc_sweep_async(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
+                                   epsr_move_log *log, epsr_stream_t stream)
+{
+    return mc_sweep_enqueue(box, n_moves, seed, move0, log, (cudaStream_t)stream);
+}
+
+extern "C" int epsr_mc_status(epsr_box *box, int32_t *status, epsr_stream_t stream)
+{
+    if (!box || !status) return set_error(EPSR_EINVAL, "NULL argument");
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, box->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    *status = (st & kStatusTimeout) ? EPSR_ETIMEOUT : EPSR_OK;
     return EPSR_OK;
 }
 

@@ -28,6 +28,7 @@ EXPORTS = [
     "epsr_box_offsets", "epsr_box_get_coords", "epsr_box_set_coords",
     "epsr_box_set_coords_device", "epsr_box_get_coords_device", "epsr_box_set_ep",
     "epsr_box_get_ep", "epsr_box_total_energy", "epsr_mc_sweep", "epsr_mc_stats_get",
+    "epsr_mc_sweep_async", "epsr_mc_status",
     "epsr_mc_set_batch", "epsr_mc_set_ctas", "epsr_debug_barrier_fault",
     "epsr_partial_gr", "epsr_partial_gr_tiles", "epsr_partial_gr_range", "epsr_normalize_g",
     "epsr_sq_weights", "epsr_sq_plan_create", "epsr_sq_plan_destroy", "epsr_sq_exec", "epsr_sq",
@@ -92,6 +93,8 @@ def lib():
             "epsr_box_total_energy": ([vp, vp, vp], C.c_int),
             "epsr_mc_sweep": ([vp, i64, u64, u64, vp, vp, vp], C.c_int),
             "epsr_mc_stats_get": ([vp, vp, vp], C.c_int),
+            "epsr_mc_sweep_async": ([vp, i64, u64, u64, vp, vp], C.c_int),
+            "epsr_mc_status": ([vp, P(i32), vp], C.c_int),
             "epsr_mc_set_batch": ([vp, i32], C.c_int),
             "epsr_mc_set_ctas": ([vp, i32], C.c_int),
             "epsr_debug_barrier_fault": ([vp, i32, dbl], C.c_int),
@@ -253,6 +256,15 @@ class Box:
         _check(lib().epsr_mc_sweep(self.h, n_moves, seed, move0, stats, _dev_ptr(log),
                                    _stream(stream)), "epsr_mc_sweep")
         return [(s.attempted, s.accepted, s.nonfinite, s.sum_dU) for s in stats]
+
+    def epsr_mc_sweep_async(self, n_moves: int, seed: int, move0: int = 0, log=None, stream=None):
+        _check(lib().epsr_mc_sweep_async(self.h, n_moves, seed, move0, _dev_ptr(log),
+                                         _stream(stream)), "epsr_mc_sweep_async")
+
+    def epsr_mc_status(self, stream=None) -> int:
+        st = C.c_int32()
+        _check(lib().epsr_mc_status(self.h, C.byref(st), _stream(stream)), "epsr_mc_status")
+        return st.value
 
     def epsr_mc_stats_get(self, stream=None):
         stats = (McStats * self.n_boxes)()

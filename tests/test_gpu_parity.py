@@ -269,3 +269,61 @@ def test_sq_flat_background_gpu():
     epsr.epsr_sq(g, 0.02, Q, np.ones(6), 3, np.array([0.25, 0.5]), None, S_t)
     torch.cuda.synchronize()
     assert torch.all(S_t[0] == 0.25) and torch.all(S_t[1] == 0.5)
+
+
+# --------------------------------------------------------------------------------------
+# batched replicas under a captured CUDA graph
+# --------------------------------------------------------------------------------------
+
+def _replica_systems():
+    Q = 0.3 + np.arange(2000) * (39.7 / 1999)
+    return [synth.water_box(700, seed=81, n_bins=600, bin_p=2, bin_q=100, Q=Q),
+            synth.silica_box(500, seed=82, n_bins=600, bin_p=2, bin_q=100, Q=Q),
+            synth.water_box(1500, seed=83, n_bins=600, bin_p=2, bin_q=100, Q=Q),
+            synth.silica_box(900, seed=84, n_bins=600, bin_p=2, bin_q=100, Q=Q)]
+
+
+def _replica_step(box, plan, H, g, S, w, flat, n_moves, seed, move0, stream):
+    box.epsr_mc_sweep_async(n_moves, seed, move0, stream=stream)
+    box.epsr_partial_gr(H, g, 1, stream=stream)
+    plan.epsr_sq_exec(g.view(-1, 600), w, 3, flat, None, S, stream=stream)
+
+
+def test_replicas_step_captured_in_cuda_graph():
+    systems = _replica_systems()
+    nb = len(systems)
+    boxes = [epsr.Box(systems), epsr.Box(systems)]
+    ws = np.concatenate([boxes[0].epsr_sq_weights(b)[0] for b in range(nb)])
+    flats = np.array([boxes[0].epsr_sq_weights(b)[1] for b in range(nb)])
+    plan = epsr.SqPlan(systems[0].Q, 600, 0.02, epsr.SQ_FP32, max_cols=3 * nb)
+    bufs = []
+    for bx in boxes:
+        bufs.append((torch.zeros(bx.hist_len, dtype=torch.int64, device=DEV),
+                     torch.zeros(bx.hist_len, dtype=torch.float32, device=DEV),
+                     torch.zeros((nb, 2000), dtype=torch.float32, device=DEV)))
+    # eager reference: two steps
+    s0 = torch.cuda.Stream()
+    with torch.cuda.stream(s0):
+        for k in range(2):
+            bufs[0][0].zero_()
+            _replica_step(boxes[0], plan, *bufs[0], ws, flats, 400, 11, 400 * k, s0.cuda_stream)
+    s0.synchronize()
+    # captured: one graph per step (the move indices are baked into the graph)
+    s1 = torch.cuda.Stream()
+    graphs = []
+    for k in range(2):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s1):
+            bufs[1][0].zero_()
+            _replica_step(boxes[1], plan, *bufs[1], ws, flats, 400, 11, 400 * k,
+                          torch.cuda.current_stream().cuda_stream)
+        graphs.append(g)
+    # capture ran nothing; start from the same coordinates and replay
+    boxes[1].epsr_box_set_coords(np.concatenate([s.xyz for s in systems]))
+    for g in graphs:
+        g.replay()
+    torch.cuda.synchronize()
+    assert boxes[1].epsr_mc_status() == epsr.EPSR_OK
+    assert np.array_equal(boxes[0].epsr_box_get_coords(), boxes[1].epsr_box_get_coords())
+    for a, b in zip(bufs[0], bufs[1]):
+        assert torch.equal(a, b)
