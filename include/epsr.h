@@ -235,6 +235,25 @@ int epsr_normalize_g(epsr_box *box, const uint64_t *hist, float *g, int64_t n_co
  * pair (b in 1e-12 cm so S is in barn) and flat = sum_a c_a b_a^2. Host only. */
 int epsr_sq_weights(const epsr_box *box, int32_t b, double *w, double *flat);
 
+/* ---- empirical-potential update (Sec. 2.1: the EMP is a Poisson series fitted in Q space
+ * to Delta S(Q); Eq. (2): pair terms through the inverse of the weight matrix) ----------------
+ * For box b with P = n_types (n_types + 1)/2 pairs:
+ *   1. pair-resolve: Delta S_p = sum_d M[p][d] dS[d], M = pinv([w; gamma I]) restricted to the
+ *      data rows (w [n_data][P] host: the Eq. (1) weights (2 - delta) c_a c_b b_a b_b of each
+ *      dataset, barn; gamma = 0 with n_data == P inverts w; fewer datasets need gamma > 0);
+ *   2. fit: C_p = argmin || Delta S_p - F C_p || by Householder QR in FP64, where
+ *      F[Q][n] = 4 pi rho int r^2 p_n(r) sin(Qr)/(Qr) dr in closed form, p_n(r) =
+ *      (r/(n s))^n exp(n - r/s) (peak 1 at r = n s), n = 1..n_basis;
+ *   3. table: U_EP[p][k] += -alpha kT sum_n C[p][n] p_n((k + 1/2) dr).
+ *   dS      device float [n_data][nQ];  Q host float [nQ] (> 0)
+ *   C_out   host double [P][n_basis] or NULL
+ * Limits: n_data <= 16, n_basis <= 40, nQ >= n_basis. Synchronises. The basis is nearly
+ * collinear (condition ~1e10 for 20 functions): C carries that conditioning, the fitted
+ * Delta S and the table do not. */
+int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t n_data, const double *w,
+                   const float *Q, int32_t nQ, int32_t n_basis, double s_basis, double gamma,
+                   double alpha, double *C_out, epsr_stream_t stream);
+
 /* ---- pair histogram without device allocation -----------------------------------------
  * The paper has no counterpart: this entry point exists for callers that must not
  * allocate device memory when they need the counts -- code running while a CUDA graph

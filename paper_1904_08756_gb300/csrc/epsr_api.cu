@@ -136,6 +136,10 @@ struct epsr_box {
     int total_mc_cells = 0;
     SortScratch mc_sort{};
     int *pos_of = nullptr;
+    // empirical-potential update scratch (allocated on first use)
+    double *ep_F = nullptr, *ep_Y = nullptr, *ep_C = nullptr;
+    float *ep_Q = nullptr;
+    long long ep_cap_Q = 0;
 
     ~epsr_box()
     {
@@ -143,7 +147,8 @@ struct epsr_box {
                         tiles, hist_box, cta_box, slots, flags, stats, status, U,
                         sort.count, sort.offset, sort.block, sort.key, sort.rank, sort.index,
                         sorted_scaled, sorted_coords, moves, mc_sort.count, mc_sort.offset,
-                        mc_sort.block, mc_sort.key, mc_sort.rank, mc_sort.index, pos_of};
+                        mc_sort.block, mc_sort.key, mc_sort.rank, mc_sort.index, pos_of,
+                        ep_F, ep_Y, ep_C, ep_Q};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -924,4 +929,67 @@ extern "C" int epsr_sq(const float *g, int32_t n_cols, int32_t n_bins, double dr
     }
     epsr_sq_plan_destroy(p);
     return rc;
+}
+
+// ---- empirical-potential update -------------------------------------------------------------
+extern "C" int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t n_data,
+                              const double *w, const float *Q, int32_t nQ, int32_t n_basis,
+                              double s_basis, double gamma, double alpha, double *C_out,
+                              epsr_stream_t stream)
+{
+    if (!box || b < 0 || b >= box->n_boxes || !dS || !w || !Q)
+        return set_error(EPSR_EINVAL, "ep update: bad argument");
+    BoxDev &bx = box->hb[b];
+    const int P = bx.n_pairs;
+    if (n_data < 1 || n_data > kEpMaxData || n_basis < 1 || n_basis > kEpMaxBasis || nQ < n_basis ||
+        nQ > (1 << 20) || !(s_basis > 0) || !(gamma >= 0) || !std::isfinite(alpha))
+        return set_error(EPSR_EINVAL, "ep update: sizes or parameters out of range");
+    if (n_data < P && !(gamma > 0))
+        return set_error(EPSR_EINVAL, "ep update: %d datasets for %d pairs need gamma > 0", n_data, P);
+    for (int i = 0; i < nQ; ++i)
+        if (!(Q[i] > 0) || !std::isfinite(Q[i])) return set_error(EPSR_EINVAL, "ep update: Q[%d] must be > 0", i);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (box->ep_cap_Q < nQ) {
+        void *ptrs[] = {box->ep_F, box->ep_Y, box->ep_C, box->ep_Q};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        box->ep_F = box->ep_Y = box->ep_C = nullptr;
+        box->ep_Q = nullptr;
+        box->ep_cap_Q = 0;
+        int rc;
+        if ((rc = dalloc(&box->ep_F, (size_t)kEpMaxBasis * nQ)) || (rc = dalloc(&box->ep_Y, (size_t)kEpMaxPairs * nQ)) ||
+            (rc = dalloc(&box->ep_C, (size_t)kEpMaxPairs * kEpMaxBasis)) || (rc = dalloc(&box->ep_Q, (size_t)nQ)))
+            return rc;
+        box->ep_cap_Q = nQ;
+    }
+    EpArgs *a = new (std::nothrow) EpArgs();
+    if (!a) return set_error(EPSR_ENOMEM, "host allocation failed");
+    a->dS = dS;
+    a->Q = box->ep_Q;
+    a->nQ = nQ;
+    a->n_data = n_data;
+    a->n_pairs = P;
+    a->n_basis = n_basis;
+    a->n_bins = bx.n_bins;
+    for (int i = 0; i < n_data * P; ++i) a->w[i] = w[i];
+    a->s = s_basis;
+    a->gamma = gamma;
+    a->alpha = alpha;
+    a->kT = bx.kT;
+    a->rho = (double)bx.n_atoms / bx.volume;
+    a->dr = bx.dr_A;
+    a->F = box->ep_F;
+    a->Y = box->ep_Y;
+    a->C_out = box->ep_C;
+    a->ep = box->ep + bx.ep_off;
+    cudaError_t e = cudaMemcpyAsync(box->ep_Q, Q, nQ * sizeof(float), cudaMemcpyHostToDevice, s);
+    int rc = e == cudaSuccess ? launch_ep_update(*a, s) : set_cuda_error(e, "ep update: Q upload");
+    delete a;
+    if (rc) return rc;
+    bx.has_ep = 1;
+    set_near(bx);
+    CK(cudaMemcpyAsync(box->boxes + b, &bx, sizeof(BoxDev), cudaMemcpyHostToDevice, s));
+    if (C_out) CK(cudaMemcpyAsync(C_out, box->ep_C, (size_t)P * n_basis * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return EPSR_OK;
 }

@@ -100,6 +100,24 @@ int launch_total_energy(const BoxDev *boxes, const int4 *coords, const int *atom
                         const long long *thresholds, const float *ep, const GrTile *tiles,
                         long long n_tiles, double *U, int grid, cudaStream_t stream);
 
+// ---- empirical-potential update -------------------------------------------------------------
+constexpr int kEpMaxData = 16;     // measured datasets
+constexpr int kEpMaxBasis = 40;    // Poisson functions per pair
+constexpr int kEpMaxPairs = EPSR_MAX_TYPES * (EPSR_MAX_TYPES + 1) / 2;
+
+struct EpArgs {
+    const float *dS;     // [n_data][nQ] device
+    const float *Q;      // [nQ] device
+    int nQ, n_data, n_pairs, n_basis, n_bins;
+    double w[kEpMaxData * kEpMaxPairs];   // [n_data][n_pairs] Eq. (1) weights (barn)
+    double s, gamma, alpha, kT, rho, dr;
+    double *F;           // [n_basis][nQ] scratch
+    double *Y;           // [n_pairs][nQ] scratch
+    double *C_out;       // [n_pairs][n_basis] device
+    float *ep;           // [n_pairs][n_bins] the box's table, updated in place
+};
+int launch_ep_update(const EpArgs &a, cudaStream_t stream);
+
 // ---- S(Q) --------------------------------------------------------------------------------
 int sq_build_kernel_matrix(const float *Q, int nQ, int n_bins, double dr, int mode, float *K32,
                            void *Ksplit, int ld_split, cudaStream_t stream);

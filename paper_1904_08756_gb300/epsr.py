@@ -32,7 +32,7 @@ EXPORTS = [
     "epsr_mc_set_batch", "epsr_mc_set_ctas", "epsr_debug_barrier_fault",
     "epsr_partial_gr", "epsr_partial_gr_tiles", "epsr_partial_gr_range", "epsr_normalize_g",
     "epsr_sq_weights", "epsr_sq_plan_create", "epsr_sq_plan_destroy", "epsr_sq_exec", "epsr_sq",
-    "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc",
+    "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc", "epsr_ep_update",
 ]
 
 
@@ -108,6 +108,7 @@ def lib():
             "epsr_sq_exec": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], C.c_int),
             "epsr_sq": ([vp, i32, i32, dbl, vp, i32, vp, i32, vp, vp, vp, i32, vp], C.c_int),
             "epsr_noalloc_scratch_bytes": ([], C.c_size_t),
+            "epsr_ep_update": ([vp, i32, vp, i32, vp, vp, i32, i32, dbl, dbl, dbl, vp, vp], C.c_int),
             "epsr_partial_gr_noalloc": ([vp, vp, i64, i64, i32, i32, i32, i32, i32, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -297,6 +298,19 @@ class Box:
     def epsr_normalize_g(self, hist, g, n_configs: int = 1, stream=None):
         _check(lib().epsr_normalize_g(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
                                       _stream(stream)), "epsr_normalize_g")
+
+    def epsr_ep_update(self, b: int, dS, w: np.ndarray, Q: np.ndarray, n_basis: int = 20,
+                       s_basis: float = 0.5, gamma: float = 0.0, alpha: float = 1.0, stream=None):
+        """Fit the Poisson basis to the pair-resolved Delta S and add it to box b's table;
+        returns the coefficients C [P][n_basis]."""
+        w = np.ascontiguousarray(w, np.float64)
+        q = np.ascontiguousarray(Q, np.float32)
+        P = self.systems[b].n_types * (self.systems[b].n_types + 1) // 2
+        C_ = np.zeros((P, n_basis), np.float64)
+        _check(lib().epsr_ep_update(self.h, b, _dev_ptr(dS), dS.shape[0], _np_ptr(w), _np_ptr(q),
+                                    len(q), n_basis, s_basis, gamma, alpha, _np_ptr(C_),
+                                    _stream(stream)), "epsr_ep_update")
+        return C_
 
     def epsr_sq_weights(self, b: int):
         P = self.systems[b].n_types * (self.systems[b].n_types + 1) // 2

@@ -327,3 +327,37 @@ def test_replicas_step_captured_in_cuda_graph():
     assert np.array_equal(boxes[0].epsr_box_get_coords(), boxes[1].epsr_box_get_coords())
     for a, b in zip(bufs[0], bufs[1]):
         assert torch.equal(a, b)
+
+
+# --------------------------------------------------------------------------------------
+# empirical-potential update
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_data,gamma", [(3, 0.0), (1, 1.0)])
+def test_ep_update_against_oracle(small_water, n_data, gamma):
+    s = small_water
+    box = epsr.Box(s)
+    rng = np.random.default_rng(12)
+    Q = s.Q
+    rho = s.n_atoms / s.L ** 3
+    F = oracle.ep_basis_matrix(20, 0.5, Q, rho)
+    C_true = rng.normal(size=(3, 20)) * 0.01
+    w = rng.uniform(0.05, 0.3, (n_data, 3))
+    dS32 = (w @ (C_true @ F.T)).astype(np.float32)
+    dS = torch.from_numpy(dS32).to(DEV)
+    C_gpu = box.epsr_ep_update(0, dS, w, Q, n_basis=20, s_basis=0.5, gamma=gamma, alpha=1.0)
+    table = box.epsr_box_get_ep(0, (3, s.n_bins)).astype(np.float64)
+    Qf = Q.astype(np.float32).astype(np.float64)
+    Ff = oracle.ep_basis_matrix(20, 0.5, Qf, rho)
+    dSp = oracle.pair_resolve(dS32.astype(np.float64), w, gamma)
+    C_ref = oracle.ep_fit(dSp, Ff)
+    kT = oracle.gas_constant() * s.temperature
+    ref = oracle.ep_table(C_ref, 0.5, s.n_bins, s.dr, 1.0, kT)
+    # the fitted Delta S is well determined; the coefficients carry the basis's conditioning
+    assert np.abs(C_gpu @ Ff.T - C_ref @ Ff.T).max() <= 1e-8 * np.abs(dSp).max()
+    assert np.abs(C_gpu - C_ref).max() <= 1e-3 * np.abs(C_ref).max()
+    assert np.abs(table - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-6
+    # the update is additive: a second call adds the same increment
+    box.epsr_ep_update(0, dS, w, Q, n_basis=20, s_basis=0.5, gamma=gamma, alpha=1.0)
+    t2 = box.epsr_box_get_ep(0, (3, s.n_bins)).astype(np.float64)
+    assert np.abs(t2 - 2 * ref).max() <= 2e-4 * np.abs(ref).max() + 1e-6
