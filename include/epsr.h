@@ -89,6 +89,7 @@ typedef struct {
 } epsr_box_desc;
 
 typedef struct epsr_box epsr_box;   /* opaque: one box or a batch of boxes */
+typedef struct epsr_sq_plan epsr_sq_plan;   /* opaque: cached sine-transform matrix */
 
 /* Running Monte Carlo statistics of one box, accumulated over every sweep since the
  * box was created. */
@@ -235,6 +236,30 @@ int epsr_normalize_g(epsr_box *box, const uint64_t *hist, float *g, int64_t n_co
  * pair (b in 1e-12 cm so S is in barn) and flat = sum_a c_a b_a^2. Host only. */
 int epsr_sq_weights(const epsr_box *box, int32_t b, double *w, double *flat);
 
+/* ---- differentiable form: Gaussian-smeared histogram, its adjoint, chi^2 ------------------
+ * A smooth stand-in for the counts N(r) of Sec. 2.3: every unordered pair at distance r
+ * adds to bin k the mass of a Gaussian of width sigma centred on r, truncated at +-5 sigma,
+ *   w_k(r) = Phi(clip((r_{k+1} - r)/sigma)) - Phi(clip((r_k - r)/sigma)),  clip to [-5, 5].
+ * epsr_gr_smeared_fwd: Ht device double [hist_len] (overwritten); gt device float [hist_len]
+ *   or NULL: the smeared g~ = Ht V / (P_ab shell_k), normalised like epsr_partial_gr's g.
+ * epsr_gr_smeared_bwd: given dL/dg~ (device float [hist_len]) writes dL/dx, device float
+ *   [n_atoms_total][3] per Angstrom (overwritten). Pair distances are recomputed.
+ * epsr_sq_exec_adjoint: dg[c][k] = w_c sum_i K[i][k] dS_total[set(c)][i], the adjoint of
+ *   epsr_sq_exec with respect to g (dS_total device [n_sets][nQ], dg device [n_cols][n_bins]).
+ * epsr_chi2: chi2 = sum_Q [S(Q) + sum_p W[p] sum_n C[p][n] F_n(Q) - target(Q)]^2 on the plan's
+ *   Q grid, F_n the closed-form transform of the Poisson function p_n (4 pi rho included);
+ *   writes chi2 (device double [1]), dS = dchi2/dS (device float [nQ]) and, if C is given,
+ *   dC = dchi2/dC (device double [P][n_basis]). W host double [P] (barn); C device or NULL.
+ * All asynchronous on `stream`. */
+int epsr_gr_smeared_fwd(epsr_box *box, double sigma, double *Ht, float *gt, epsr_stream_t stream);
+int epsr_gr_smeared_bwd(epsr_box *box, double sigma, const float *dgt, float *grad,
+                        epsr_stream_t stream);
+int epsr_sq_exec_adjoint(epsr_sq_plan *plan, const float *dS_total, int32_t n_cols, const double *w,
+                         int32_t cols_per_set, float *dg, epsr_stream_t stream);
+int epsr_chi2(epsr_sq_plan *plan, const float *S, const float *target, const double *W, int32_t P,
+              const double *C, int32_t n_basis, double s_basis, double rho, double *chi2, float *dS,
+              double *dC, epsr_stream_t stream);
+
 /* ---- empirical-potential update (Sec. 2.1: the EMP is a Poisson series fitted in Q space
  * to Delta S(Q); Eq. (2): pair terms through the inverse of the weight matrix) ----------------
  * For box b with P = n_types (n_types + 1)/2 pairs:
@@ -293,7 +318,6 @@ int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, int64_t n_a
  *   S_partial  device float [n_cols][nQ] or NULL;  S_total device float [n_sets][nQ] or NULL
  * epsr_sq_plan_create synchronises; epsr_sq_exec is asynchronous and allocates nothing
  * (graph-capturable). epsr_sq is a one-shot convenience (plan, exec, free).            */
-typedef struct epsr_sq_plan epsr_sq_plan;
 int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, double dr, int32_t mode,
                         int32_t max_cols, epsr_stream_t stream, epsr_sq_plan **out);
 int epsr_sq_plan_destroy(epsr_sq_plan *plan);

@@ -140,6 +140,8 @@ struct epsr_box {
     double *ep_F = nullptr, *ep_Y = nullptr, *ep_C = nullptr;
     float *ep_Q = nullptr;
     long long ep_cap_Q = 0;
+    float *lambda = nullptr;     // adjoint of the smeared normalisation [hist_len]
+    unsigned long long *smear_acc = nullptr;   // fixed-point smeared counts [hist_len]
 
     ~epsr_box()
     {
@@ -148,7 +150,7 @@ struct epsr_box {
                         sort.count, sort.offset, sort.block, sort.key, sort.rank, sort.index,
                         sorted_scaled, sorted_coords, moves, mc_sort.count, mc_sort.offset,
                         mc_sort.block, mc_sort.key, mc_sort.rank, mc_sort.index, pos_of,
-                        ep_F, ep_Y, ep_C, ep_Q};
+                        ep_F, ep_Y, ep_C, ep_Q, lambda, smear_acc};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -442,7 +444,8 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         (rc = dalloc(&h->sort.index, atom0)) ||
         (rc = dalloc(&h->sorted_scaled, atom0)) || (rc = dalloc(&h->sorted_coords, atom0)) ||
         (rc = dalloc(&h->mc_sort.key, atom0)) || (rc = dalloc(&h->mc_sort.rank, atom0)) ||
-        (rc = dalloc(&h->mc_sort.index, atom0)) || (rc = dalloc(&h->pos_of, atom0))) {
+        (rc = dalloc(&h->mc_sort.index, atom0)) || (rc = dalloc(&h->pos_of, atom0)) ||
+        (rc = dalloc(&h->lambda, (size_t)hist0)) || (rc = dalloc(&h->smear_acc, (size_t)hist0))) {
         delete h;
         return rc;
     }
@@ -838,11 +841,13 @@ struct epsr_sq_plan {
     float *Q = nullptr;
     float *Kt = nullptr;
     float *Sp_scratch = nullptr;
+    double *res = nullptr;      // chi^2 residuals [nQ]
     ~epsr_sq_plan()
     {
         if (Q) cudaFree(Q);
         if (Kt) cudaFree(Kt);
         if (Sp_scratch) cudaFree(Sp_scratch);
+        if (res) cudaFree(res);
     }
 };
 
@@ -862,7 +867,7 @@ extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, d
     p->nQ = nQ; p->n_bins = n_bins; p->mode = mode; p->max_cols = max_cols; p->dr = dr;
     int rc;
     if ((rc = dalloc(&p->Q, nQ)) || (rc = dalloc(&p->Kt, (size_t)nQ * n_bins)) ||
-        (rc = dalloc(&p->Sp_scratch, (size_t)max_cols * nQ))) {
+        (rc = dalloc(&p->Sp_scratch, (size_t)max_cols * nQ)) || (rc = dalloc(&p->res, (size_t)nQ))) {
         delete p;
         return rc;
     }
@@ -992,4 +997,98 @@ extern "C" int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t
     if (C_out) CK(cudaMemcpyAsync(C_out, box->ep_C, (size_t)P * n_basis * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return EPSR_OK;
+}
+
+// ---- differentiable form: smeared histogram, adjoints, chi^2 ----------------------------------
+static int smear_common(epsr_box *box, double sigma, cudaStream_t s)
+{
+    if (!(sigma > 0) || sigma > 2.0) return set_error(EPSR_EINVAL, "smeared g: sigma must be in (0, 2] A");
+    int rc = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
+    if (rc) return rc;
+    return launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
+                               box->total_cells, 0, box->sort, box->sorted_scaled, box->sorted_coords,
+                               nullptr, s);
+}
+
+static SmearArgs smear_args(epsr_box *box, double sigma)
+{
+    SmearArgs a;
+    memset(&a, 0, sizeof(a));
+    a.boxes = box->boxes;
+    a.coords = box->sorted_coords;
+    a.scaled = box->sorted_scaled;
+    a.index = box->sort.index;
+    a.tiles = box->tiles;
+    a.n_tiles = (long long)box->tiles_h.size();
+    a.sigma = sigma;
+    a.max_pairs_bins = box->ep_cap;
+    return a;
+}
+
+extern "C" int epsr_gr_smeared_fwd(epsr_box *box, double sigma, double *Ht, float *gt, epsr_stream_t stream)
+{
+    if (!box || !Ht) return set_error(EPSR_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = smear_common(box, sigma, s);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(box->smear_acc, 0, (size_t)box->hist_len * sizeof(unsigned long long), s));
+    SmearArgs a = smear_args(box, sigma);
+    a.acc = box->smear_acc;
+    rc = launch_smear(a, false, box->sms * 2, s);
+    if (rc) return rc;
+    return launch_smear_norm(box->boxes, box->n_boxes, box->smear_acc, Ht, gt, box->hist_len,
+                             box->hist_box, s);
+}
+
+extern "C" int epsr_gr_smeared_bwd(epsr_box *box, double sigma, const float *dgt, float *grad,
+                                   epsr_stream_t stream)
+{
+    if (!box || !dgt || !grad) return set_error(EPSR_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = smear_common(box, sigma, s);
+    if (rc) return rc;
+    rc = launch_smear_lambda(box->boxes, box->n_boxes, dgt, box->lambda, box->hist_len, box->hist_box, s);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(grad, 0, (size_t)box->n_atoms * 3 * sizeof(float), s));
+    SmearArgs a = smear_args(box, sigma);
+    a.lambda = box->lambda;
+    a.grad = grad;
+    return launch_smear(a, true, box->sms * 2, s);
+}
+
+extern "C" int epsr_sq_exec_adjoint(epsr_sq_plan *plan, const float *dS_total, int32_t n_cols,
+                                    const double *w, int32_t cols_per_set, float *dg, epsr_stream_t stream)
+{
+    if (!plan || !dS_total || !w || !dg || n_cols < 1 || n_cols > plan->max_cols || cols_per_set < 1 ||
+        n_cols % cols_per_set != 0)
+        return set_error(EPSR_EINVAL, "sq adjoint: bad argument");
+    SqArgs *a = new (std::nothrow) SqArgs();
+    if (!a) return set_error(EPSR_ENOMEM, "host allocation failed");
+    a->Kt = plan->Kt;
+    a->nQ = plan->nQ;
+    a->n_bins = plan->n_bins;
+    a->n_cols = n_cols;
+    for (int c = 0; c < n_cols; ++c) a->w[c] = w[c];
+    int rc = sq_exec_adjoint(*a, dS_total, cols_per_set, dg, (cudaStream_t)stream);
+    delete a;
+    return rc;
+}
+
+extern "C" int epsr_chi2(epsr_sq_plan *plan, const float *S, const float *target, const double *W,
+                         int32_t P, const double *C, int32_t n_basis, double s_basis, double rho,
+                         double *chi2, float *dS, double *dC, epsr_stream_t stream)
+{
+    if (!plan || !S || !target || !W || !chi2 || !dS || P < 1 || P > kEpMaxPairs ||
+        (C && (n_basis < 1 || n_basis > kEpMaxBasis || !(s_basis > 0) || !(rho > 0))))
+        return set_error(EPSR_EINVAL, "chi2: bad argument");
+    ChiParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.P = P;
+    prm.n_basis = C ? n_basis : 0;
+    prm.s = s_basis;
+    prm.rho = rho;
+    for (int p = 0; p < P; ++p) prm.W[p] = W[p];
+    prm.res_scratch = plan->res;
+    return launch_chi2(S, target, plan->Q, plan->nQ, prm, C, chi2, dS, C ? dC : nullptr,
+                       (cudaStream_t)stream);
 }

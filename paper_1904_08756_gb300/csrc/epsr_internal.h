@@ -100,6 +100,26 @@ int launch_total_energy(const BoxDev *boxes, const int4 *coords, const int *atom
                         const long long *thresholds, const float *ep, const GrTile *tiles,
                         long long n_tiles, double *U, int grid, cudaStream_t stream);
 
+// ---- smeared histogram and adjoint -----------------------------------------------------------
+struct SmearArgs {
+    const BoxDev *boxes;
+    const int4 *coords;        // spatially sorted
+    const uint4 *scaled;       // spatially sorted, 2^32-periodic copy
+    const int *index;          // atom at each sorted position
+    const GrTile *tiles;
+    long long n_tiles;
+    double sigma;
+    unsigned long long *acc;   // forward output: weights * 2^32, accumulated
+    const float *lambda;       // backward input: dL/dHt [hist_len]
+    float *grad;               // backward output [n_atoms_total][3] (accumulated)
+    int max_pairs_bins;
+};
+int launch_smear(const SmearArgs &a, bool backward, int grid, cudaStream_t stream);
+int launch_smear_norm(const BoxDev *boxes, int n_boxes, const unsigned long long *acc, double *Ht,
+                      float *gt, long long hist_len, const long long *hist_box, cudaStream_t stream);
+int launch_smear_lambda(const BoxDev *boxes, int n_boxes, const float *dgt, float *lam, long long hist_len,
+                        const long long *hist_box, cudaStream_t stream);
+
 // ---- empirical-potential update -------------------------------------------------------------
 constexpr int kEpMaxData = 16;     // measured datasets
 constexpr int kEpMaxBasis = 40;    // Poisson functions per pair
@@ -117,6 +137,15 @@ struct EpArgs {
     float *ep;           // [n_pairs][n_bins] the box's table, updated in place
 };
 int launch_ep_update(const EpArgs &a, cudaStream_t stream);
+
+struct ChiParams {
+    int P, n_basis;
+    double s, rho;
+    double W[kEpMaxPairs];     // Eq. (1) weights (2 - delta) c_a c_b b_a b_b, barn
+    double *res_scratch;       // [nQ] residuals
+};
+int launch_chi2(const float *S, const float *target, const float *Q, int nQ, const ChiParams &prm,
+                const double *C, double *chi2, float *dS, double *dC, cudaStream_t stream);
 
 // ---- S(Q) --------------------------------------------------------------------------------
 int sq_build_kernel_matrix(const float *Q, int nQ, int n_bins, double dr, int mode, float *K32,

@@ -16,6 +16,19 @@ namespace epsr {
 
 constexpr int kEpThreads = 512;
 
+__device__ double block_sum_chi(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[i];
+    return t;
+}
+
 __device__ double block_sum(double v, double *red)
 {
 #pragma unroll
@@ -144,11 +157,57 @@ ep_update_kernel(EpArgs A)
     }
 }
 
+// ---- chi^2 of the differentiable form: chi2 = sum_Q [S(Q) + sum_p W_p sum_n C_pn F_n(Q) - T(Q)]^2
+// One CTA (deterministic FP64 reduction order); dS = 2 res, dC_pn = 2 W_p sum_Q res F_n(Q).
+constexpr int kChiThreads = 512;
+constexpr int kChiMaxQ = 8192;
+
+__global__ void __launch_bounds__(kChiThreads, 1)
+chi2_kernel(const float *S, const float *T, const float *Q, int nQ, ChiParams prm, const double *C,
+            double *chi2, float *dS, double *dC)
+{
+    __shared__ double red[kChiThreads / 32];
+    double part = 0.0;
+    for (int i = threadIdx.x; i < nQ; i += kChiThreads) {
+        double img = 0.0;
+        if (C)
+            for (int p = 0; p < prm.P; ++p) {
+                double v = 0.0;
+                for (int n = 1; n <= prm.n_basis; ++n)
+                    v += C[p * prm.n_basis + n - 1] * poisson_F(n, prm.s, (double)Q[i], prm.rho);
+                img += prm.W[p] * v;
+            }
+        const double res = (double)S[i] + img - (double)T[i];
+        dS[i] = (float)(2.0 * res);
+        prm.res_scratch[i] = res;
+        part += res * res;
+    }
+    const double tot = block_sum_chi(part, red);
+    if (threadIdx.x == 0) *chi2 = tot;
+    __syncthreads();
+    if (dC)
+        for (int e = threadIdx.x; e < prm.P * prm.n_basis; e += kChiThreads) {
+            const int p = e / prm.n_basis, n = e % prm.n_basis + 1;
+            double v = 0.0;
+            for (int i = 0; i < nQ; ++i) v += prm.res_scratch[i] * poisson_F(n, prm.s, (double)Q[i], prm.rho);
+            dC[e] = 2.0 * prm.W[p] * v;
+        }
+}
+
 int launch_ep_update(const EpArgs &a, cudaStream_t stream)
 {
     ep_update_kernel<<<1, kEpThreads, 0, stream>>>(a);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "ep_update");
+}
+
+int launch_chi2(const float *S, const float *target, const float *Q, int nQ, const ChiParams &prm,
+                const double *C, double *chi2, float *dS, double *dC, cudaStream_t stream)
+{
+    if (nQ > kChiMaxQ) return set_error(EPSR_EINVAL, "chi2: nQ above %d", kChiMaxQ);
+    chi2_kernel<<<1, kChiThreads, 0, stream>>>(S, target, Q, nQ, prm, C, chi2, dS, dC);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "chi2");
 }
 
 }  // namespace epsr

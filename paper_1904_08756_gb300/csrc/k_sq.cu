@@ -109,4 +109,33 @@ int sq_totals(const float *S_partial, int n_sets, int cols_per_set, int nQ, cons
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_total");
 }
 
+// Adjoint of the contraction: dg[c][k] = w_c sum_i K[i][k] dS_total[set(c)][i] (Kahan FP32).
+__global__ void sq_adjoint_kernel(SqArgs A, const float *dS, int cols_per_set, float *dg)
+{
+    const long long n = (long long)A.n_cols * A.n_bins;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / A.n_bins), k = (int)(e % A.n_bins);
+        const float *row = A.Kt + (long long)k * A.nQ;
+        const float *d = dS + (long long)(c / cols_per_set) * A.nQ;
+        float sum = 0.f, comp = 0.f;
+        for (int i = 0; i < A.nQ; ++i) {
+            const float y = row[i] * d[i] - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        dg[e] = (float)((double)sum * A.w[c]);
+    }
+}
+
+int sq_exec_adjoint(const SqArgs &A, const float *dS, int cols_per_set, float *dg, cudaStream_t stream)
+{
+    const long long n = (long long)A.n_cols * A.n_bins;
+    const int grid = (int)((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096);
+    sq_adjoint_kernel<<<grid, 128, 0, stream>>>(A, dS, cols_per_set, dg);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_adjoint");
+}
+
 }  // namespace epsr

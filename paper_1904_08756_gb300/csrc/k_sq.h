@@ -22,6 +22,7 @@ struct SqWeights {
 
 int sq_build_kt(const float *Q_dev, int nQ, int n_bins, double dr, float *Kt, cudaStream_t stream);
 int sq_exec_fp32(const SqArgs &A, cudaStream_t stream);
+int sq_exec_adjoint(const SqArgs &A, const float *dS, int cols_per_set, float *dg, cudaStream_t stream);
 int sq_totals(const float *S_partial, int n_sets, int cols_per_set, int nQ, const SqWeights &W,
               float *S_total, cudaStream_t stream);
 

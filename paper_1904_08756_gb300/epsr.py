@@ -33,6 +33,7 @@ EXPORTS = [
     "epsr_partial_gr", "epsr_partial_gr_tiles", "epsr_partial_gr_range", "epsr_normalize_g",
     "epsr_sq_weights", "epsr_sq_plan_create", "epsr_sq_plan_destroy", "epsr_sq_exec", "epsr_sq",
     "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc", "epsr_ep_update",
+    "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
 ]
 
 
@@ -109,6 +110,10 @@ def lib():
             "epsr_sq": ([vp, i32, i32, dbl, vp, i32, vp, i32, vp, vp, vp, i32, vp], C.c_int),
             "epsr_noalloc_scratch_bytes": ([], C.c_size_t),
             "epsr_ep_update": ([vp, i32, vp, i32, vp, vp, i32, i32, dbl, dbl, dbl, vp, vp], C.c_int),
+            "epsr_gr_smeared_fwd": ([vp, dbl, vp, vp, vp], C.c_int),
+            "epsr_gr_smeared_bwd": ([vp, dbl, vp, vp, vp], C.c_int),
+            "epsr_sq_exec_adjoint": ([vp, vp, i32, vp, i32, vp, vp], C.c_int),
+            "epsr_chi2": ([vp, vp, vp, vp, i32, vp, i32, dbl, dbl, vp, vp, vp, vp], C.c_int),
             "epsr_partial_gr_noalloc": ([vp, vp, i64, i64, i32, i32, i32, i32, i32, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -312,6 +317,14 @@ class Box:
                                     _stream(stream)), "epsr_ep_update")
         return C_
 
+    def epsr_gr_smeared_fwd(self, sigma: float, Ht, gt=None, stream=None):
+        _check(lib().epsr_gr_smeared_fwd(self.h, sigma, _dev_ptr(Ht), _dev_ptr(gt), _stream(stream)),
+               "epsr_gr_smeared_fwd")
+
+    def epsr_gr_smeared_bwd(self, sigma: float, dgt, grad, stream=None):
+        _check(lib().epsr_gr_smeared_bwd(self.h, sigma, _dev_ptr(dgt), _dev_ptr(grad), _stream(stream)),
+               "epsr_gr_smeared_bwd")
+
     def epsr_sq_weights(self, b: int):
         P = self.systems[b].n_types * (self.systems[b].n_types + 1) // 2
         w = np.zeros(P, np.float64)
@@ -350,6 +363,67 @@ class SqPlan:
         _check(lib().epsr_sq_exec(self.h, _dev_ptr(g), n_cols, _np_ptr(w), cols_per_set,
                                   _np_ptr(flat), _dev_ptr(S_partial), _dev_ptr(S_total),
                                   _stream(stream)), "epsr_sq_exec")
+
+
+def _plan_adjoint(plan, dS_total, w, cols_per_set, dg, stream=None):
+    w = np.ascontiguousarray(w, np.float64)
+    _check(lib().epsr_sq_exec_adjoint(plan.h, _dev_ptr(dS_total), dg.shape[0], _np_ptr(w), cols_per_set,
+                                      _dev_ptr(dg), _stream(stream)), "epsr_sq_exec_adjoint")
+
+
+def _plan_chi2(plan, S, target, W, C, s_basis, rho, chi2, dS, dC, stream=None):
+    W = np.ascontiguousarray(W, np.float64)
+    n_basis = C.shape[1] if C is not None else 0
+    _check(lib().epsr_chi2(plan.h, _dev_ptr(S), _dev_ptr(target), _np_ptr(W), len(W), _dev_ptr(C),
+                           n_basis, s_basis, rho, _dev_ptr(chi2), _dev_ptr(dS), _dev_ptr(dC),
+                           _stream(stream)), "epsr_chi2")
+
+
+SqPlan.epsr_sq_exec_adjoint = _plan_adjoint
+SqPlan.epsr_chi2 = _plan_chi2
+
+
+def smeared_chi2_function():
+    """torch.autograd.Function for chi^2(x, C) of the differentiable form: forward runs
+    epsr_gr_smeared_fwd -> epsr_sq_exec -> epsr_chi2, backward runs epsr_sq_exec_adjoint ->
+    epsr_gr_smeared_bwd. The positions are the box's own; `pos` is the tensor the gradient
+    dchi2/dx (per Angstrom, [n_atoms][3]) is returned for. Only the upstream gradient is
+    applied in torch (a scalar scale)."""
+    import torch
+
+    class SmearedChi2(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, pos, C_, box, plan, sigma, W, w_cols, flat, target, s_basis, rho):
+            dev = pos.device
+            P = len(W)
+            Ht = torch.empty(box.hist_len, dtype=torch.float64, device=dev)
+            gt = torch.empty(box.hist_len, dtype=torch.float32, device=dev)
+            box.epsr_gr_smeared_fwd(sigma, Ht, gt)
+            S = torch.empty((1, plan.nQ), dtype=torch.float32, device=dev)
+            plan.epsr_sq_exec(gt.view(P, -1), w_cols, P, np.array([flat]), None, S)
+            chi2 = torch.empty(1, dtype=torch.float64, device=dev)
+            dS = torch.empty(plan.nQ, dtype=torch.float32, device=dev)
+            dC = torch.empty_like(C_) if C_ is not None else None
+            plan.epsr_chi2(S, target, W, C_.contiguous() if C_ is not None else None, s_basis, rho,
+                           chi2, dS, dC)
+            ctx.box, ctx.plan, ctx.sigma, ctx.w_cols, ctx.P = box, plan, sigma, w_cols, P
+            ctx.save_for_backward(dS, dC if dC is not None else torch.empty(0, device=dev))
+            ctx.has_C = C_ is not None
+            ctx.S = S
+            return chi2[0]
+
+        @staticmethod
+        def backward(ctx, gout):
+            dS, dC = ctx.saved_tensors
+            dev = dS.device
+            dg = torch.empty((ctx.P, ctx.plan.n_bins), dtype=torch.float32, device=dev)
+            ctx.plan.epsr_sq_exec_adjoint((dS * gout.float()).view(1, -1), ctx.w_cols, ctx.P, dg)
+            grad = torch.empty((ctx.box.n_atoms, 3), dtype=torch.float32, device=dev)
+            ctx.box.epsr_gr_smeared_bwd(ctx.sigma, dg, grad)
+            gC = dC * gout if ctx.has_C else None
+            return grad, gC, None, None, None, None, None, None, None, None, None
+
+    return SmearedChi2
 
 
 def epsr_sq(g, dr: float, Q: np.ndarray, w: np.ndarray, cols_per_set: int, flat: np.ndarray,

@@ -361,3 +361,82 @@ def test_ep_update_against_oracle(small_water, n_data, gamma):
     box.epsr_ep_update(0, dS, w, Q, n_basis=20, s_basis=0.5, gamma=gamma, alpha=1.0)
     t2 = box.epsr_box_get_ep(0, (3, s.n_bins)).astype(np.float64)
     assert np.abs(t2 - 2 * ref).max() <= 2e-4 * np.abs(ref).max() + 1e-6
+
+
+# --------------------------------------------------------------------------------------
+# differentiable form: smeared g(r), chi^2 and its adjoint
+# --------------------------------------------------------------------------------------
+
+def _diff_setup(s, target_seed, sigma, n_basis=4, noise=0.005):
+    box = epsr.Box(s)
+    W, flat = oracle.eq1_weights(s)
+    rho = s.n_atoms / s.L ** 3
+    w_cols = 4 * math.pi * rho * W
+    Q = s.Q.astype(np.float32).astype(np.float64)
+    plan = epsr.SqPlan(s.Q, s.n_bins, s.dr, epsr.SQ_FP32, max_cols=3)
+    rng = np.random.default_rng(target_seed)
+    target = flat + rng.normal(size=len(Q)) * noise
+    C_ = rng.normal(size=(3, n_basis)) * 0.01
+    return box, plan, W, flat, rho, w_cols, Q, target, C_
+
+
+def test_smeared_chi2_and_gradients_small_box():
+    s = synth.water_box(300, seed=41, L_A=20.8)
+    sigma = 0.05
+    box, plan, W, flat, rho, w_cols, Q, target, C_ = _diff_setup(s, 5, sigma)
+    F = epsr.smeared_chi2_function()
+    pos = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device=DEV, requires_grad=True)
+    Ct = torch.tensor(C_, dtype=torch.float64, device=DEV, requires_grad=True)
+    tgt = torch.tensor(target, dtype=torch.float32, device=DEV)
+    chi2 = F.apply(pos, Ct, box, plan, sigma, W, w_cols, flat, tgt, 0.5, rho)
+    chi2.backward()
+    ob = oracle.Box(s)
+    tgt64 = tgt.cpu().numpy().astype(np.float64)
+    c_ref, dC_ref, gx_ref, S_ref, _ = oracle.chi2_and_grads(ob, sigma, Q, tgt64, C_, 0.5)
+    assert abs(chi2.item() - c_ref) <= 1e-4 * abs(c_ref)
+    assert np.abs(Ct.grad.cpu().numpy() - dC_ref).max() <= 1e-4 * np.abs(dC_ref).max()
+    g = pos.grad.cpu().numpy()
+    rel = np.linalg.norm(g - gx_ref) / np.linalg.norm(gx_ref)
+    assert rel <= 1e-4, rel
+
+
+def test_smeared_histogram_matches_oracle():
+    s = synth.water_box(400, seed=42, L_A=23.0)
+    box = epsr.Box(s)
+    Ht = torch.zeros(box.hist_len, dtype=torch.float64, device=DEV)
+    box.epsr_gr_smeared_fwd(0.05, Ht)
+    torch.cuda.synchronize()
+    ref = oracle.Box(s).smeared_hist(0.05)
+    got = Ht.cpu().numpy().reshape(ref.shape)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_smeared_gradient_paper_size_sampled():
+    """99,999-atom water (seed 4), target from a seed-5 box plus N(0, 0.005^2) noise: the
+    GPU gradient of chi^2 against the FP64 oracle on 64 sampled atoms."""
+    s = synth.paper_water(seed=4)
+    t = synth.paper_water(seed=5)
+    sigma = 0.05
+    box = epsr.Box(s)
+    W, flat = oracle.eq1_weights(s)
+    rho = s.n_atoms / s.L ** 3
+    w_cols = 4 * math.pi * rho * W
+    Q = s.Q.astype(np.float32).astype(np.float64)
+    plan = epsr.SqPlan(s.Q, s.n_bins, s.dr, epsr.SQ_FP32, max_cols=3)
+    ot = oracle.Box(t)
+    _, St = oracle.sq_of_box(ot, ot.normalize_g(ot.histogram(threads=0)), Q=Q)
+    target = St + np.random.default_rng(5).normal(size=len(Q)) * 0.005
+    C_ = np.random.default_rng(6).normal(size=(3, 20)) * 0.001
+    F = epsr.smeared_chi2_function()
+    pos = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device=DEV, requires_grad=True)
+    Ct = torch.tensor(C_, dtype=torch.float64, device=DEV, requires_grad=True)
+    tgt = torch.tensor(target, dtype=torch.float32, device=DEV)
+    chi2 = F.apply(pos, Ct, box, plan, sigma, W, w_cols, flat, tgt, 0.5, rho)
+    chi2.backward()
+    ob = oracle.Box(s)
+    idx = np.random.default_rng(7).choice(s.n_atoms, 64, replace=False)
+    tgt64 = tgt.cpu().numpy().astype(np.float64)
+    c_ref, dC_ref, gx_ref, _, _ = oracle.chi2_and_grads(ob, sigma, Q, tgt64, C_, 0.5, grad_atoms=idx)
+    assert abs(chi2.item() - c_ref) <= 1e-4 * abs(c_ref)
+    g = pos.grad.cpu().numpy()[idx]
+    assert np.linalg.norm(g - gx_ref) <= 1e-4 * np.linalg.norm(gx_ref)
