@@ -842,12 +842,16 @@ struct epsr_sq_plan {
     float *Kt = nullptr;
     float *Sp_scratch = nullptr;
     double *res = nullptr;      // chi^2 residuals [nQ]
+    // tensor-core modes
+    unsigned char *a_packed = nullptr, *b_packed = nullptr;
+    int *tc_status = nullptr;
+    int fmt_bf16 = 1, np = 2, kt = 64, stages = 0, m_tiles = 0, n_products = 0;
+    int prod_a[8] = {0}, prod_b[8] = {0};
     ~epsr_sq_plan()
     {
-        if (Q) cudaFree(Q);
-        if (Kt) cudaFree(Kt);
-        if (Sp_scratch) cudaFree(Sp_scratch);
-        if (res) cudaFree(res);
+        void *ptrs[] = {Q, Kt, Sp_scratch, res, a_packed, b_packed, tc_status};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
     }
 };
 
@@ -859,7 +863,7 @@ extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, d
     if (!Q || nQ < 1 || nQ > (1 << 20) || n_bins < 1 || n_bins > EPSR_MAX_BINS || !(dr > 0) ||
         max_cols < 1 || max_cols > EPSR_SQ_MAX_COLS)
         return set_error(EPSR_EINVAL, "sq plan: argument out of range");
-    if (mode != EPSR_SQ_FP32) return set_error(EPSR_EINVAL, "sq plan: mode %d not available", mode);
+    if (mode < EPSR_SQ_FP32 || mode > EPSR_SQ_BF16X6) return set_error(EPSR_EINVAL, "sq plan: mode %d unknown", mode);
     for (int i = 0; i < nQ; ++i)
         if (!(Q[i] > 0) || !std::isfinite(Q[i])) return set_error(EPSR_EINVAL, "sq plan: Q[%d] must be > 0", i);
     epsr_sq_plan *p = new (std::nothrow) epsr_sq_plan();
@@ -875,6 +879,33 @@ extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, d
     cudaError_t e = cudaMemcpyAsync(p->Q, Q, nQ * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { delete p; return set_cuda_error(e, "sq plan upload"); }
     if ((rc = sq_build_kt(p->Q, nQ, n_bins, dr, p->Kt, s))) { delete p; return rc; }
+    if (mode != EPSR_SQ_FP32) {
+        p->fmt_bf16 = mode == EPSR_SQ_TF32X3 ? 0 : 1;
+        p->np = mode == EPSR_SQ_BF16X6 ? 3 : 2;
+        const int esize = p->fmt_bf16 ? 2 : 4;
+        p->kt = 128 / esize;                       // 128-byte rows per stage
+        p->stages = (n_bins + p->kt - 1) / p->kt;
+        p->m_tiles = (nQ + 127) / 128;
+        int np_ = 0;
+        for (int i = 0; i < p->np; ++i)
+            for (int j = 0; j < p->np; ++j)
+                if (i + j < p->np) { p->prod_a[np_] = i; p->prod_b[np_] = j; ++np_; }
+        p->n_products = np_;
+        const int n_pad = std::min(256, ((max_cols + 15) / 16) * 16);
+        const size_t a_bytes = (size_t)p->m_tiles * p->stages * p->np * 128 * p->kt * esize;
+        const size_t b_bytes = (size_t)p->stages * p->np * n_pad * p->kt * esize;
+        if ((rc = dalloc(&p->a_packed, a_bytes)) || (rc = dalloc(&p->b_packed, b_bytes)) ||
+            (rc = dalloc(&p->tc_status, 1))) {
+            delete p;
+            return rc;
+        }
+        cudaMemsetAsync(p->tc_status, 0, sizeof(int), s);
+        if ((rc = tc_pack_a(p->Kt, nQ, n_bins, p->m_tiles, p->stages, p->kt, p->np, p->fmt_bf16,
+                            p->a_packed, s))) {
+            delete p;
+            return rc;
+        }
+    }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { delete p; return set_cuda_error(e, "sq plan sync"); }
     *out = p;
@@ -907,7 +938,38 @@ extern "C" int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, 
     a->n_bins = plan->n_bins;
     a->n_cols = n_cols;
     for (int c = 0; c < n_cols; ++c) a->w[c] = w[c];
-    int rc = sq_exec_fp32(*a, (cudaStream_t)stream);
+    int rc = EPSR_OK;
+    if (plan->mode == EPSR_SQ_FP32) {
+        rc = sq_exec_fp32(*a, (cudaStream_t)stream);
+    } else {
+        // tensor cores: chunks of at most 256 columns (one N tile of M = 128 MMAs)
+        TcArgs *t = new (std::nothrow) TcArgs();
+        if (!t) { delete a; return set_error(EPSR_ENOMEM, "host allocation failed"); }
+        for (int c0 = 0; c0 < n_cols && !rc; c0 += 256) {
+            const int nc = std::min(256, n_cols - c0);
+            t->a_packed = plan->a_packed;
+            t->b_packed = plan->b_packed;
+            t->S_partial = a->S_partial + (size_t)c0 * plan->nQ;
+            t->status = plan->tc_status;
+            t->nQ = plan->nQ;
+            t->n_bins = plan->n_bins;
+            t->n_cols = nc;
+            t->n_pad = ((nc + 15) / 16) * 16;
+            int tc = 32;
+            while (tc < t->n_pad) tc <<= 1;
+            t->tmem_cols = tc;
+            t->m_tiles = plan->m_tiles;
+            t->stages = plan->stages;
+            t->kt = plan->kt;
+            t->np_a = t->np_b = plan->np;
+            t->fmt_bf16 = plan->fmt_bf16;
+            t->n_products = plan->n_products;
+            for (int i = 0; i < 8; ++i) { t->prod_a[i] = plan->prod_a[i]; t->prod_b[i] = plan->prod_b[i]; }
+            for (int c = 0; c < nc; ++c) t->w[c] = w[c0 + c];
+            rc = tc_exec(*t, g + (size_t)c0 * plan->n_bins, (cudaStream_t)stream);
+        }
+        delete t;
+    }
     if (!rc && S_total) {
         SqWeights *W = new (std::nothrow) SqWeights();
         if (!W) { delete a; return set_error(EPSR_ENOMEM, "host allocation failed"); }
@@ -931,6 +993,11 @@ extern "C" int epsr_sq(const float *g, int32_t n_cols, int32_t n_bins, double dr
     if (!rc) {
         cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
         if (e != cudaSuccess) rc = set_cuda_error(e, "sq sync");
+    }
+    if (!rc && p->tc_status) {
+        int st = 0;
+        cudaMemcpy(&st, p->tc_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (st) rc = set_error(EPSR_ETIMEOUT, "sq: a tensor-core completion wait gave up");
     }
     epsr_sq_plan_destroy(p);
     return rc;

@@ -440,3 +440,45 @@ def test_smeared_gradient_paper_size_sampled():
     assert abs(chi2.item() - c_ref) <= 1e-4 * abs(c_ref)
     g = pos.grad.cpu().numpy()[idx]
     assert np.linalg.norm(g - gx_ref) <= 1e-4 * np.linalg.norm(gx_ref)
+
+
+# --------------------------------------------------------------------------------------
+# S(Q) on tensor cores (tcgen05) with split precision
+# --------------------------------------------------------------------------------------
+
+def _synthetic_g(n_cols, n_bins, dr, seed):
+    """g-like columns: excluded core, oscillating shells, a sharp intramolecular spike."""
+    rng = np.random.default_rng(seed)
+    r = (np.arange(n_bins) + 0.5) * dr
+    g = np.ones((n_cols, n_bins))
+    for c in range(n_cols):
+        r0 = rng.uniform(2.4, 3.2)
+        g[c] = 1 + 1.5 * np.exp(-((r - r0) / 0.25) ** 2) - np.exp(-(r / 1.8) ** 8) \
+            + 0.3 * np.sin(2 * np.pi * r / r0) * np.exp(-r / 4) + rng.normal(size=n_bins) * 0.01
+        k = int(rng.uniform(0.95, 1.6) / dr)
+        g[c, k] += rng.uniform(10, 80)
+    return g.astype(np.float32)
+
+
+@pytest.mark.parametrize("mode,tol", [(epsr.SQ_TF32X3, 1e-4), (epsr.SQ_BF16X6, 1e-4),
+                                      (epsr.SQ_BF16X3, 1e-4), (epsr.SQ_FP32, 1e-4)])
+@pytest.mark.parametrize("n_cols", [3, 192])
+def test_sq_modes_against_oracle(mode, tol, n_cols):
+    n_bins, dr = 600, 0.02
+    Q = 0.3 + np.arange(2000) * (39.7 / 1999)
+    g = _synthetic_g(n_cols, n_bins, dr, seed=n_cols)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.05, 0.4, n_cols)
+    flat = rng.uniform(0.2, 0.6, n_cols // 3)
+    plan = epsr.SqPlan(Q, n_bins, dr, mode, max_cols=n_cols)
+    gd = torch.from_numpy(g).to(DEV)
+    Sp = torch.zeros((n_cols, 2000), dtype=torch.float32, device=DEV)
+    St = torch.zeros((n_cols // 3, 2000), dtype=torch.float32, device=DEV)
+    plan.epsr_sq_exec(gd, w, 3, flat, Sp, St)
+    torch.cuda.synchronize()
+    Sp_ref, St_ref = oracle.sq(g.astype(np.float64), dr, Q.astype(np.float32).astype(np.float64),
+                               w, 3, flat)
+    err_p = np.abs(Sp.cpu().numpy() - Sp_ref).max()
+    err_t = np.abs(St.cpu().numpy() - St_ref).max()
+    print(f"mode {mode} cols {n_cols}: max |dS_partial| {err_p:.3e}, max |dS_total| {err_t:.3e}")
+    assert err_t <= tol and err_p <= tol
