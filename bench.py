@@ -99,11 +99,19 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_name(system, moves: int) -> str:
+    m = int(system.mol_start[1] - system.mol_start[0])
+    kind = (f"{system.n_mol} rigid {m}-site molecules" if m > 1 else "single-atom moves")
+    return (f"paper-scale {system.name}, {system.n_atoms:,} atoms ({kind}), {moves:,} MC moves + full "
+            f"g_ab(r) ({system.n_bins} x {system.dr:g} A) + S(Q) ({len(system.Q)} Q) per step")
+
+
 # ------------------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
 
-def oracle_step_estimate(system, n_moves_sample: int, n_rows_sample: int, seed: int = 1):
+def oracle_step_estimate(system, n_moves_sample: int, n_rows_sample: int, seed: int = 1,
+                         moves_per_step: int = MOVES_PER_STEP):
     """Time the FP64 oracle on a bounded sample of one step and scale to the full step.
     Returns (seconds per full step, description, threads used)."""
     import oracle
@@ -122,9 +130,9 @@ def oracle_step_estimate(system, n_moves_sample: int, n_rows_sample: int, seed: 
     t0 = time.perf_counter()
     oracle.sq_of_box(ob, g)
     t_sq = time.perf_counter() - t0
-    t_step = MOVES_PER_STEP * t_move + pairs * t_pair + t_sq
+    t_step = moves_per_step * t_move + pairs * t_pair + t_sq
     desc = (f"{n_moves_sample} moves + {pairs_sample:.3g} of {pairs:.3g} pair distances + 1 S(Q) "
-            f"timed, scaled to {MOVES_PER_STEP} moves + all pairs; 1 thread")
+            f"timed, scaled to {moves_per_step} moves + all pairs; 1 thread")
     return t_step, desc, 1, t_move, t_pair
 
 
@@ -157,6 +165,48 @@ def run_reference(args):
 # Replicas: 64 boxes of uneven size advanced together, each step captured as a CUDA graph
 # ------------------------------------------------------------------------------------------
 
+def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
+    """S(Q) of the same resident g(r) columns in every contraction mode: mean time of one
+    epsr_sq_exec (CUDA events on the launching stream, L2 flushed before each) and the largest
+    difference from the FP32 mode's result."""
+    import torch
+    from paper_1904_08756_gb300 import epsr
+    peaks, peak_kind = measured_peaks()
+    names = {epsr.SQ_FP32: "fp32", epsr.SQ_TF32X3: "tf32x3", epsr.SQ_BF16X3: "bf16x3",
+             epsr.SQ_BF16X6: "bf16x6"}
+    products = {epsr.SQ_TF32X3: 3, epsr.SQ_BF16X3: 3, epsr.SQ_BF16X6: 6}
+    n_q, n_bins, n_cols = len(Q), g.shape[1], g.shape[0]
+    out = {}
+    with torch.cuda.stream(stream):
+        for mode, name in names.items():
+            plan = epsr.SqPlan(Q, n_bins, 0.02, mode, max_cols=n_cols)
+            S = torch.zeros_like(S_ref)
+            for _ in range(3):
+                plan.epsr_sq_exec(g, ws, 3, flats, None, S, stream=stream.cuda_stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
+            for a, b in evs:
+                flush.fill_(1.0)
+                a.record(stream)
+                plan.epsr_sq_exec(g, ws, 3, flats, None, S, stream=stream.cuda_stream)
+                b.record(stream)
+            stream.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / reps
+            flops = 2.0 * n_q * n_bins * n_cols
+            rec = {"ms": ms, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
+                   "max_abs_diff_vs_fp32": float((S - S_ref).abs().max())}
+            if mode in products and peaks.get("bf16_tflops"):
+                issued = flops * products[mode] / (ms * 1e-3) / 1e12
+                peak = peaks["bf16_tflops"] * (0.5 if mode == epsr.SQ_TF32X3 else 1.0)
+                rec.update({"tensor_tflops_issued": issued, "tensor_peak_tflops": peak,
+                            "tensor_frac": issued / peak,
+                            "peak_source": f"{peak_kind} bf16 burst" + (" x 1/2 (tf32 nominal ratio)"
+                                                                   if mode == epsr.SQ_TF32X3 else "")})
+            out[name] = rec
+            plan.close()
+    return out
+
+
 def run_replicas(args):
     import torch
     from paper_1904_08756_gb300 import build, epsr, synth
@@ -188,11 +238,13 @@ def run_replicas(args):
             enqueue(k, stream.cuda_stream)
     torch.cuda.synchronize()
     graphs = []
+    launches0 = epsr.epsr_launch_count()
     for k in range(args.steps):
         gr = torch.cuda.CUDAGraph()
         with torch.cuda.graph(gr, stream=stream):
             enqueue(args.warmup + k, torch.cuda.current_stream().cuda_stream)
         graphs.append(gr)
+    launches = epsr.epsr_launch_count() - launches0     # each captured graph is replayed once
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -206,6 +258,7 @@ def run_replicas(args):
         torch.cuda.synchronize()
     status = box.epsr_mc_status()
     t = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    sq_modes = time_sq_modes(systems[0].Q, g.view(-1, 600), ws, flats, S, nb, stream, flush)
     n_atoms = [s.n_atoms for s in systems]
     line = {"metric": METRIC + " (replica batch)", "value": nb * moves / (t * 1e-3),
             "unit": "moves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -216,7 +269,8 @@ def run_replicas(args):
                                    f"S(Q) [2000 x 600] x [600 x {3 * nb}] per step, one CUDA graph per step",
                        "l2": "flushed before every step outside the timed events"},
             "pair_distances_per_step": sum(n * (n - 1) // 2 for n in n_atoms),
-            "status": status, "clocks": clk.summary()}
+            "status": status, "clocks": clk.summary(), "gpu_launches": launches,
+            "sq_modes": sq_modes}
     print(json.dumps(line), flush=True)
     box.close()
     plan.close()
@@ -234,8 +288,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water", choices=["water", "replicas"],
-                    help="water: the paper-scale box (default line); replicas: 64 uneven boxes")
+    ap.add_argument("--workload", default="water", choices=["water", "silica", "replicas"],
+                    help="water: the paper-scale water box (default line); silica: the paper-scale "
+                         "SiO2 box with single-atom moves; replicas: 64 uneven boxes")
     ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
                     help="moves per step (profiling runs only; the benchmark uses 10,000)")
     args = ap.parse_args()
@@ -247,7 +302,7 @@ def main():
         return run_replicas(args)
 
     import torch
-    from paper_1904_08756_gb300 import build, epsr, synth
+    from paper_1904_08756_gb300 import build, epsr, shard, synth
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -258,8 +313,10 @@ def main():
     if not os.path.exists(epsr.LIB_PATH):
         build.build()
 
-    system = synth.paper_water(seed=1 + rank)
+    system = synth.paper_silica(seed=2 + rank) if args.workload == "silica" else synth.paper_water(seed=1 + rank)
     N = system.n_atoms
+    m_atoms = int(system.mol_start[1] - system.mol_start[0])
+    moves = args.moves
     stream = torch.cuda.current_stream(dev)
     box = epsr.Box(system)
     P = 3
@@ -275,8 +332,8 @@ def main():
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        box.epsr_mc_sweep(args.moves, 2024 + rank, move0[0])
-        move0[0] += args.moves
+        box.epsr_mc_sweep(moves, shard.replica_seed(2024, rank), move0[0])
+        move0[0] += moves
         if ev is not None:
             ev[1].record(stream)
         n_cfg[0] += 1
@@ -294,11 +351,13 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    launches0 = epsr.epsr_launch_count()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))                 # L2 flush, outside the events
             step(evs[k])
         torch.cuda.synchronize()
+    launches = epsr.epsr_launch_count() - launches0
     if ws > 1:
         torch.distributed.barrier()
     t_mc = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
@@ -309,7 +368,7 @@ def main():
         tt = torch.tensor([t_step, t_mc, t_gr, t_sq], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_step, t_mc, t_gr, t_sq = tt.tolist()
-    moves_per_s = ws * MOVES_PER_STEP / (t_step * 1e-3)
+    moves_per_s = ws * moves / (t_step * 1e-3)
     pairs = N * (N - 1) // 2
     gr_pairs_per_s = pairs / (t_gr * 1e-3)
 
@@ -338,9 +397,8 @@ def main():
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         clock = clk.summary()
         alu_peak = sms * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6   # lane-ops/s
-        m_atoms = 3
         evals_per_move = 2 * m_atoms * (N - m_atoms)
-        mc_ops = MOVES_PER_STEP * evals_per_move * OPS_PER_PAIR_EVAL
+        mc_ops = moves * evals_per_move * OPS_PER_PAIR_EVAL
         mc_achieved = mc_ops / (t_mc * 1e-3)
         gr_achieved = pairs * OPS_PER_PAIR_DIST / (t_gr * 1e-3)
         traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
@@ -352,13 +410,13 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "fp32+int64", "data": "synthetic",
-            "config": {"workload": "paper-scale water, 99,999 atoms (33,333 rigid molecules), "
-                                   "10,000 MC moves + full g_ab(r) (333 x 0.03 A) + S(Q) (1000 Q) per step",
-                       "n_atoms": N, "moves_per_step": MOVES_PER_STEP,
+            "config": {"workload": workload_name(system, moves),
+                       "n_atoms": N, "moves_per_step": moves,
                        "l2": "flushed before every step by a 256 MiB write outside the timed events",
                        "parallelism": f"replicas x{ws}"},
             "gr_pair_distances_per_s": gr_pairs_per_s,
-            "mc_moves_per_s_kernel": MOVES_PER_STEP / (t_mc * 1e-3),
+            "mc_moves_per_s_kernel": moves / (t_mc * 1e-3),
+            "mc_pair_evals_per_s_kernel": moves * evals_per_move / (t_mc * 1e-3),
             "ms_breakdown": {"mc_sweep": t_mc, "partial_gr": t_gr, "sq": t_sq},
             "roofline": {"bound": "alu", "achieved": mc_achieved / 1e12, "peak": alu_peak / 1e12,
                          "unit": "Tops/s", "frac": mc_achieved / alu_peak, "traffic": traffic,
@@ -368,13 +426,13 @@ def main():
                             "unit": "Tops/s", "frac": gr_achieved / alu_peak, "kernel": "partial_gr_kernel"},
             "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                        "reasons": clock["reasons"]},
-            "e2e": {"value": ws * MOVES_PER_STEP / (t_e2e * 1e-3), "unit": "moves/s",
+            "e2e": {"value": ws * moves / (t_e2e * 1e-3), "unit": "moves/s",
                     "h2d_bytes_per_step": N * 3 * 4, "d2h_bytes_per_step": len(system.Q) * 4},
-            "gpu_launches": args.steps * 6,
+            "gpu_launches": launches,
         }
         if not args.no_cpu_baseline and ws == 1:
-            t_cpu, desc, cores, t_move, t_pair = oracle_step_estimate(system, 300, 3000)
-            line["cpu_baseline"] = {"value": MOVES_PER_STEP / t_cpu, "unit": "moves/s",
+            t_cpu, desc, cores, t_move, t_pair = oracle_step_estimate(system, 300, 3000, moves_per_step=moves)
+            line["cpu_baseline"] = {"value": moves / t_cpu, "unit": "moves/s",
                                     "cores": cores, "kind": "oracle", "sample": desc,
                                     "moves_per_s": 1.0 / t_move, "pair_distances_per_s": 1.0 / t_pair}
         print(json.dumps(line), flush=True)

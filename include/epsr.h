@@ -209,6 +209,23 @@ int epsr_mc_set_ctas(epsr_box *box, int32_t ctas);
  * and the default limit (2000 ms). Host only. */
 int epsr_debug_barrier_fault(epsr_box *box, int32_t cta, double timeout_ms);
 
+/* Number of kernels this library has enqueued, on any stream and device, since it was
+ * loaded (a host-side counter, one per kernel launch; a launch recorded into a CUDA graph
+ * counts once when it is captured, not at each replay). No counterpart in the paper: it
+ * lets a caller state how many of the library's kernels ran inside a timed region. */
+int epsr_launch_count(uint64_t *count);
+
+/* ---- checkpoint / resume ----------------------------------------------------------------
+ * A checkpoint is the coordinates, the empirical-potential tables and the running MC
+ * statistics of every box, in a host buffer of epsr_checkpoint_size() bytes. The move
+ * stream is counter-based (Philox), so a run resumed from a checkpoint at move index t with
+ * move0 = t continues bit for bit as if it had not stopped. epsr_checkpoint_load accepts
+ * only a checkpoint of a handle with the same boxes, atoms and tables (else EPSR_EINVAL).
+ * Both synchronise. */
+int epsr_checkpoint_size(const epsr_box *box, size_t *bytes);
+int epsr_checkpoint_save(epsr_box *box, void *buf, size_t len, epsr_stream_t stream);
+int epsr_checkpoint_load(epsr_box *box, const void *buf, size_t len, epsr_stream_t stream);
+
 /* ---- pair histograms and g(r) (Sec. 2.3: N(r), O(N^2) per evaluation) -----------------
  * For every unordered pair i < j of each box (intra-molecular pairs included), the
  * exact squared minimum-image distance selects bin k = floor(r / dr); if k < n_bins the

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -34,6 +35,17 @@ int epsr::set_error(int status, const char *fmt, ...)
 int epsr::set_cuda_error(cudaError_t e, const char *what)
 {
     return set_error(EPSR_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void epsr::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int epsr_launch_count(uint64_t *count)
+{
+    if (!count) return set_error(EPSR_EINVAL, "NULL argument");
+    *count = g_launches.load(std::memory_order_relaxed);
+    return EPSR_OK;
 }
 
 #define CK(call)                                                   \
@@ -540,6 +552,7 @@ extern "C" int epsr_box_get_coords_device(epsr_box *box, int32_t *xyz_dev, epsr_
 {
     if (!box || !xyz_dev) return set_error(EPSR_EINVAL, "NULL argument");
     pack_xyz_kernel<<<grid_for(box->n_atoms), 256, 0, (cudaStream_t)stream>>>(box->coords, xyz_dev, box->n_atoms);
+    note_launch();
     CK(cudaGetLastError());
     return EPSR_OK;
 }
@@ -548,6 +561,7 @@ extern "C" int epsr_box_set_coords_device(epsr_box *box, const int32_t *xyz_dev,
 {
     if (!box || !xyz_dev) return set_error(EPSR_EINVAL, "NULL argument");
     unpack_xyz_kernel<<<grid_for(box->n_atoms), 256, 0, (cudaStream_t)stream>>>(xyz_dev, box->coords, box->n_atoms);
+    note_launch();
     CK(cudaGetLastError());
     return EPSR_OK;
 }
@@ -1158,4 +1172,84 @@ extern "C" int epsr_chi2(epsr_sq_plan *plan, const float *S, const float *target
     prm.res_scratch = plan->res;
     return launch_chi2(S, target, plan->Q, plan->nQ, prm, C, chi2, dS, C ? dC : nullptr,
                        (cudaStream_t)stream);
+}
+
+// ---- checkpoint / resume ------------------------------------------------------------------------
+// Layout: magic, version, n_boxes, n_atoms, ep_len; then int32 [n_atoms][3] coordinates,
+// float [ep_len] empirical-potential tables, epsr_mc_stats [n_boxes], int32 [n_boxes] has_ep.
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version, n_boxes;
+    int64_t n_atoms, ep_len;
+};
+static const uint64_t kCkptMagic = 0x5450434b52535045ull;   // "EPSRCKPT"
+
+static size_t ckpt_bytes(const epsr_box *box, long long ep_len)
+{
+    return sizeof(CkptHeader) + (size_t)box->n_atoms * 3 * sizeof(int32_t) + (size_t)ep_len * sizeof(float) +
+           (size_t)box->n_boxes * (sizeof(epsr_mc_stats) + sizeof(int32_t));
+}
+
+static long long ep_total(const epsr_box *box)
+{
+    long long n = 0;
+    for (const auto &b : box->hb) n += (long long)b.n_pairs * b.n_bins;
+    return n;
+}
+
+extern "C" int epsr_checkpoint_size(const epsr_box *box, size_t *bytes)
+{
+    if (!box || !bytes) return set_error(EPSR_EINVAL, "NULL argument");
+    *bytes = ckpt_bytes(box, ep_total(box));
+    return EPSR_OK;
+}
+
+extern "C" int epsr_checkpoint_save(epsr_box *box, void *buf, size_t len, epsr_stream_t stream)
+{
+    if (!box || !buf) return set_error(EPSR_EINVAL, "NULL argument");
+    const long long ep_len = ep_total(box);
+    if (len < ckpt_bytes(box, ep_len)) return set_error(EPSR_EINVAL, "checkpoint buffer too small");
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    CkptHeader h{kCkptMagic, 1u, (uint32_t)box->n_boxes, box->n_atoms, ep_len};
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    int rc = epsr_box_get_coords(box, reinterpret_cast<int32_t *>(p), stream);
+    if (rc) return rc;
+    p += (size_t)box->n_atoms * 3 * sizeof(int32_t);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(p, box->ep, (size_t)ep_len * sizeof(float), cudaMemcpyDeviceToHost, s));
+    p += (size_t)ep_len * sizeof(float);
+    CK(cudaMemcpyAsync(p, box->stats, box->n_boxes * sizeof(epsr_mc_stats), cudaMemcpyDeviceToHost, s));
+    p += box->n_boxes * sizeof(epsr_mc_stats);
+    for (int b = 0; b < box->n_boxes; ++b) reinterpret_cast<int32_t *>(p)[b] = box->hb[b].has_ep;
+    CK(cudaStreamSynchronize(s));
+    return EPSR_OK;
+}
+
+extern "C" int epsr_checkpoint_load(epsr_box *box, const void *buf, size_t len, epsr_stream_t stream)
+{
+    if (!box || !buf) return set_error(EPSR_EINVAL, "NULL argument");
+    const long long ep_len = ep_total(box);
+    if (len < sizeof(CkptHeader)) return set_error(EPSR_EINVAL, "checkpoint too short");
+    CkptHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != kCkptMagic || h.version != 1u || h.n_boxes != (uint32_t)box->n_boxes ||
+        h.n_atoms != box->n_atoms || h.ep_len != ep_len || len < ckpt_bytes(box, ep_len))
+        return set_error(EPSR_EINVAL, "checkpoint does not match this handle");
+    const unsigned char *p = static_cast<const unsigned char *>(buf) + sizeof(h);
+    int rc = epsr_box_set_coords(box, reinterpret_cast<const int32_t *>(p), stream);
+    if (rc) return rc;
+    p += (size_t)box->n_atoms * 3 * sizeof(int32_t);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(box->ep, p, (size_t)ep_len * sizeof(float), cudaMemcpyHostToDevice, s));
+    p += (size_t)ep_len * sizeof(float);
+    CK(cudaMemcpyAsync(box->stats, p, box->n_boxes * sizeof(epsr_mc_stats), cudaMemcpyHostToDevice, s));
+    p += box->n_boxes * sizeof(epsr_mc_stats);
+    for (int b = 0; b < box->n_boxes; ++b) {
+        box->hb[b].has_ep = reinterpret_cast<const int32_t *>(p)[b];
+        set_near(box->hb[b]);
+    }
+    CK(cudaMemcpyAsync(box->boxes, box->hb.data(), box->hb.size() * sizeof(BoxDev), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return EPSR_OK;
 }

@@ -16,6 +16,9 @@ struct MoveRec;
 int set_error(int status, const char *fmt, ...);
 int set_cuda_error(cudaError_t e, const char *what);
 
+// ---- launch accounting (epsr_launch_count): called once after every kernel enqueue ----------
+void note_launch();
+
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
 constexpr size_t kMcMaxDynSmem = 190 * 1024;
 

@@ -178,6 +178,7 @@ extern "C" int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, 
         return set_cuda_error(e, "noalloc gr: upload");
     const int grid = (int)std::min<long long>((n_atoms + 255) / 256, 4096);
     pack_kernel<<<grid, 256, 0, s>>>(d_xyz_in, d_type_in, d_coords, d_atom_box, n_atoms);
+    note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return set_cuda_error(e, "noalloc gr: pack");
     if ((rc = launch_scale_coords(d_box, d_atom_box, d_coords, d_scaled, n_atoms, s))) return rc;
     if ((rc = launch_spatial_sort(d_box, d_atom_box, d_scaled, d_coords, n_atoms, bx.cells_p3, 0, sc,

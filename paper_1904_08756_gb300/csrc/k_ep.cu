@@ -197,6 +197,7 @@ chi2_kernel(const float *S, const float *T, const float *Q, int nQ, ChiParams pr
 int launch_ep_update(const EpArgs &a, cudaStream_t stream)
 {
     ep_update_kernel<<<1, kEpThreads, 0, stream>>>(a);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "ep_update");
 }
@@ -206,6 +207,7 @@ int launch_chi2(const float *S, const float *target, const float *Q, int nQ, con
 {
     if (nQ > kChiMaxQ) return set_error(EPSR_EINVAL, "chi2: nQ above %d", kChiMaxQ);
     chi2_kernel<<<1, kChiThreads, 0, stream>>>(S, target, Q, nQ, prm, C, chi2, dS, dC);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "chi2");
 }

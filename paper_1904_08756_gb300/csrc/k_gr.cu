@@ -44,6 +44,7 @@ int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *co
     if (n == 0) return EPSR_OK;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     scale_coords_kernel<<<grid, 256, 0, stream>>>(boxes, atom_box, coords, scaled, n);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "scale_coords");
 }
@@ -216,13 +217,19 @@ int launch_spatial_sort(const BoxDev *boxes, const int *atom_box, const uint4 *s
     if (e != cudaSuccess) return set_cuda_error(e, "sort memset");
     cell_key_kernel<<<grid, 256, 0, stream>>>(boxes, atom_box, scaled, sc.key, sc.rank, sc.count, n,
                                               type_major);
+    note_launch();
     scan_block_sums_kernel<<<nblk, kScanBlock, 0, stream>>>(sc.count, total_cells, sc.block);
+    note_launch();
     scan_block_offsets_kernel<<<1, 1024, 0, stream>>>(sc.block, nblk);
+    note_launch();
     scan_finish_kernel<<<nblk, kScanBlock, 0, stream>>>(sc.count, total_cells, sc.block, sc.offset);
+    note_launch();
     scatter_index_kernel<<<grid, 256, 0, stream>>>(sc.key, sc.rank, sc.offset, sc.index, n);
+    note_launch();
     const int cgrid = (total_cells + 255) / 256 < 4096 ? (total_cells + 255) / 256 : 4096;
     cell_order_kernel<<<cgrid, 256, 0, stream>>>(sc.count, sc.offset, total_cells, sc.index, scaled,
                                                  coords, s_scaled, s_coords, pos_of);
+    note_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "spatial sort");
 }
@@ -346,6 +353,7 @@ int launch_partial_gr(const GrArgs &args, int grid, cudaStream_t stream)
     if (smem > 200 * 1024)
         return set_error(EPSR_EINVAL, "partial_gr: n_pairs*n_bins too large for shared memory");
     partial_gr_kernel<<<grid, kGrThreads, smem, stream>>>(args);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "partial_gr launch");
 }
@@ -385,6 +393,7 @@ int launch_normalize_g(const BoxDev *boxes, int n_boxes, const unsigned long lon
     const int grid = (int)((hist_len + 255) / 256 < 2048 ? (hist_len + 255) / 256 : 2048);
     normalize_g_kernel<<<grid, 256, 0, stream>>>(boxes, n_boxes, hist, g, 1.0 / (double)n_configs,
                                                  hist_len, hist_box);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "normalize_g");
 }
@@ -479,6 +488,7 @@ int launch_total_energy(const BoxDev *boxes, const int4 *coords, const int *atom
     }
     total_energy_kernel<<<grid, kUThreads, smem, stream>>>(boxes, coords, atom_mol, thresholds, ep,
                                                            tiles, n_tiles, U);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "total_energy launch");
 }

@@ -85,6 +85,7 @@ int launch_mc_moves(const BoxDev *boxes, const int *mol_start, int n_boxes, long
     const long long total = (long long)n_boxes * chunk;
     const int grid = (int)((total + 127) / 128 < 8192 ? (total + 127) / 128 : 8192);
     mc_moves_kernel<<<grid, 128, 0, stream>>>(boxes, mol_start, n_boxes, chunk, n, seed, move0, out);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "mc_moves");
 }
@@ -567,6 +568,7 @@ int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stre
     if (e == cudaErrorCooperativeLaunchTooLarge)
         return set_error(EPSR_ELAUNCH, "mc sweep: cooperative launch of %d CTAs refused", grid);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaLaunchCooperativeKernel(mc)");
+    note_launch();
     return EPSR_OK;
 }
 

@@ -197,6 +197,7 @@ int launch_smear(const SmearArgs &a, bool backward, int grid, cudaStream_t strea
     if (smem > 200 * 1024) return set_error(EPSR_EINVAL, "smeared g: n_pairs*n_bins too large");
     if (backward) smear_kernel<true><<<grid, kSmThreads, smem, stream>>>(a);
     else smear_kernel<false><<<grid, kSmThreads, smem, stream>>>(a);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "smear launch");
 }
@@ -259,6 +260,7 @@ int launch_smear_norm(const BoxDev *boxes, int n_boxes, const unsigned long long
 {
     const int grid = (int)((hist_len + 255) / 256 < 2048 ? (hist_len + 255) / 256 : 2048);
     smear_norm_kernel<<<grid, 256, 0, stream>>>(boxes, n_boxes, acc, Ht, gt, hist_len, hist_box);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "smear_norm");
 }
@@ -268,6 +270,7 @@ int launch_smear_lambda(const BoxDev *boxes, int n_boxes, const float *dgt, floa
 {
     const int grid = (int)((hist_len + 255) / 256 < 2048 ? (hist_len + 255) / 256 : 2048);
     smear_lambda_kernel<<<grid, 256, 0, stream>>>(boxes, n_boxes, dgt, lam, hist_len, hist_box);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "smear_lambda");
 }

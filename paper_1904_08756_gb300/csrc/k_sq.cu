@@ -29,6 +29,7 @@ int sq_build_kt(const float *Q_dev, int nQ, int n_bins, double dr, float *Kt, cu
     const long long n = (long long)nQ * n_bins;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     build_sine_matrix_kernel<<<grid, 256, 0, stream>>>(Q_dev, nQ, n_bins, dr, Kt);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "build_sine_matrix");
 }
@@ -95,6 +96,7 @@ int sq_exec_fp32(const SqArgs &A, cudaStream_t stream)
         attr = true;
     }
     sq_fp32_kernel<<<grid, kSqThreads, smem, stream>>>(A);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_fp32");
 }
@@ -105,6 +107,7 @@ int sq_totals(const float *S_partial, int n_sets, int cols_per_set, int nQ, cons
     const long long n = (long long)n_sets * nQ;
     const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
     sq_total_kernel<<<grid, 256, 0, stream>>>(S_partial, n_sets, cols_per_set, nQ, W, S_total);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_total");
 }
@@ -134,6 +137,7 @@ int sq_exec_adjoint(const SqArgs &A, const float *dS, int cols_per_set, float *d
     const long long n = (long long)A.n_cols * A.n_bins;
     const int grid = (int)((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096);
     sq_adjoint_kernel<<<grid, 128, 0, stream>>>(A, dS, cols_per_set, dg);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "sq_adjoint");
 }

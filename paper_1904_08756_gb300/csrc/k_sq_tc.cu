@@ -288,6 +288,7 @@ int tc_pack_a(const float *Kt, int nQ, int n_bins, int m_tiles, int stages, int 
     const long long total = (long long)m_tiles * kTcM * stages * kt;
     const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
     tc_pack_a_kernel<<<grid, 256, 0, stream>>>(Kt, nQ, n_bins, m_tiles, stages, kt, np, fmt_bf16, out);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "tc_pack_a");
 }
@@ -298,6 +299,7 @@ int tc_exec(const TcArgs &a, const float *g, cudaStream_t stream)
     const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
     tc_pack_b_kernel<<<grid, 256, 0, stream>>>(g, a.n_cols, a.n_bins, a.n_pad, a.stages, a.kt, a.np_b,
                                                a.fmt_bf16, a.b_packed);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e, "tc_pack_b");
     const int esize = a.fmt_bf16 ? 2 : 4;
@@ -310,6 +312,7 @@ int tc_exec(const TcArgs &a, const float *g, cudaStream_t stream)
     }
     if (smem > 200 * 1024) return set_error(EPSR_EINVAL, "tc sq: stage does not fit in shared memory");
     tc_sq_kernel<<<a.m_tiles, kTcThreads, smem, stream>>>(a);
+    note_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "tc_sq launch");
 }

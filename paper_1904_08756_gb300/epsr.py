@@ -34,6 +34,7 @@ EXPORTS = [
     "epsr_sq_weights", "epsr_sq_plan_create", "epsr_sq_plan_destroy", "epsr_sq_exec", "epsr_sq",
     "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc", "epsr_ep_update",
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
+    "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
 ]
 
 
@@ -111,6 +112,10 @@ def lib():
             "epsr_noalloc_scratch_bytes": ([], C.c_size_t),
             "epsr_ep_update": ([vp, i32, vp, i32, vp, vp, i32, i32, dbl, dbl, dbl, vp, vp], C.c_int),
             "epsr_gr_smeared_fwd": ([vp, dbl, vp, vp, vp], C.c_int),
+            "epsr_checkpoint_size": ([vp, P(C.c_size_t)], C.c_int),
+            "epsr_launch_count": ([P(C.c_uint64)], C.c_int),
+            "epsr_checkpoint_save": ([vp, vp, C.c_size_t, vp], C.c_int),
+            "epsr_checkpoint_load": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_gr_smeared_bwd": ([vp, dbl, vp, vp, vp], C.c_int),
             "epsr_sq_exec_adjoint": ([vp, vp, i32, vp, i32, vp, vp], C.c_int),
             "epsr_chi2": ([vp, vp, vp, vp, i32, vp, i32, dbl, dbl, vp, vp, vp, vp], C.c_int),
@@ -180,6 +185,12 @@ def epsr_strerror(status: int) -> str:
 
 def epsr_version() -> int:
     return lib().epsr_version()
+
+
+def epsr_launch_count() -> int:
+    n = C.c_uint64()
+    _check(lib().epsr_launch_count(C.byref(n)), "epsr_launch_count")
+    return n.value
 
 
 class Box:
@@ -316,6 +327,17 @@ class Box:
                                     len(q), n_basis, s_basis, gamma, alpha, _np_ptr(C_),
                                     _stream(stream)), "epsr_ep_update")
         return C_
+
+    def epsr_checkpoint_save(self, stream=None) -> bytes:
+        n = C.c_size_t()
+        _check(lib().epsr_checkpoint_size(self.h, C.byref(n)), "epsr_checkpoint_size")
+        buf = (C.c_char * n.value)()
+        _check(lib().epsr_checkpoint_save(self.h, buf, n.value, _stream(stream)), "epsr_checkpoint_save")
+        return bytes(buf)
+
+    def epsr_checkpoint_load(self, data: bytes, stream=None):
+        buf = (C.c_char * len(data)).from_buffer_copy(data)
+        _check(lib().epsr_checkpoint_load(self.h, buf, len(data), _stream(stream)), "epsr_checkpoint_load")
 
     def epsr_gr_smeared_fwd(self, sigma: float, Ht, gt=None, stream=None):
         _check(lib().epsr_gr_smeared_fwd(self.h, sigma, _dev_ptr(Ht), _dev_ptr(gt), _stream(stream)),

@@ -482,3 +482,25 @@ def test_sq_modes_against_oracle(mode, tol, n_cols):
     err_t = np.abs(St.cpu().numpy() - St_ref).max()
     print(f"mode {mode} cols {n_cols}: max |dS_partial| {err_p:.3e}, max |dS_total| {err_t:.3e}")
     assert err_t <= tol and err_p <= tol
+
+
+def test_checkpoint_resume_is_bit_exact():
+    s = synth.silica_box(800, seed=91)
+    ep = (np.random.default_rng(2).normal(size=(3, s.n_bins)) * 0.2).astype(np.float32)
+    a = epsr.Box(s)
+    a.epsr_box_set_ep(0, ep)
+    a.epsr_mc_sweep(2000, seed=17, move0=0)
+    b = epsr.Box(s)
+    b.epsr_box_set_ep(0, ep)
+    b.epsr_mc_sweep(1000, seed=17, move0=0)
+    ck = b.epsr_checkpoint_save()
+    c = epsr.Box(synth.silica_box(800, seed=91))      # a fresh handle, zero EP table
+    c.epsr_checkpoint_load(ck)
+    c.epsr_mc_sweep(1000, seed=17, move0=1000)
+    assert np.array_equal(a.epsr_box_get_coords(), c.epsr_box_get_coords())
+    assert a.epsr_mc_stats_get()[0][:3] == c.epsr_mc_stats_get()[0][:3]
+    assert np.array_equal(c.epsr_box_get_ep(0, ep.shape), ep)
+    bad = bytearray(ck)
+    bad[0] ^= 1
+    with pytest.raises(epsr.EpsrError):
+        c.epsr_checkpoint_load(bytes(bad))
