@@ -313,7 +313,7 @@ static int upload_mc_groups(epsr_box *h)
     if (h->flags) cudaFree(h->flags);
     h->cta_box = nullptr; h->slots = nullptr; h->flags = nullptr;
     int rc;
-    if ((rc = dalloc(&h->cta_box, cb.size())) || (rc = dalloc(&h->slots, 2 * cb.size() * mc_batch_max())) ||
+    if ((rc = dalloc(&h->cta_box, cb.size())) || (rc = dalloc(&h->slots, 2 * cb.size() * kMcSlotStride)) ||
         (rc = dalloc(&h->flags, cb.size())))
         return rc;
     if (h->mc_sort.count) cudaFree(h->mc_sort.count);

@@ -176,7 +176,7 @@ __device__ __forceinline__ float pair_du(Sep sn, Sep so, const PairRow &pr, cons
     const bool co = below(g2o, so, bx.rc2, bx.rc2_lo, bx.rc2_hi);
     if (cn && co) {
         const float p = an * ao;
-        du = fmaf(pr.kqq * dr2, p * p / (an + ao), du);
+        du = fmaf(pr.kqq * dr2, __fdividef(p * p, an + ao), du);   // 2 ulp; an + ao ~ 0.1..10
     } else if (cn) {
         du = fmaf(pr.kqq, an, du);
     } else if (co) {

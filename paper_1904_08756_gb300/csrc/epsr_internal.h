@@ -21,6 +21,9 @@ void note_launch();
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
 constexpr size_t kMcMaxDynSmem = 190 * 1024;
+// per-CTA barrier slot: the batch's partial dU (16 moves), then the pair-energy corrections
+// this CTA computed (at most 16 * 15 / 2 = 120 pairs)
+constexpr int kMcSlotStride = 16 + 120;
 
 struct McArgs {
     const BoxDev *boxes;
@@ -29,7 +32,7 @@ struct McArgs {
     const long long *thresholds;  // concatenated [n_bins + 1] per box
     const float *ep;              // concatenated [n_pairs * n_bins] per box
     const int *cta_box;           // [grid]
-    float *slots;                 // [2][grid][batch max] partial dU per CTA
+    float *slots;                 // [2][grid][kMcSlotStride] partial dU and pair corrections per CTA
     unsigned *flags;              // [grid] arrival sequence numbers (zeroed per launch)
     epsr_mc_stats *stats;         // [n_boxes] running totals (device)
     epsr_move_log *log;           // nullable [n_boxes][log_stride]

@@ -33,6 +33,8 @@ constexpr int kMcThreads = 512;
 constexpr int kMcWarps = kMcThreads / 32;
 constexpr int kBatchMax = kMcWarps;            // one move per warp
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
+constexpr int kCorrItems = 2160;               // 120 pairs x 3 x 3 atoms x 2 sides (G = 1, water)
+static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
 __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n_boxes,
@@ -114,9 +116,10 @@ struct McShared {
     double u_acc[kBatchMax];
     float part[kBatchMax];
     float base[kBatchMax];
-    float corr_part[kBatchMax * (kBatchMax - 1) / 2 * kMaxMolAtoms];
+    float corr_part[kCorrItems];
     int mm;                                  // largest molecule of the batch
     MoveRec mv[kMoveBlock];                  // staged move records [mv_base, mv_base + kMoveBlock)
+    float acc_du[kMoveBlock];                // rank 0: dU of each decided move if accepted, else 0
     float corr[kBatchMax][kBatchMax];
     float dU[kBatchMax];
     int abort_flag;
@@ -130,6 +133,36 @@ __device__ __forceinline__ float warp_sum(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Warp-wide FP64 sum of v[0..n) (lane-strided, then a fixed shuffle tree), added to acc by lane 0.
+__device__ __forceinline__ void block_sum_du(const float *v, int n, int lane, double &acc)
+{
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += (double)v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) acc += s;
+}
+
+// Correction of local pair u: the sum over atoms a of move k of the sum over atoms b of move
+// k1 of [du(a; b new) - du(a; b old)], in that order. `fine` items hold each du separately;
+// otherwise each item already holds the sum over b (same operations, same order).
+__device__ __forceinline__ float corr_sum(const float *part, int u, int mm, bool fine)
+{
+    float c = 0.f;
+    for (int a = 0; a < mm; ++a) {
+        float ca = 0.f;
+        if (fine)
+            for (int b = 0; b < mm; ++b) {
+                const float *v = part + ((u * mm + a) * mm + b) * 2;
+                ca += v[0] - v[1];
+            }
+        else
+            ca = part[u * mm + a];
+        c += ca;
+    }
+    return c;
 }
 
 __device__ __forceinline__ int floordiv32(int a, int b)   // b > 0
@@ -294,6 +327,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     for (long long t0 = 0; t0 < A.n_moves; par ^= 1) {
         const int kmax = (int)min((long long)A.batch_k, A.n_moves - t0);
         if (t0 + kmax > mv_end) {           // stage the next block of move records
+            if (rank == 0 && warp == 0) block_sum_du(sh.acc_du, (int)(t0 - mv_base), lane, sh.st_sum);
             mv_base = t0;
             mv_end = min(A.n_moves, t0 + kMoveBlock);
             const int4 *src = reinterpret_cast<const int4 *>(moves + mv_base);
@@ -384,6 +418,52 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             if (lane == 0) sh.hw[k] = bx.near_fx + reach + 2;
         }
         __syncthreads();
+        // ---- E. pair-energy corrections between the batch's moved molecules -----------------
+        // Pair pq = (k1 < k) is computed by CTA pq mod G of the box's group, as items (pq, atom
+        // a of move k) against the whole molecule of move k1, spread one per warp before the
+        // partner sums; the per-pair sums travel with the partials through the grid barrier.
+        // Items are (pair, a, b, side): atom a of move k (old and new) against atom b of
+        // move k1 at its new (side 0) or old (side 1) position, one pair_du each, so a CTA's
+        // share (18 items for water with G >= 120) runs as one warp's lanes in parallel.
+        const int npq = nb * (nb - 1) / 2;
+        const int mm = sh.mm;
+        const int n_local = npq > rank ? (npq - rank + G - 1) / G : 0;
+        const int n_items = n_local * mm * mm * 2;
+        if (n_items <= kCorrItems) {
+            for (int it = tid; it < n_items; it += kMcThreads) {
+                const int side = it & 1, b = (it >> 1) % mm, a = ((it >> 1) / mm) % mm;
+                const int pq = rank + ((it >> 1) / mm / mm) * G;
+                int k = 1;
+                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k1 = pq - k * (k - 1) / 2;
+                float v = 0.f;
+                if (a < sh.natoms[k] && b < sh.natoms[k1]) {
+                    const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
+                    const int4 p1 = side ? sh.oldp[k1][b] : sh.newp[par][k1][b];
+                    v = pair_du_cold(sep(na, p1, L), sep(oa, p1, L), bx.row[na.w * kMaxTypes + p1.w], bx, T, ep);
+                }
+                sh.corr_part[it] = v;
+            }
+        } else {                                  // large molecules and few CTAs: items (pair, a)
+            for (int it = tid; it < n_local * mm; it += kMcThreads) {
+                const int a = it % mm, pq = rank + (it / mm) * G;
+                int k = 1;
+                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k1 = pq - k * (k - 1) / 2;
+                float ca = 0.f;
+                if (a < sh.natoms[k]) {
+                    const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
+                    for (int b = 0; b < sh.natoms[k1]; ++b) {
+                        const int4 nb1 = sh.newp[par][k1][b], ob1 = sh.oldp[k1][b];
+                        const PairRow &pr = bx.row[na.w * kMaxTypes + nb1.w];
+                        ca += pair_du_cold(sep(na, nb1, L), sep(oa, nb1, L), pr, bx, T, ep) -
+                              pair_du_cold(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
+                    }
+                }
+                sh.corr_part[it] = ca;
+            }
+        }
+        const bool fine = n_items <= kCorrItems;
         // ---- C. partial dU of move `warp` against this CTA's slice ---------------------------
         if (warp < nb) {
             const int m = sh.natoms[warp];
@@ -408,9 +488,10 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         ++seq;
         if (G > 1) {
             if (tid == 0) {
-                float *slot = A.slots + ((size_t)(seq & 1u) * A.grid + cta) * kBatchMax;
+                float *slot = A.slots + ((size_t)(seq & 1u) * A.grid + cta) * kMcSlotStride;
                 if (cta != A.skip_arrival_cta) {
                     for (int k = 0; k < nb; ++k) slot[k] = sh.part[k];
+                    for (int u = 0; u < n_local; ++u) slot[kBatchMax + u] = corr_sum(sh.corr_part, u, mm, fine);
                     red_add_release_gpu(&A.flags[box], 1u);
                 }
                 const unsigned target = seq * (unsigned)G;
@@ -433,46 +514,25 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             }
             __syncthreads();
             if (sh.abort_flag) return;
+            const float *bs = A.slots + (size_t)(seq & 1u) * A.grid * kMcSlotStride;
             if (warp < nb) {
-                const float *bs = A.slots + (size_t)(seq & 1u) * A.grid * kBatchMax;
                 float v = 0.f;
-                for (int r = lane; r < G; r += 32) v += __ldcg(&bs[(size_t)(bx.cta0 + r) * kBatchMax + warp]);
+                for (int r = lane; r < G; r += 32) v += __ldcg(&bs[(size_t)(bx.cta0 + r) * kMcSlotStride + warp]);
                 v = warp_sum(v);
                 if (lane == 0) sh.base[warp] = v;
             }
-        } else if (tid < nb) {
-            sh.base[tid] = sh.part[tid];
-        }
-        // ---- E. pair-energy corrections between the batch's moved molecules -----------------
-        // item (pair k1 < k, atom a of move k) against the whole molecule of move k1
-        {
-            const int mm = sh.mm;
-            const int npq = nb * (nb - 1) / 2;
-            for (int it = tid; it < npq * mm; it += kMcThreads) {
-                const int pq = it / mm, a = it - pq * mm;
-                int k = 1;
-                while ((k + 1) * k / 2 <= pq) ++k;
-                const int k1 = pq - k * (k - 1) / 2;
-                float c = 0.f;
-                if (a < sh.natoms[k]) {
-                    const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
-                    for (int b = 0; b < sh.natoms[k1]; ++b) {
-                        const int4 nb1 = sh.newp[par][k1][b], ob1 = sh.oldp[k1][b];
-                        const PairRow pr = bx.row[na.w * kMaxTypes + nb1.w];
-                        c += pair_du_cold(sep(na, nb1, L), sep(oa, nb1, L), pr, bx, T, ep) -
-                             pair_du_cold(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
-                    }
-                }
-                sh.corr_part[it] = c;
-            }
-            __syncthreads();
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 int k = 1;
                 while ((k + 1) * k / 2 <= pq) ++k;
-                const int k1 = pq - k * (k - 1) / 2;
-                float c = 0.f;
-                for (int i = 0; i < mm; ++i) c += sh.corr_part[pq * mm + i];
-                sh.corr[k1][k] = c;
+                sh.corr[pq - k * (k - 1) / 2][k] =
+                    __ldcg(&bs[(size_t)(bx.cta0 + pq % G) * kMcSlotStride + kBatchMax + pq / G]);
+            }
+        } else {
+            if (tid < nb) sh.base[tid] = sh.part[tid];
+            for (int pq = tid; pq < npq; pq += kMcThreads) {
+                int k = 1;
+                while ((k + 1) * k / 2 <= pq) ++k;
+                sh.corr[pq - k * (k - 1) / 2][k] = corr_sum(sh.corr_part, pq, mm, fine);
             }
         }
         __syncthreads();
@@ -480,28 +540,32 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         if (warp == 0) {
             float d = lane < nb ? sh.base[lane] : 0.f;
             const float thr = lane < nb ? sh.thr[lane] : 0.f;
+            float cj[kBatchMax];
+#pragma unroll
+            for (int j = 0; j < kBatchMax; ++j) cj[j] = (lane > j && lane < nb) ? sh.corr[j][lane] : 0.f;
             int accepted = 0;
-            for (int j = 0; j < nb; ++j) {
-                const int aj = __shfl_sync(0xffffffffu, (d <= 0.f) || (d < thr), j);
-                if (lane == j) accepted = aj;
-                if (lane > j && lane < nb && aj) d += sh.corr[j][lane];
+#pragma unroll
+            for (int j = 0; j < kBatchMax; ++j) {
+                if (j < nb) {
+                    const int aj = __shfl_sync(0xffffffffu, (d <= 0.f) || (d < thr), j);
+                    if (lane == j) accepted = aj;
+                    if (aj) d += cj[j];
+                }
             }
             if (lane < nb) {
                 sh.dU[lane] = d;
                 sh.acc[par][lane] = accepted;
             }
             if (rank == 0) {
+                // counts now; the FP64 sum of accepted dU once per staged block of moves
                 const unsigned in = lane < nb ? 1u : 0u;
                 const unsigned b_acc = __ballot_sync(0xffffffffu, in && accepted);
                 const unsigned b_nf = __ballot_sync(0xffffffffu, in && !isfinite(d));
-                double v = (in && accepted) ? (double)d : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (in) sh.acc_du[t0 - mv_base + lane] = accepted ? d : 0.f;
                 if (lane == 0) {
                     sh.st_att += nb;
                     sh.st_acc += __popc(b_acc);
                     sh.st_nonfinite += __popc(b_nf);
-                    sh.st_sum += v;
                 }
             }
         }
@@ -532,6 +596,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         t0 += nb;
     }
 
+    if (rank == 0 && warp == 0) block_sum_du(sh.acc_du, (int)(A.n_moves - mv_base), lane, sh.st_sum);
     if (rank == 0 && tid == 0) {
         epsr_mc_stats *st = A.stats + box;
         st->attempted += sh.st_att;
