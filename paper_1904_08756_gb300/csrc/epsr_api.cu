@@ -681,8 +681,12 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     if (n_moves == 0) return EPSR_OK;
     int slice_cap = 0;
     for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
+    int types_cap = 1;
+    for (auto &b : box->hb) types_cap = std::max(types_cap, b.n_types);
+    // slice, thresholds, EP table, cell index [types][513] and home cell per slot (uint16)
     size_t smem = (size_t)slice_cap * sizeof(int4) + (size_t)box->tbl_cap * sizeof(long long) +
-                  (size_t)box->ep_cap * sizeof(float);
+                  (size_t)box->ep_cap * sizeof(float) +
+                  ((size_t)types_cap * (kMcCells + 1) + (size_t)slice_cap) * sizeof(unsigned short);
     smem = (smem + 15) & ~(size_t)15;
     if (smem > kMcMaxDynSmem)
         return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of shared memory per CTA needed (limit %zu); "
@@ -720,6 +724,8 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     a.batch_k = box->mc_batch;
     a.slice_cap = slice_cap;
     a.tbl_cap = box->tbl_cap;
+    a.ep_cap = box->ep_cap;
+    a.types_cap = types_cap;
     a.skip_arrival_cta = box->fault_cta;
     a.moves = box->moves;
     a.chunk = chunk;

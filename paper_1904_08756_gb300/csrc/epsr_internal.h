@@ -52,6 +52,8 @@ struct McArgs {
     int batch_k;
     int slice_cap;                // int4 capacity of the shared partner slice
     int tbl_cap;                  // capacity (entries) of the shared threshold table
+    int ep_cap;                   // capacity (entries) of the shared empirical-potential table
+    int types_cap;                // largest number of atom types of the handle's boxes
     int skip_arrival_cta;         // test hook: this CTA never arrives (-1: none)
 };
 

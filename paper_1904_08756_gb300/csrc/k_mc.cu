@@ -34,6 +34,9 @@ constexpr int kMcWarps = kMcThreads / 32;
 constexpr int kBatchMax = kMcWarps;            // one move per warp
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
 constexpr int kCorrItems = 2160;               // 120 pairs x 3 x 3 atoms x 2 sides (G = 1, water)
+constexpr int kCellMargin = 1 << 20;           // drift allowed before an escapee: 1 A on the 2^20 grid
+constexpr int kEscMax = 256;                   // escapee list capacity per CTA
+constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
 static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
@@ -123,6 +126,9 @@ struct McShared {
     float corr[kBatchMax][kBatchMax];
     float dU[kBatchMax];
     int abort_flag;
+    int cb[9];                               // cell boundaries ceil(j L / 8)
+    int n_esc, cells_on;
+    unsigned short esc[kEscMax];             // escapee slots
     // leader-only running statistics
     long long st_att, st_acc, st_nonfinite;
     double st_sum;
@@ -172,6 +178,66 @@ __device__ __forceinline__ int floordiv32(int a, int b)   // b > 0
     return q;
 }
 
+// ---- near-partner cells -------------------------------------------------------------------------
+// A CTA's partners of each type are ordered by the cell of an 8^3 grid (cell k on an axis
+// holds ceil(k L / 8) <= x < ceil((k + 1) L / 8)) as the sweep starts, so the partners
+// inside a cube around a moved molecule lie in the slice ranges of the few cells the cube
+// meets. Atoms move during the sweep: a partner that leaves its home cell widened by
+// kCellMargin is an escapee; it keeps its slot (flagged in bit 31 of .w) and joins a
+// per-CTA list that every cell query scans in full. Cell queries cover the cube widened by
+// the margin, so together with the escapees every partner inside the cube is found.
+
+struct CellIndex {
+    const unsigned short *cst;   // [n_types][kMcCells + 1] first slot of each cell, relative to blk[t]
+    const int *cb;               // [9] cell boundaries ceil(j L / 8), cb[8] = L
+    const unsigned short *esc;   // escapee slots
+    int n_esc;
+    bool on;                     // cell queries allowed (escapee list not overflowed)
+};
+
+__device__ __forceinline__ int cell_of(int x, const int *cb)   // x in [0, L)
+{
+    int k = 0;
+#pragma unroll
+    for (int j = 1; j < 8; ++j) k += x >= cb[j] ? 1 : 0;
+    return k;
+}
+
+// Cyclic run of cells [k0, k0 + n) (mod 8) meeting [c - w, c + w] on one axis.
+__device__ __forceinline__ void cell_run(int c, long long w, int L, const int *cb, int &k0, int &n)
+{
+    if (8 * (2 * w + 1) >= 7LL * L) { k0 = 0; n = 8; return; }
+    long long lo = c - w, hi = c + w;
+    if (lo < 0) lo += L;
+    if (hi >= L) hi -= L;
+    k0 = cell_of((int)lo, cb);
+    n = ((cell_of((int)hi, cb) - k0) & 7) + 1;
+}
+
+__device__ __forceinline__ unsigned spread3(unsigned v)   // bits 0..2 -> 0, 3, 6
+{
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
+}
+
+__device__ __forceinline__ unsigned compact3(unsigned v)  // bits 0, 3, 6 -> 0..2
+{
+    return (v & 1u) | ((v >> 2) & 2u) | ((v >> 4) & 4u);
+}
+
+__device__ __forceinline__ unsigned cell_code(int cx, int cy, int cz)
+{
+    return spread3((unsigned)cx) | (spread3((unsigned)cy) << 1) | (spread3((unsigned)cz) << 2);
+}
+
+// Is grid point x (one axis) within kCellMargin of cell k's interval (cyclically)?
+__device__ __forceinline__ bool near_cell(int x, int k, const int *cb, int L)
+{
+    long long d = (long long)x - (cb[k] - kCellMargin);
+    if (d < 0) d += L;
+    if (d >= L) d -= L;
+    return d < (long long)(cb[k + 1] - cb[k]) + 2LL * kCellMargin;
+}
+
 // Out-of-line copy of pair_du for code that runs once per batch (keeps the kernel small).
 __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, const BoxDev &bx,
                                            const long long *T, const float *ep)
@@ -181,49 +247,124 @@ __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, co
 
 // Partial dU of one move (atoms np/op, m <= M) against the partners of this CTA, lane-
 // strided. Per partner type the kind of each moved atom's pair row is uniform across the
-// warp: with Lennard-Jones every partner is evaluated (LJ is not cut); without, only
-// partners inside the near cube around old atom 0 (half width hw) can have Coulomb or
-// empirical-potential terms. M is a compile-time bound so the atom loop unrolls into
-// independent dependency chains.
-template <int M>
+// warp: a Lennard-Jones row (LJ is not cut) is evaluated against every partner of the type;
+// a row without LJ has Coulomb or empirical-potential terms only inside the near cube
+// around old atom 0 (half width hw), so its partners come from a cell query when the cube
+// meets at most 32 cells, else from the full scan with the cube test. M is a compile-time
+// bound so the atom loop unrolls into independent dependency chains.
+template <int M, bool CELLS>
 __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int m, int a0, int hw,
-                                             const int4 *slice, const int *blk, const BoxDev &bx,
-                                             const long long *T, const float *ep, int lane)
+                                             const int4 *slice, const int *blk, const CellIndex &ci,
+                                             const BoxDev &bx, const long long *T, const float *ep,
+                                             int lane)
 {
     const int L = bx.L;
     const int4 o0 = op[0];
     int4 pn[M], po[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a)
-        if (a < m) { pn[a] = np[a]; po[a] = op[a]; }
+    for (int a = 0; a < M; ++a) {
+        pn[a] = a < m ? np[a] : make_int4(0, 0, 0, 0);
+        po[a] = a < m ? op[a] : make_int4(0, 0, 0, 0);
+    }
+    int k0x = 0, nx = 8, k0y = 0, ny = 8, k0z = 0, nz = 8;
+    if (CELLS && ci.on) {
+        const long long w = (long long)hw + kCellMargin;
+        cell_run(o0.x, w, L, ci.cb, k0x, nx);
+        cell_run(o0.y, w, L, ci.cb, k0y, ny);
+        cell_run(o0.z, w, L, ci.cb, k0z, nz);
+    }
+    const int ncell = nx * ny * nz;
+    const bool use_cells = CELLS && ci.on && ncell <= 32;
+    unsigned cell_types = 0u;
     float acc = 0.f;
     for (int t = 0; t < bx.n_types; ++t) {
         unsigned lj = 0u, nr = 0u;
-        PairRow pr[M];
+        const PairRow *pr[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) {
+            pr[a] = &bx.row[pn[a].w * kMaxTypes + t];
             if (a >= m) continue;
-            pr[a] = bx.row[pn[a].w * kMaxTypes + t];
-            if (pr[a].c12 != 0.f || pr[a].c6 != 0.f) lj |= 1u << a;
-            else if (pr[a].kqq != 0.f || bx.has_ep) nr |= 1u << a;
+            if (pr[a]->c12 != 0.f || pr[a]->c6 != 0.f) lj |= 1u << a;
+            else if (pr[a]->kqq != 0.f || bx.has_ep) nr |= 1u << a;
         }
         if (!(lj | nr)) continue;
-        const int jb = blk[t + 1];
+        const bool cells = nr && use_cells;
+        const unsigned scan_nr = cells ? 0u : nr;
+        if (lj | scan_nr) {
+            const int jb = blk[t + 1];
 #pragma unroll 2
-        for (int j = blk[t] + lane; j < jb; j += 32) {
-            int4 pj = slice[j];
-            const int jatom = pj.w >> 3;
-            const bool self = jatom >= a0 && jatom < a0 + m;
-            pj.w = t;
-            const bool near = nr && mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw &&
-                              mi_abs(pj.z - o0.z, L) < hw;
+            for (int j = blk[t] + lane; j < jb; j += 32) {
+                int4 pj = slice[j];
+                const int jatom = (pj.w & 0x7fffffff) >> 3;
+                const bool self = jatom >= a0 && jatom < a0 + m;
+                const bool near = scan_nr && mi_abs(pj.x - o0.x, L) < hw &&
+                                  mi_abs(pj.y - o0.y, L) < hw && mi_abs(pj.z - o0.z, L) < hw;
 #pragma unroll
-            for (int a = 0; a < M; ++a) {
-                if (a < m && !self && (((lj >> a) & 1u) || (((nr >> a) & 1u) && near)))
-                    acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), pr[a], bx, T, ep);
+                for (int a = 0; a < M; ++a) {
+                    if (a < m && !self && (((lj >> a) & 1u) || (((scan_nr >> a) & 1u) && near)))
+                        acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
+                }
+            }
+        }
+        if (CELLS && cells) {
+            cell_types |= 1u << t;
+            const unsigned short *cst = ci.cst + t * (kMcCells + 1);
+            int first = 0, cnt = 0;
+            if (lane < ncell) {
+                const int ix = lane % nx, iy = (lane / nx) % ny, iz = lane / (nx * ny);
+                const unsigned code = cell_code((k0x + ix) & 7, (k0y + iy) & 7, (k0z + iz) & 7);
+                first = cst[code];
+                cnt = cst[code + 1] - first;
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - cnt;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                int c = 0;                               // last cell whose run starts at or before q
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(0xffffffffu, excl, c + step);
+                    if (c + step < ncell && e <= q) c += step;
+                }
+                const int cf = __shfl_sync(0xffffffffu, first, c);
+                const int ce = __shfl_sync(0xffffffffu, excl, c);
+                if (q < total) {
+                    const int4 pj = slice[blk[t] + cf + (q - ce)];
+                    const int jatom = (pj.w & 0x7fffffff) >> 3;
+                    const bool take = pj.w >= 0 && !(jatom >= a0 && jatom < a0 + m) &&
+                                      mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw &&
+                                      mi_abs(pj.z - o0.z, L) < hw;
+                    if (take) {
+#pragma unroll
+                        for (int a = 0; a < M; ++a)
+                            if (a < m && ((nr >> a) & 1u))
+                                acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
+                    }
+                }
             }
         }
     }
+    // escapees of the types answered by cell queries (their LJ rows were in the full scans)
+    if (CELLS && cell_types)
+        for (int e = lane; e < ci.n_esc; e += 32) {
+            const int4 pj = slice[ci.esc[e]];
+            const int t = pj.w & 7;
+            const int jatom = (pj.w & 0x7fffffff) >> 3;
+            if (!((cell_types >> t) & 1u) || (jatom >= a0 && jatom < a0 + m)) continue;
+            if (!(mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw && mi_abs(pj.z - o0.z, L) < hw))
+                continue;
+            for (int a = 0; a < m; ++a) {
+                const PairRow &r = bx.row[np[a].w * kMaxTypes + t];
+                if (r.c12 == 0.f && r.c6 == 0.f && (r.kqq != 0.f || bx.has_ep))
+                    acc += pair_du_cold(sep(np[a], pj, L), sep(op[a], pj, L), r, bx, T, ep);
+            }
+        }
     return acc;
 }
 
@@ -245,7 +386,7 @@ __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, in
         if (!(lj | nr)) continue;
         for (int j = blk[t] + lane; j < blk[t + 1]; j += 32) {
             int4 pj = slice[j];
-            const int jatom = pj.w >> 3;
+            const int jatom = (pj.w & 0x7fffffff) >> 3;
             if (jatom >= a0 && jatom < a0 + m) continue;
             pj.w = t;
             const bool near = nr && mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw &&
@@ -317,6 +458,37 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     for (int k = tid; k <= bx.n_bins; k += kMcThreads) T[k] = A.thresholds[bx.tbl_off + k];
     if (bx.has_ep)
         for (int k = tid; k < bx.n_pairs * bx.n_bins; k += kMcThreads) ep[k] = A.ep[bx.ep_off + k];
+    // cell index: first slot of each cell per type (relative to the type's block), the
+    // home cell of every slot, cell boundaries; cell queries only where some pair row has
+    // no Lennard-Jones term but a Coulomb or empirical-potential one
+    unsigned short *cst = reinterpret_cast<unsigned short *>(ep + A.ep_cap);
+    unsigned short *home = cst + A.types_cap * (kMcCells + 1);
+    for (int t = 0; t < nt; ++t) {
+        const int key0 = bx.mc_cell0 + (t * G + rank) * kMcCells;
+        for (int c = tid; c <= kMcCells; c += kMcThreads)
+            cst[t * (kMcCells + 1) + c] = (unsigned short)(A.mc_offset[key0 + c] - A.mc_offset[key0]);
+    }
+    if (tid <= 8) sh.cb[tid] = (int)(((long long)tid * L + 7) / 8);
+    if (tid == 0) {
+        bool near_rows = false;
+        for (int a = 0; a < nt; ++a)
+            for (int b = 0; b < nt; ++b) {
+                const PairRow &r = bx.row[a * kMaxTypes + b];
+                near_rows |= r.c12 == 0.f && r.c6 == 0.f && (r.kqq != 0.f || bx.has_ep);
+            }
+        sh.n_esc = 0;
+        sh.cells_on = near_rows ? 1 : 0;
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const unsigned short *ct = cst + t * (kMcCells + 1);
+        for (int i = tid; i < sh.rl[t]; i += kMcThreads) {
+            int c = 0;                                   // last cell starting at or before i
+            for (int step = kMcCells / 2; step > 0; step >>= 1)
+                if (ct[c + step] <= i) c += step;
+            home[sh.blk[t] + i] = (unsigned short)c;
+        }
+    }
     __syncthreads();
 
     const MoveRec *moves = A.moves + (size_t)box * A.chunk;
@@ -468,12 +640,22 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         if (warp < nb) {
             const int m = sh.natoms[warp];
             float acc;
+            CellIndex ci;
+            ci.cst = cst;
+            ci.cb = sh.cb;
+            ci.esc = sh.esc;
+            ci.n_esc = min(sh.n_esc, kEscMax);
+            ci.on = sh.cells_on != 0;
             if (m == 1)
-                acc = partner_sum<1>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
-                                     slice, sh.blk, bx, T, ep, lane);
+                acc = ci.on ? partner_sum<1, true>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
+                                                   slice, sh.blk, ci, bx, T, ep, lane)
+                            : partner_sum<1, false>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
+                                                    slice, sh.blk, ci, bx, T, ep, lane);
             else if (m <= 3)
-                acc = partner_sum<3>(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
-                                     slice, sh.blk, bx, T, ep, lane);
+                acc = ci.on ? partner_sum<3, true>(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                                                   slice, sh.blk, ci, bx, T, ep, lane)
+                            : partner_sum<3, false>(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                                                    slice, sh.blk, ci, bx, T, ep, lane);
             else
                 acc = partner_sum_any(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
                                       slice, sh.blk, bx, T, ep, lane);
@@ -577,7 +759,26 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             const int ja = sh.a0[k] + a;
             const int4 p = sh.newp[par][k][a];
             const int t = p.w, sp = sh.spos[k][a] - sh.rs[t];
-            if (sp >= 0 && sp < sh.rl[t]) slice[sh.blk[t] + sp] = make_int4(p.x, p.y, p.z, t | (ja << 3));
+            if (sp >= 0 && sp < sh.rl[t]) {
+                const int slot = sh.blk[t] + sp;
+                int w = t | (ja << 3);
+                if (sh.cells_on) {
+                    bool esc = slice[slot].w < 0;
+                    if (!esc) {
+                        const unsigned h = home[slot];
+                        esc = !(near_cell(p.x, (int)compact3(h), sh.cb, L) &&
+                                near_cell(p.y, (int)compact3(h >> 1), sh.cb, L) &&
+                                near_cell(p.z, (int)compact3(h >> 2), sh.cb, L));
+                        if (esc) {
+                            const int e = atomicAdd(&sh.n_esc, 1);
+                            if (e < kEscMax) sh.esc[e] = (unsigned short)slot;
+                            else sh.cells_on = 0;            // too many: full scans from now on
+                        }
+                    }
+                    if (esc) w |= kEscFlag;
+                }
+                slice[slot] = make_int4(p.x, p.y, p.z, w);
+            }
             if (rank == 0) A.coords[bx.atom0 + ja] = p;
         }
         if (rank == 0 && A.log && tid < nb) {
