@@ -203,6 +203,15 @@ int epsr_mc_set_batch(epsr_box *box, int32_t batch_k);
 /* CTAs per box of the sweep (0 = automatic). For a batch of boxes, a total budget split
  * in proportion to the atom counts. Host only; takes effect at the next sweep. */
 int epsr_mc_set_ctas(epsr_box *box, int32_t ctas);
+/* Cell queries of the sweep (a performance device, no effect on results): partners whose
+ * pair rows have no Lennard-Jones term are looked up in the 8^3 cells of each CTA's slice
+ * that meet the cube around the moved molecule widened by margin_fx grid units; a partner
+ * that drifts more than margin_fx out of its cell during a launch joins a per-CTA escapee
+ * list of escapee_cap entries (-1: the maximum, 256; 0: no cell queries, every partner is
+ * scanned) and, when that list is full, the CTA scans every partner for the rest of the
+ * launch. Defaults: 2^20 (1 A), -1. EPSR_EINVAL for margin_fx < 0, margin_fx >= L_fx / 4
+ * of a box, or escapee_cap outside [-1, 256]. Host only; takes effect at the next sweep. */
+int epsr_mc_set_cells(epsr_box *box, int32_t margin_fx, int32_t escapee_cap);
 /* Test hook: CTA `cta` of the following sweeps skips its barrier arrival and every
  * barrier wait is limited to timeout_ms, so the bounded wait expires and the sweep
  * returns EPSR_ETIMEOUT with the GPU context intact. cta = -1 restores normal operation

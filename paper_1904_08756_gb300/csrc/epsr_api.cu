@@ -115,6 +115,8 @@ struct epsr_box {
     std::vector<GrTile> tiles_h;
     int sms = 0;
     int mc_batch = 16;
+    int cell_margin = 1 << 20;                // 1 A on the 2^20 grid
+    int esc_cap = -1;                         // -1: the kernel's maximum
     int mc_ctas = 0;
     int fault_cta = -1;
     double timeout_ms = 2000.0;
@@ -648,6 +650,20 @@ extern "C" int epsr_mc_set_batch(epsr_box *box, int32_t batch_k)
     return EPSR_OK;
 }
 
+extern "C" int epsr_mc_set_cells(epsr_box *box, int32_t margin_fx, int32_t escapee_cap)
+{
+    if (!box) return set_error(EPSR_EINVAL, "NULL argument");
+    if (margin_fx < 0 || escapee_cap < -1 || escapee_cap > mc_escapee_max())
+        return set_error(EPSR_EINVAL, "mc cells: margin %d must be >= 0 and escapee_cap %d in [-1, %d]",
+                         margin_fx, escapee_cap, mc_escapee_max());
+    for (const auto &b : box->hb)
+        if (margin_fx >= b.L / 4)
+            return set_error(EPSR_EINVAL, "mc cells: margin %d not below a quarter of box side %d", margin_fx, b.L);
+    box->cell_margin = margin_fx;
+    box->esc_cap = escapee_cap;
+    return EPSR_OK;
+}
+
 extern "C" int epsr_mc_set_ctas(epsr_box *box, int32_t ctas)
 {
     if (!box || ctas < 0 || ctas > 65536) return set_error(EPSR_EINVAL, "ctas out of range");
@@ -726,6 +742,8 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     a.tbl_cap = box->tbl_cap;
     a.ep_cap = box->ep_cap;
     a.types_cap = types_cap;
+    a.cell_margin = box->cell_margin;
+    a.esc_cap = box->esc_cap < 0 ? mc_escapee_max() : box->esc_cap;
     a.skip_arrival_cta = box->fault_cta;
     a.moves = box->moves;
     a.chunk = chunk;

@@ -54,6 +54,8 @@ struct McArgs {
     int tbl_cap;                  // capacity (entries) of the shared threshold table
     int ep_cap;                   // capacity (entries) of the shared empirical-potential table
     int types_cap;                // largest number of atom types of the handle's boxes
+    int cell_margin;              // drift (grid units) before a partner leaves its cell's queries
+    int esc_cap;                  // escapee list capacity (0: no cell queries)
     int skip_arrival_cta;         // test hook: this CTA never arrives (-1: none)
 };
 
@@ -62,6 +64,7 @@ int launch_mc_moves(const BoxDev *boxes, const int *mol_start, int n_boxes, long
                     long long n, unsigned long long seed, unsigned long long move0, MoveRec *out,
                     cudaStream_t stream);
 int mc_threads();
+int mc_escapee_max();
 int mc_batch_max();
 
 // ---- pair histogram kernels ---------------------------------------------------------------

@@ -34,8 +34,7 @@ constexpr int kMcWarps = kMcThreads / 32;
 constexpr int kBatchMax = kMcWarps;            // one move per warp
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
 constexpr int kCorrItems = 2160;               // 120 pairs x 3 x 3 atoms x 2 sides (G = 1, water)
-constexpr int kCellMargin = 1 << 20;           // drift allowed before an escapee: 1 A on the 2^20 grid
-constexpr int kEscMax = 256;                   // escapee list capacity per CTA
+constexpr int kEscMax = 256;                   // escapee list capacity per CTA (at most)
 constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
 static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
 
@@ -183,7 +182,7 @@ __device__ __forceinline__ int floordiv32(int a, int b)   // b > 0
 // holds ceil(k L / 8) <= x < ceil((k + 1) L / 8)) as the sweep starts, so the partners
 // inside a cube around a moved molecule lie in the slice ranges of the few cells the cube
 // meets. Atoms move during the sweep: a partner that leaves its home cell widened by
-// kCellMargin is an escapee; it keeps its slot (flagged in bit 31 of .w) and joins a
+// the cell margin is an escapee; it keeps its slot (flagged in bit 31 of .w) and joins a
 // per-CTA list that every cell query scans in full. Cell queries cover the cube widened by
 // the margin, so together with the escapees every partner inside the cube is found.
 
@@ -192,6 +191,7 @@ struct CellIndex {
     const int *cb;               // [9] cell boundaries ceil(j L / 8), cb[8] = L
     const unsigned short *esc;   // escapee slots
     int n_esc;
+    int margin;                  // drift (grid units) allowed before an atom becomes an escapee
     bool on;                     // cell queries allowed (escapee list not overflowed)
 };
 
@@ -229,13 +229,13 @@ __device__ __forceinline__ unsigned cell_code(int cx, int cy, int cz)
     return spread3((unsigned)cx) | (spread3((unsigned)cy) << 1) | (spread3((unsigned)cz) << 2);
 }
 
-// Is grid point x (one axis) within kCellMargin of cell k's interval (cyclically)?
-__device__ __forceinline__ bool near_cell(int x, int k, const int *cb, int L)
+// Is grid point x (one axis) within `margin` of cell k's interval (cyclically)?
+__device__ __forceinline__ bool near_cell(int x, int k, const int *cb, int L, int margin)
 {
-    long long d = (long long)x - (cb[k] - kCellMargin);
+    long long d = (long long)x - ((long long)cb[k] - margin);
     if (d < 0) d += L;
     if (d >= L) d -= L;
-    return d < (long long)(cb[k + 1] - cb[k]) + 2LL * kCellMargin;
+    return d < (long long)(cb[k + 1] - cb[k]) + 2LL * margin;
 }
 
 // Out-of-line copy of pair_du for code that runs once per batch (keeps the kernel small).
@@ -268,7 +268,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
     }
     int k0x = 0, nx = 8, k0y = 0, ny = 8, k0z = 0, nz = 8;
     if (CELLS && ci.on) {
-        const long long w = (long long)hw + kCellMargin;
+        const long long w = (long long)hw + ci.margin;
         cell_run(o0.x, w, L, ci.cb, k0x, nx);
         cell_run(o0.y, w, L, ci.cb, k0y, ny);
         cell_run(o0.z, w, L, ci.cb, k0z, nz);
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 near_rows |= r.c12 == 0.f && r.c6 == 0.f && (r.kqq != 0.f || bx.has_ep);
             }
         sh.n_esc = 0;
-        sh.cells_on = near_rows ? 1 : 0;
+        sh.cells_on = near_rows && A.esc_cap > 0 ? 1 : 0;
     }
     __syncthreads();
     for (int t = 0; t < nt; ++t) {
@@ -644,7 +644,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             ci.cst = cst;
             ci.cb = sh.cb;
             ci.esc = sh.esc;
-            ci.n_esc = min(sh.n_esc, kEscMax);
+            ci.n_esc = min(sh.n_esc, A.esc_cap);
+            ci.margin = A.cell_margin;
             ci.on = sh.cells_on != 0;
             if (m == 1)
                 acc = ci.on ? partner_sum<1, true>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
@@ -766,12 +767,12 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     bool esc = slice[slot].w < 0;
                     if (!esc) {
                         const unsigned h = home[slot];
-                        esc = !(near_cell(p.x, (int)compact3(h), sh.cb, L) &&
-                                near_cell(p.y, (int)compact3(h >> 1), sh.cb, L) &&
-                                near_cell(p.z, (int)compact3(h >> 2), sh.cb, L));
+                        esc = !(near_cell(p.x, (int)compact3(h), sh.cb, L, A.cell_margin) &&
+                                near_cell(p.y, (int)compact3(h >> 1), sh.cb, L, A.cell_margin) &&
+                                near_cell(p.z, (int)compact3(h >> 2), sh.cb, L, A.cell_margin));
                         if (esc) {
                             const int e = atomicAdd(&sh.n_esc, 1);
-                            if (e < kEscMax) sh.esc[e] = (unsigned short)slot;
+                            if (e < A.esc_cap) sh.esc[e] = (unsigned short)slot;
                             else sh.cells_on = 0;            // too many: full scans from now on
                         }
                     }
@@ -839,6 +840,7 @@ int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stre
 }
 
 int mc_threads() { return kMcThreads; }
+int mc_escapee_max() { return kEscMax; }
 int mc_batch_max() { return kBatchMax; }
 
 }  // namespace epsr

@@ -35,6 +35,7 @@ EXPORTS = [
     "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc", "epsr_ep_update",
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
+    "epsr_mc_set_cells",
 ]
 
 
@@ -114,6 +115,7 @@ def lib():
             "epsr_gr_smeared_fwd": ([vp, dbl, vp, vp, vp], C.c_int),
             "epsr_checkpoint_size": ([vp, P(C.c_size_t)], C.c_int),
             "epsr_launch_count": ([P(C.c_uint64)], C.c_int),
+            "epsr_mc_set_cells": ([vp, C.c_int32, C.c_int32], C.c_int),
             "epsr_checkpoint_save": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_checkpoint_load": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_gr_smeared_bwd": ([vp, dbl, vp, vp, vp], C.c_int),
@@ -290,6 +292,9 @@ class Box:
 
     def epsr_mc_set_batch(self, k: int):
         _check(lib().epsr_mc_set_batch(self.h, k), "epsr_mc_set_batch")
+
+    def epsr_mc_set_cells(self, margin_fx: int, escapee_cap: int = -1):
+        _check(lib().epsr_mc_set_cells(self.h, margin_fx, escapee_cap), "epsr_mc_set_cells")
 
     def epsr_mc_set_ctas(self, n: int):
         _check(lib().epsr_mc_set_ctas(self.h, n), "epsr_mc_set_ctas")

@@ -74,3 +74,9 @@ def test_null_handles_are_rejected(lib):
     assert lib.epsr_box_destroy(None) == epsr.EPSR_OK
     assert lib.epsr_mc_set_batch(None, 4) == epsr.EPSR_EINVAL
     assert lib.epsr_sq_plan_destroy(None) == epsr.EPSR_OK
+    assert lib.epsr_mc_set_cells(None, 0, 0) == epsr.EPSR_EINVAL
+    assert lib.epsr_checkpoint_save(None, None, 0, None) == epsr.EPSR_EINVAL
+    assert lib.epsr_checkpoint_load(None, None, 0, None) == epsr.EPSR_EINVAL
+    assert lib.epsr_launch_count(None) == epsr.EPSR_EINVAL
+    n0 = C.c_uint64()
+    assert lib.epsr_launch_count(C.byref(n0)) == epsr.EPSR_OK

@@ -184,11 +184,17 @@ def test_mc_replay_silica_atom_moves_with_ep():
     assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
 
 
-def test_mc_replay_paper_water_sampled():
+@pytest.mark.parametrize("cells", [None, (0, 256), (0, 4), (0, 0)],
+                         ids=["default", "margin0", "escapee-overflow", "no-cells"])
+def test_mc_replay_paper_water_sampled(cells):
     """99,999-atom water on the full grid of CTAs: trial coordinates of every move
-    bit-exact, dU checked on a sample of moves, final coordinates bit-exact."""
+    bit-exact, dU checked on a sample of moves, final coordinates bit-exact. With a zero
+    cell margin every partner that leaves its cell becomes an escapee; a list of 4 overflows
+    and the CTAs fall back to full scans; capacity 0 turns cell queries off."""
     s = synth.paper_water()
     box = epsr.Box(s)
+    if cells is not None:
+        box.epsr_mc_set_cells(*cells)
     n = 4000
     stats, log = run_logged(box, n, seed=2024)
     ob, checked, worst, flips = replay(s, s.xyz, log[0], 2024, check_every=40)
