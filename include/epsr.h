@@ -343,10 +343,14 @@ int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, int64_t n_a
  *   w, flat    host double [n_cols], [n_cols / cols_per_set]
  *   S_partial  device float [n_cols][nQ] or NULL;  S_total device float [n_sets][nQ] or NULL
  * epsr_sq_plan_create synchronises; epsr_sq_exec is asynchronous and allocates nothing
- * (graph-capturable). epsr_sq is a one-shot convenience (plan, exec, free).            */
+ * (graph-capturable). epsr_sq is a one-shot convenience (plan, exec, free).
+ * Every tensor-core completion wait is bounded; one that gives up skips its tile and sets
+ * the plan's status word, which epsr_sq_plan_status reads (synchronising `stream`; status
+ * EPSR_OK or EPSR_ETIMEOUT, and the word is cleared) and epsr_sq checks before returning. */
 int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, double dr, int32_t mode,
                         int32_t max_cols, epsr_stream_t stream, epsr_sq_plan **out);
 int epsr_sq_plan_destroy(epsr_sq_plan *plan);
+int epsr_sq_plan_status(epsr_sq_plan *plan, int32_t *status, epsr_stream_t stream);
 int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, const double *w,
                  int32_t cols_per_set, const double *flat, float *S_partial, float *S_total,
                  epsr_stream_t stream);

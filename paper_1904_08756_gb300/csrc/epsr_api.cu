@@ -1041,6 +1041,20 @@ extern "C" int epsr_sq(const float *g, int32_t n_cols, int32_t n_bins, double dr
     return rc;
 }
 
+extern "C" int epsr_sq_plan_status(epsr_sq_plan *p, int32_t *status, epsr_stream_t stream)
+{
+    if (!p || !status) return set_error(EPSR_EINVAL, "NULL argument");
+    *status = EPSR_OK;
+    if (!p->tc_status) return EPSR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, p->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(p->tc_status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    *status = st ? EPSR_ETIMEOUT : EPSR_OK;
+    return EPSR_OK;
+}
+
 // ---- empirical-potential update -------------------------------------------------------------
 extern "C" int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t n_data,
                               const double *w, const float *Q, int32_t nQ, int32_t n_basis,

@@ -35,7 +35,7 @@ EXPORTS = [
     "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc", "epsr_ep_update",
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
-    "epsr_mc_set_cells",
+    "epsr_mc_set_cells", "epsr_sq_plan_status",
 ]
 
 
@@ -116,6 +116,7 @@ def lib():
             "epsr_checkpoint_size": ([vp, P(C.c_size_t)], C.c_int),
             "epsr_launch_count": ([P(C.c_uint64)], C.c_int),
             "epsr_mc_set_cells": ([vp, C.c_int32, C.c_int32], C.c_int),
+            "epsr_sq_plan_status": ([vp, P(C.c_int32), vp], C.c_int),
             "epsr_checkpoint_save": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_checkpoint_load": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_gr_smeared_bwd": ([vp, dbl, vp, vp, vp], C.c_int),
@@ -381,6 +382,11 @@ class SqPlan:
             self.close()
         except Exception:
             pass
+
+    def epsr_sq_plan_status(self, stream=None) -> int:
+        st = C.c_int32()
+        _check(lib().epsr_sq_plan_status(self.h, C.byref(st), _stream(stream)), "epsr_sq_plan_status")
+        return st.value
 
     def epsr_sq_exec(self, g, w: np.ndarray, cols_per_set: int, flat: np.ndarray,
                      S_partial=None, S_total=None, stream=None):

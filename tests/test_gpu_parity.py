@@ -488,6 +488,7 @@ def test_sq_modes_against_oracle(mode, tol, n_cols):
     err_t = np.abs(St.cpu().numpy() - St_ref).max()
     print(f"mode {mode} cols {n_cols}: max |dS_partial| {err_p:.3e}, max |dS_total| {err_t:.3e}")
     assert err_t <= tol and err_p <= tol
+    assert plan.epsr_sq_plan_status() == epsr.EPSR_OK
 
 
 def test_checkpoint_resume_is_bit_exact():
