@@ -221,7 +221,10 @@ __device__ __forceinline__ double uniform53(uint32_t a, uint32_t b)
 
 __device__ __forceinline__ int wrap_coord(long long x, int L)
 {
-    long long r = x % L;
+    if (x >= 0 && x < L) return (int)x;                  // trial coordinates land within one
+    if (x < 0 && x >= -(long long)L) return (int)(x + L); // box side of [0, L): no division
+    if (x >= L && x < 2LL * L) return (int)(x - L);
+    const long long r = x % L;
     return (int)(r < 0 ? r + L : r);
 }
 
