@@ -114,7 +114,7 @@ struct epsr_box {
     std::vector<int> type_h;
     std::vector<GrTile> tiles_h;
     int sms = 0;
-    int mc_batch = 16;
+    int mc_batch = 0;                         // 0: chosen per box by the kernel
     int cell_margin = 1 << 20;                // 1 A on the 2^20 grid
     int esc_cap = -1;                         // -1: the kernel's maximum
     int mc_ctas = 0;
@@ -645,7 +645,7 @@ extern "C" int epsr_box_total_energy(epsr_box *box, double *U_host, epsr_stream_
 // ---- Monte Carlo ------------------------------------------------------------------------------
 extern "C" int epsr_mc_set_batch(epsr_box *box, int32_t batch_k)
 {
-    if (!box || batch_k < 1 || batch_k > mc_batch_max()) return set_error(EPSR_EINVAL, "batch_k out of range");
+    if (!box || batch_k < 0 || batch_k > mc_batch_max()) return set_error(EPSR_EINVAL, "batch_k out of range");
     box->mc_batch = batch_k;
     return EPSR_OK;
 }

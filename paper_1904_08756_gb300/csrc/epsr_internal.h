@@ -20,10 +20,10 @@ int set_cuda_error(cudaError_t e, const char *what);
 void note_launch();
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
-constexpr size_t kMcMaxDynSmem = 190 * 1024;
-// per-CTA barrier slot: the batch's partial dU (16 moves), then the pair-energy corrections
-// this CTA computed (at most 16 * 15 / 2 = 120 pairs)
-constexpr int kMcSlotStride = 16 + 120;
+constexpr size_t kMcMaxDynSmem = 176 * 1024;   // with ~48 KB static: under the 227 KB per CTA
+// per-CTA barrier slot: the batch's partial dU (32 moves), then the pair-energy corrections
+// this CTA computed (at most 32 * 31 / 2 = 496 pairs)
+constexpr int kMcSlotStride = 32 + 496;
 
 struct McArgs {
     const BoxDev *boxes;

@@ -14,8 +14,8 @@
 //
 // Batching without changing the chain: moves are taken in batches of up to K
 // consecutive moves with distinct molecules (a batch ends before the first molecule that
-// repeats). Warp k computes the partial dU of move k against the slice as it stood at
-// the start of the batch. One grid barrier per batch gathers the per-CTA partials; every
+// repeats; K <= 32). Warp w computes the partial dU of moves w and w + 16 against the
+// slice as it stood at the start of the batch. One grid barrier per batch gathers the per-CTA partials; every
 // CTA sums them in the same fixed order and resolves the batch in order: move k's dU is
 // its batch-start value plus, for every earlier accepted move k' of the batch, the exact
 // change of the pair energies between the two moved molecules,
@@ -31,9 +31,9 @@ namespace epsr {
 
 constexpr int kMcThreads = 512;
 constexpr int kMcWarps = kMcThreads / 32;
-constexpr int kBatchMax = kMcWarps;            // one move per warp
+constexpr int kBatchMax = 32;                  // moves per batch: warp w takes moves w and w + 16
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
-constexpr int kCorrItems = 2160;               // 120 pairs x 3 x 3 atoms x 2 sides (G = 1, water)
+constexpr int kCorrItems = 4096;               // >= 496 pairs x 8 atoms (coarse items at G = 1)
 constexpr int kEscMax = 256;                   // escapee list capacity per CTA (at most)
 constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
 static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
@@ -491,13 +491,16 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     }
     __syncthreads();
 
+    // moves per batch: as set, else 32 for large CTA groups (the per-batch phases amortise
+    // over more moves) and 16 for small ones (corrections grow with the square of the batch)
+    const int batch_k = A.batch_k > 0 ? A.batch_k : (G >= 32 ? kBatchMax : kBatchMax / 2);
     const MoveRec *moves = A.moves + (size_t)box * A.chunk;
     unsigned seq = 0;
     int par = 0;
 
     long long mv_base = 0, mv_end = 0;
     for (long long t0 = 0; t0 < A.n_moves; par ^= 1) {
-        const int kmax = (int)min((long long)A.batch_k, A.n_moves - t0);
+        const int kmax = (int)min((long long)batch_k, A.n_moves - t0);
         if (t0 + kmax > mv_end) {           // stage the next block of move records
             if (rank == 0 && warp == 0) block_sum_du(sh.acc_du, (int)(t0 - mv_base), lane, sh.st_sum);
             mv_base = t0;
@@ -527,8 +530,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         __syncthreads();
         const int nb = sh.nb[par];
         // ---- B. current and trial coordinates of each moved molecule (integer arithmetic) ----
-        if (warp < nb) {
-            const int k = warp;
+        for (int k = warp; k < nb; k += kMcWarps) {
             const MoveRec &mr = sh.mv[t0 + k - mv_base];
             const int mol = sh.mol[par][k];
             const int a0 = mr.a0, m = mr.m;
@@ -637,8 +639,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         }
         const bool fine = n_items <= kCorrItems;
         // ---- C. partial dU of move `warp` against this CTA's slice ---------------------------
-        if (warp < nb) {
-            const int m = sh.natoms[warp];
+        for (int k = warp; k < nb; k += kMcWarps) {
+            const int m = sh.natoms[k];
             float acc;
             CellIndex ci;
             ci.cst = cst;
@@ -648,20 +650,20 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             ci.margin = A.cell_margin;
             ci.on = sh.cells_on != 0;
             if (m == 1)
-                acc = ci.on ? partner_sum<1, true>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
+                acc = ci.on ? partner_sum<1, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
                                                    slice, sh.blk, ci, bx, T, ep, lane)
-                            : partner_sum<1, false>(sh.newp[par][warp], sh.oldp[warp], 1, sh.a0[warp], sh.hw[warp],
+                            : partner_sum<1, false>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
                                                     slice, sh.blk, ci, bx, T, ep, lane);
             else if (m <= 3)
-                acc = ci.on ? partner_sum<3, true>(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                acc = ci.on ? partner_sum<3, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                                    slice, sh.blk, ci, bx, T, ep, lane)
-                            : partner_sum<3, false>(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                            : partner_sum<3, false>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                                     slice, sh.blk, ci, bx, T, ep, lane);
             else
-                acc = partner_sum_any(sh.newp[par][warp], sh.oldp[warp], m, sh.a0[warp], sh.hw[warp],
+                acc = partner_sum_any(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                       slice, sh.blk, bx, T, ep, lane);
             acc = warp_sum(acc);
-            if (lane == 0) sh.part[warp] = acc;
+            if (lane == 0) sh.part[k] = acc;
         }
         __syncthreads();
         // ---- D. gather the partials of the box's CTA group (one bounded grid barrier) -------
@@ -698,11 +700,11 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             __syncthreads();
             if (sh.abort_flag) return;
             const float *bs = A.slots + (size_t)(seq & 1u) * A.grid * kMcSlotStride;
-            if (warp < nb) {
+            for (int k = warp; k < nb; k += kMcWarps) {
                 float v = 0.f;
-                for (int r = lane; r < G; r += 32) v += __ldcg(&bs[(size_t)(bx.cta0 + r) * kMcSlotStride + warp]);
+                for (int r = lane; r < G; r += 32) v += __ldcg(&bs[(size_t)(bx.cta0 + r) * kMcSlotStride + k]);
                 v = warp_sum(v);
-                if (lane == 0) sh.base[warp] = v;
+                if (lane == 0) sh.base[k] = v;
             }
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 int k = 1;
@@ -711,7 +713,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     __ldcg(&bs[(size_t)(bx.cta0 + pq % G) * kMcSlotStride + kBatchMax + pq / G]);
             }
         } else {
-            if (tid < nb) sh.base[tid] = sh.part[tid];
+            for (int k = tid; k < nb; k += kMcThreads) sh.base[k] = sh.part[k];
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 int k = 1;
                 while ((k + 1) * k / 2 <= pq) ++k;

@@ -149,7 +149,7 @@ def replay(system, start_xyz, log, seed, move0=0, box_index=0, check_every=1, ep
     return ob, checked, worst, flips
 
 
-@pytest.mark.parametrize("batch", [16, 5, 1])
+@pytest.mark.parametrize("batch", [32, 16, 5, 1])
 def test_mc_replay_small_water(small_water, batch):
     box = epsr.Box(small_water)
     box.epsr_mc_set_batch(batch)
