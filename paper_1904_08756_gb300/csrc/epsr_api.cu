@@ -822,7 +822,7 @@ static int gr_range(epsr_box *box, long long t0, long long t1, uint64_t *hist, c
     a.hist = (unsigned long long *)hist;
     a.max_pairs_bins = box->ep_cap;
     a.max_bins1 = box->tbl_cap;
-    const int grid = (int)std::min<long long>(t1 - t0, (long long)box->sms * 2);
+    const int grid = (int)std::min<long long>(t1 - t0, (long long)box->sms * 4);   // 4 CTAs per SM
     return launch_partial_gr(a, std::max(grid, 1), s);
 }
 

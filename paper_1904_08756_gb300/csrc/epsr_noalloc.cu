@@ -198,5 +198,5 @@ extern "C" int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, 
     a.hist = (unsigned long long *)hist;
     a.max_pairs_bins = n_pairs * n_bins;
     a.max_bins1 = n_bins + 1;
-    return launch_partial_gr(a, (int)std::max<long long>(1, std::min<long long>(a.tile_end, 2LL * sms)), s);
+    return launch_partial_gr(a, (int)std::max<long long>(1, std::min<long long>(a.tile_end, 4LL * sms)), s);
 }

@@ -9,8 +9,9 @@
 // Prefilter: a second copy of the coordinates is scaled so that the box side maps to
 // 2^32 (x' = floor(x 2^32 / L)). Differences then wrap modulo 2^32 exactly as minimum
 // images wrap modulo L, and |min-image dx| <= R implies |x'_i - x'_j| < R' with
-// R' = ceil(R 2^32 / L) + 2. The test per axis is one add and one unsigned compare:
-// (x'_i + R') - x'_j < 2 R'. Pairs that pass take the exact path: integer minimum
+// R' = ceil(R 2^32 / L) + 2. The test is one subtraction per axis and one unsigned compare
+// of their three-way maximum: max((x'_i + R') - x'_j, ...) < 2 R'; the four i-atoms of a
+// thread are tested against one j before a single branch on the combined hit mask. Pairs that pass take the exact path: integer minimum
 // image on the true grid coordinates, exact 64-bit squared distance, bin from the
 // threshold table. Counts go to a per-CTA shared-memory histogram (32-bit) and are
 // flushed to the caller's 64-bit histogram with one atomic per non-empty bin.
@@ -245,7 +246,7 @@ __device__ __forceinline__ void flush_hist(unsigned *sh_hist, int n, unsigned lo
     }
 }
 
-__global__ void __launch_bounds__(kGrThreads, 2) partial_gr_kernel(GrArgs A)
+__global__ void __launch_bounds__(kGrThreads, 4) partial_gr_kernel(GrArgs A)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     uint4 *s_scaled = reinterpret_cast<uint4 *>(dyn);
@@ -312,10 +313,16 @@ __global__ void __launch_bounds__(kGrThreads, 2) partial_gr_kernel(GrArgs A)
         __syncthreads();
         for (int j = 0; j < nj; ++j) {
             const uint4 sj = s_scaled[j];
+            unsigned mask = 0u;
 #pragma unroll
             for (int r = 0; r < kGrR; ++r) {
-                const bool hit = (xi[r] - sj.x < R2) & (yi[r] - sj.y < R2) & (zi[r] - sj.z < R2);
-                if (hit) {
+                const bool hit = __vimax3_u32(xi[r] - sj.x, yi[r] - sj.y, zi[r] - sj.z) < R2;
+                mask |= hit ? 1u << r : 0u;
+            }
+            if (mask == 0u) continue;
+#pragma unroll
+            for (int r = 0; r < kGrR; ++r) {
+                if ((mask >> r) & 1u) {
                     if (il[r] < 0 || (diag && j <= il[r])) continue;
                     const int4 pi = A.coords[bx.atom0 + i0 + il[r]];
                     const int4 pj = s_true[j];
