@@ -207,6 +207,71 @@ def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
     return out
 
 
+# the paper's Table 1: simulation speed of its GPU code (V100), steps/s, by atom count
+PAPER_TABLE1_GPU = {3000: 1562.0, 30000: 9507.0, 100000: 12412.0, 250000: 10189.0,
+                    1200000: 3917.0, 3000000: 1963.0, 10000000: 757.0, 30000000: 340.3}
+
+
+def run_sweep(args):
+    """Monte Carlo moves/s of rigid water at the atom counts of the paper's Table 1 (3e3 to
+    3e7 atoms, lattice-placed boxes at 0.1 atoms/A^3), each timed over about half a second of
+    sweeps after a warm-up; boxes whose partner slices exceed shared memory run the
+    global-memory variant of the sweep."""
+    import torch
+    from paper_1904_08756_gb300 import build, epsr, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if not os.path.exists(epsr.LIB_PATH):
+        build.build()
+    sizes = sorted(PAPER_TABLE1_GPU)
+    if args.max_atoms:
+        sizes = [n for n in sizes if n <= args.max_atoms]
+    rows = []
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with ClockSampler(0) as clk:
+        for n_atoms in sizes:
+            s = synth.water_lattice(n_atoms // 3, seed=11)
+            box = epsr.Box(s)
+            move0 = 0
+            t0 = time.perf_counter()
+            box.epsr_mc_sweep(512, 5, move0)
+            move0 += 512
+            est = 512 / max(time.perf_counter() - t0, 1e-6)
+            n_timed = int(min(200000, max(1024, 0.5 * est)))
+            for _ in range(args.warmup):
+                box.epsr_mc_sweep(256, 5, move0)
+                move0 += 256
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            stats = box.epsr_mc_sweep(n_timed, 5, move0)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            mps = n_timed / (ms * 1e-3)
+            rows.append({"atoms": s.n_atoms, "moves": n_timed, "ms": ms, "moves_per_s": mps,
+                         "pair_evals_per_s": mps * 6 * (s.n_atoms - 3),
+                         "acceptance": stats[0][1] / max(1, stats[0][0]),
+                         "paper_v100_steps_per_s": PAPER_TABLE1_GPU[n_atoms],
+                         "ratio_to_paper": mps / PAPER_TABLE1_GPU[n_atoms]})
+            box.close()
+            del s
+    ref = next((r for r in rows if r["atoms"] == 99999), rows[-1])
+    line = {"metric": METRIC + " (atom-count sweep, MC only)", "value": ref["moves_per_s"],
+            "unit": "moves/s", "n_gpus": 1, "steps": len(rows), "warmup": args.warmup,
+            "ms_per_step": ref["ms"], "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "fp32+int64", "data": "synthetic",
+            "config": {"workload": "rigid 3-site water on a simple cubic lattice of molecules, "
+                                   "0.1 atoms/A^3, at the atom counts of the paper's Table 1; "
+                                   "value = the 99,999-atom box",
+                       "l2": "flushed before each timed sweep"},
+            "sweep": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_replicas(args):
     import torch
     from paper_1904_08756_gb300 import build, epsr, synth
@@ -288,9 +353,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water", choices=["water", "silica", "replicas"],
+    ap.add_argument("--workload", default="water", choices=["water", "silica", "replicas", "sweep"],
                     help="water: the paper-scale water box (default line); silica: the paper-scale "
-                         "SiO2 box with single-atom moves; replicas: 64 uneven boxes")
+                         "SiO2 box with single-atom moves; replicas: 64 uneven boxes; sweep: MC "
+                         "moves/s at the paper's Table 1 atom counts")
+    ap.add_argument("--max-atoms", type=int, default=0, help="sweep: largest atom count (0: all)")
     ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
                     help="moves per step (profiling runs only; the benchmark uses 10,000)")
     args = ap.parse_args()
@@ -300,6 +367,8 @@ def main():
         return run_reference(args)
     if args.workload == "replicas":
         return run_replicas(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
 
     import torch
     from paper_1904_08756_gb300 import build, epsr, shard, synth

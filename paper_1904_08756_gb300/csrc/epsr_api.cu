@@ -156,6 +156,10 @@ struct epsr_box {
     long long ep_cap_Q = 0;
     float *lambda = nullptr;     // adjoint of the smeared normalisation [hist_len]
     unsigned long long *smear_acc = nullptr;   // fixed-point smeared counts [hist_len]
+    // partner slices in global memory, for boxes whose slices do not fit in shared memory
+    int4 *slice_g = nullptr;
+    unsigned short *home_g = nullptr;
+    size_t slice_g_cap = 0;
 
     ~epsr_box()
     {
@@ -164,7 +168,7 @@ struct epsr_box {
                         sort.count, sort.offset, sort.block, sort.key, sort.rank, sort.index,
                         sorted_scaled, sorted_coords, moves, mc_sort.count, mc_sort.offset,
                         mc_sort.block, mc_sort.key, mc_sort.rank, mc_sort.index, pos_of,
-                        ep_F, ep_Y, ep_C, ep_Q, lambda, smear_acc};
+                        ep_F, ep_Y, ep_C, ep_Q, lambda, smear_acc, slice_g, home_g};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -699,14 +703,31 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
     int types_cap = 1;
     for (auto &b : box->hb) types_cap = std::max(types_cap, b.n_types);
-    // slice, thresholds, EP table, cell index [types][513] and home cell per slot (uint16)
-    size_t smem = (size_t)slice_cap * sizeof(int4) + (size_t)box->tbl_cap * sizeof(long long) +
-                  (size_t)box->ep_cap * sizeof(float) +
-                  ((size_t)types_cap * (kMcCells + 1) + (size_t)slice_cap) * sizeof(unsigned short);
-    smem = (smem + 15) & ~(size_t)15;
-    if (smem > kMcMaxDynSmem)
-        return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of shared memory per CTA needed (limit %zu); "
-                         "give the sweep more CTAs", smem, kMcMaxDynSmem);
+    // shared memory: thresholds, EP table, cell index [types][513] (uint32), and, when they
+    // fit, the partner slice (int4 per slot) and the home cell of every slot (uint16);
+    // otherwise the slices and home cells live in global memory
+    const size_t tables = (size_t)box->tbl_cap * sizeof(long long) + (size_t)box->ep_cap * sizeof(float) +
+                          (size_t)types_cap * (kMcCells + 1) * sizeof(unsigned);
+    const size_t per_slot = sizeof(int4) + sizeof(unsigned short);
+    size_t smem = (((size_t)slice_cap * per_slot + tables) + 15) & ~(size_t)15;
+    const bool gslice = smem > kMcMaxDynSmem;
+    if (gslice) {
+        smem = (tables + 15) & ~(size_t)15;
+        if (smem > kMcMaxDynSmem)
+            return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of tables per CTA (limit %zu)", smem, kMcMaxDynSmem);
+        const size_t slots = (size_t)box->cta_box_len * slice_cap;
+        if (box->slice_g_cap < slots) {
+            if (box->slice_g) cudaFree(box->slice_g);
+            if (box->home_g) cudaFree(box->home_g);
+            box->slice_g = nullptr;
+            box->home_g = nullptr;
+            box->slice_g_cap = 0;
+            int rc = dalloc(&box->slice_g, slots);
+            if (!rc) rc = dalloc(&box->home_g, slots);
+            if (rc) return rc;
+            box->slice_g_cap = slots;
+        }
+    }
     // moves per launch: the table (allocated at creation) holds at most 2^22 moves over all boxes
     const long long chunk = std::min<long long>(n_moves, box->moves_cap / box->n_boxes);
     // type-major spatial partition of the partners for this sweep
@@ -742,6 +763,8 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     a.tbl_cap = box->tbl_cap;
     a.ep_cap = box->ep_cap;
     a.types_cap = types_cap;
+    a.slice_g = gslice ? box->slice_g : nullptr;
+    a.home_g = gslice ? box->home_g : nullptr;
     a.cell_margin = box->cell_margin;
     a.esc_cap = box->esc_cap < 0 ? mc_escapee_max() : box->esc_cap;
     a.skip_arrival_cta = box->fault_cta;

@@ -54,6 +54,8 @@ struct McArgs {
     int tbl_cap;                  // capacity (entries) of the shared threshold table
     int ep_cap;                   // capacity (entries) of the shared empirical-potential table
     int types_cap;                // largest number of atom types of the handle's boxes
+    int4 *slice_g;                // [grid][slice_cap] partner slices in global memory, or NULL
+    unsigned short *home_g;       // [grid][slice_cap] home cells of those slots, or NULL
     int cell_margin;              // drift (grid units) before a partner leaves its cell's queries
     int esc_cap;                  // escapee list capacity (0: no cell queries)
     int skip_arrival_cta;         // test hook: this CTA never arrives (-1: none)

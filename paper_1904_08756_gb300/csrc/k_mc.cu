@@ -127,7 +127,7 @@ struct McShared {
     int abort_flag;
     int cb[9];                               // cell boundaries ceil(j L / 8)
     int n_esc, cells_on;
-    unsigned short esc[kEscMax];             // escapee slots
+    int esc[kEscMax];                        // escapee slots
     // leader-only running statistics
     long long st_att, st_acc, st_nonfinite;
     double st_sum;
@@ -187,9 +187,9 @@ __device__ __forceinline__ int floordiv32(int a, int b)   // b > 0
 // the margin, so together with the escapees every partner inside the cube is found.
 
 struct CellIndex {
-    const unsigned short *cst;   // [n_types][kMcCells + 1] first slot of each cell, relative to blk[t]
+    const unsigned *cst;         // [n_types][kMcCells + 1] first slot of each cell, relative to blk[t]
     const int *cb;               // [9] cell boundaries ceil(j L / 8), cb[8] = L
-    const unsigned short *esc;   // escapee slots
+    const int *esc;              // escapee slots
     int n_esc;
     int margin;                  // drift (grid units) allowed before an atom becomes an escapee
     bool on;                     // cell queries allowed (escapee list not overflowed)
@@ -308,7 +308,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
         }
         if (CELLS && cells) {
             cell_types |= 1u << t;
-            const unsigned short *cst = ci.cst + t * (kMcCells + 1);
+            const unsigned *cst = ci.cst + t * (kMcCells + 1);
             int first = 0, cnt = 0;
             if (lane < ncell) {
                 const int ix = lane % nx, iy = (lane / nx) % ny, iz = lane / (nx * ny);
@@ -403,6 +403,10 @@ __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, in
     return acc;
 }
 
+// GSLICE: the partner slices live in global memory ([grid][slice_cap], read through L1/L2)
+// because they do not fit in shared memory; the thresholds, EP table and cell index stay
+// in shared memory either way.
+template <bool GSLICE>
 __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -445,8 +449,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     const int n_slice = sh.blk[nt];
 
     // shared memory: partner slice {x, y, z, type | atom << 3}, thresholds, empirical potential
-    int4 *slice = reinterpret_cast<int4 *>(dyn);
-    long long *T = reinterpret_cast<long long *>(slice + A.slice_cap);
+    int4 *slice = GSLICE ? A.slice_g + (size_t)cta * A.slice_cap : reinterpret_cast<int4 *>(dyn);
+    long long *T = GSLICE ? reinterpret_cast<long long *>(dyn) : reinterpret_cast<long long *>(slice + A.slice_cap);
     float *ep = reinterpret_cast<float *>(T + A.tbl_cap);
     for (int t = 0; t < nt; ++t)
         for (int i = tid; i < sh.rl[t]; i += kMcThreads) {
@@ -461,12 +465,13 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     // cell index: first slot of each cell per type (relative to the type's block), the
     // home cell of every slot, cell boundaries; cell queries only where some pair row has
     // no Lennard-Jones term but a Coulomb or empirical-potential one
-    unsigned short *cst = reinterpret_cast<unsigned short *>(ep + A.ep_cap);
-    unsigned short *home = cst + A.types_cap * (kMcCells + 1);
+    unsigned *cst = reinterpret_cast<unsigned *>(ep + A.ep_cap);
+    unsigned short *home = GSLICE ? A.home_g + (size_t)cta * A.slice_cap
+                                  : reinterpret_cast<unsigned short *>(cst + A.types_cap * (kMcCells + 1));
     for (int t = 0; t < nt; ++t) {
         const int key0 = bx.mc_cell0 + (t * G + rank) * kMcCells;
         for (int c = tid; c <= kMcCells; c += kMcThreads)
-            cst[t * (kMcCells + 1) + c] = (unsigned short)(A.mc_offset[key0 + c] - A.mc_offset[key0]);
+            cst[t * (kMcCells + 1) + c] = (unsigned)(A.mc_offset[key0 + c] - A.mc_offset[key0]);
     }
     if (tid <= 8) sh.cb[tid] = (int)(((long long)tid * L + 7) / 8);
     if (tid == 0) {
@@ -481,11 +486,11 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     }
     __syncthreads();
     for (int t = 0; t < nt; ++t) {
-        const unsigned short *ct = cst + t * (kMcCells + 1);
+        const unsigned *ct = cst + t * (kMcCells + 1);
         for (int i = tid; i < sh.rl[t]; i += kMcThreads) {
             int c = 0;                                   // last cell starting at or before i
             for (int step = kMcCells / 2; step > 0; step >>= 1)
-                if (ct[c + step] <= i) c += step;
+                if (ct[c + step] <= (unsigned)i) c += step;
             home[sh.blk[t] + i] = (unsigned short)c;
         }
     }
@@ -774,7 +779,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                                 near_cell(p.z, (int)compact3(h >> 2), sh.cb, L, A.cell_margin));
                         if (esc) {
                             const int e = atomicAdd(&sh.n_esc, 1);
-                            if (e < A.esc_cap) sh.esc[e] = (unsigned short)slot;
+                            if (e < A.esc_cap) sh.esc[e] = slot;
                             else sh.cells_on = 0;            // too many: full scans from now on
                         }
                     }
@@ -814,15 +819,17 @@ int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stre
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(mc_sweep_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(mc_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMcMaxDynSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mc_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kMcMaxDynSmem);
         if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(mc)");
         attr_set = true;
     }
+    const void *fn = args.slice_g ? (const void *)mc_sweep_kernel<true> : (const void *)mc_sweep_kernel<false>;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_sweep_kernel,
-                                                                  kMcThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMcThreads, smem);
     if (e != cudaSuccess) return set_cuda_error(e, "occupancy(mc)");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -832,8 +839,7 @@ int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stre
                          grid, per_sm, sms);
     McArgs a = args;
     void *params[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void *)mc_sweep_kernel, dim3(grid), dim3(kMcThreads),
-                                    params, smem, stream);
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kMcThreads), params, smem, stream);
     if (e == cudaErrorCooperativeLaunchTooLarge)
         return set_error(EPSR_ELAUNCH, "mc sweep: cooperative launch of %d CTAs refused", grid);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaLaunchCooperativeKernel(mc)");

@@ -264,6 +264,41 @@ def water_box(n_mol: int, seed: int, L_A: float | None = None, density: float = 
                   seed=seed)
 
 
+def water_lattice(n_mol: int, seed: int, density: float = 0.1) -> System:
+    """Rigid 3-site water for large boxes: O atoms on the first n_mol sites of a simple cubic
+    lattice of side k = ceil(n_mol^(1/3)) in the box of the given density, each molecule in
+    a random orientation. Same potentials, moves and bins as water_box.
+
+    With O on the sites, two molecules' atoms are at least (spacing - 2 A) apart, so the
+    intermolecular bounds of water_box (O-O >= 2.3 A, any pair >= 1.0 A) hold whenever the
+    spacing is at least 3 A, without rejection; the generator refuses smaller spacings. It
+    builds 10^7 molecules in seconds, where random sequential addition would take hours.
+    """
+    n_atoms = 3 * n_mol
+    L_fx = box_side_fx(n_atoms, density)
+    k = 1
+    while k * k * k < n_mol:
+        k += 1
+    spacing_fx = L_fx // k
+    if spacing_fx < 3 * SCALE:
+        raise ValueError(f"lattice spacing {spacing_fx / SCALE:.3f} A below 3 A for {n_mol} molecules")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.arange(n_mol, dtype=np.int64)
+    sites = np.stack([idx % k, (idx // k) % k, idx // (k * k)], axis=1) * spacing_fx
+    xyz = np.empty((n_atoms, 3), np.int64)
+    geom = water_geometry_A()
+    chunk = 1 << 20
+    for c0 in range(0, n_mol, chunk):
+        c1 = min(n_mol, c0 + chunk)
+        qt = _rand_quat(rng, c1 - c0)
+        off = np.rint(_rotate(qt, np.broadcast_to(geom, (c1 - c0,) + geom.shape)) * SCALE).astype(np.int64)
+        xyz[3 * c0:3 * c1] = ((sites[c0:c1, None, :] + off) % L_fx).reshape(-1, 3)
+    base = water_box(1, seed=0, L_A=L_fx / SCALE)
+    return System(**{**base.__dict__, "L_fx": L_fx, "xyz": xyz.astype(np.int32),
+                     "type": np.tile(np.array([0, 1, 1], np.int32), n_mol),
+                     "mol_start": np.arange(0, n_atoms + 1, 3, dtype=np.int64), "seed": seed})
+
+
 def silica_box(n_si: int, seed: int, density: float = 0.0662, n_bins: int = 600,
                bin_p: int = 2, bin_q: int = 100, Q: np.ndarray | None = None) -> System:
     """Amorphous SiO2 as single atoms: RSA with 1.5 A minimum separation.

@@ -202,6 +202,27 @@ def test_mc_replay_paper_water_sampled(cells):
     assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
 
 
+def test_mc_replay_global_memory_slices():
+    """Slices too large for shared memory (8 CTAs for 99,999 atoms) run the global-memory
+    variant of the sweep: same bit-exact trial coordinates and final state."""
+    s = synth.paper_water()
+    box = epsr.Box(s)
+    box.epsr_mc_set_ctas(8)
+    stats, log = run_logged(box, 1500, seed=31)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 31, check_every=30)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
+def test_mc_replay_lattice_1_5m_atoms():
+    """1.5 million atoms (lattice water) on the full grid: global-memory slices, cell
+    queries over 8^3 cells of 59 A."""
+    s = synth.water_lattice(500_000, seed=12)
+    box = epsr.Box(s)
+    stats, log = run_logged(box, 1000, seed=32)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 32, check_every=50)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
 def test_mc_batched_replicas_replay():
     systems = [synth.water_box(400, seed=61), synth.silica_box(500, seed=62),
                synth.water_box(900, seed=63, n_bins=600, bin_p=2, bin_q=100)]
