@@ -249,6 +249,14 @@ int epsr_checkpoint_load(epsr_box *box, const void *buf, size_t len, epsr_stream
  * Asynchronous. Errors: EINVAL, ECUDA.                                                 */
 int epsr_partial_gr(epsr_box *box, uint64_t *hist, float *g, int64_t n_configs,
                     epsr_stream_t stream);
+/* The same histogram counted over cell lists: cells at least the histogram range wide
+ * (at least 3 per side), each pair counted from its home cell against itself and the 13
+ * forward neighbour cells, so the work is O(N * rho * r_max^3) instead of O(N^2) while
+ * the integer counts are identical to epsr_partial_gr's. Boxes with fewer than three cells
+ * per side are counted with the all-pairs kernel. Same arguments, accumulation and errors
+ * as epsr_partial_gr. No counterpart in the paper, whose kernel is the O(N^2) scan. */
+int epsr_partial_gr_cells(epsr_box *box, uint64_t *hist, float *g, int64_t n_configs,
+                          epsr_stream_t stream);
 /* The same over a sub-range [pair_begin, pair_end) of the handle's pair-tile work list
  * (for splitting one evaluation across devices or calls; the union of disjoint ranges
  * covering [0, n_tiles) equals one full call). epsr_partial_gr_tiles reports n_tiles. */

@@ -156,6 +156,14 @@ struct epsr_box {
     long long ep_cap_Q = 0;
     float *lambda = nullptr;     // adjoint of the smeared normalisation [hist_len]
     unsigned long long *smear_acc = nullptr;   // fixed-point smeared counts [hist_len]
+    // cell-list histogram: keys, items, per-box tile ranges of the all-pairs list (fallback)
+    int total_gcells = 0;
+    std::vector<GcItem> gc_items_h;
+    GcItem *gc_items = nullptr;
+    int *gc_count = nullptr, *gc_offset = nullptr, *gc_block = nullptr;
+    uint4 *gc_scaled = nullptr;
+    int4 *gc_coords = nullptr;
+    std::vector<long long> tile_lo, tile_hi;
     // partner slices in global memory, for boxes whose slices do not fit in shared memory
     int4 *slice_g = nullptr;
     unsigned short *home_g = nullptr;
@@ -168,7 +176,8 @@ struct epsr_box {
                         sort.count, sort.offset, sort.block, sort.key, sort.rank, sort.index,
                         sorted_scaled, sorted_coords, moves, mc_sort.count, mc_sort.offset,
                         mc_sort.block, mc_sort.key, mc_sort.rank, mc_sort.index, pos_of,
-                        ep_F, ep_Y, ep_C, ep_Q, lambda, smear_acc, slice_g, home_g};
+                        ep_F, ep_Y, ep_C, ep_Q, lambda, smear_acc, slice_g, home_g,
+                        gc_items, gc_count, gc_offset, gc_block, gc_scaled, gc_coords};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -424,12 +433,23 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
         const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
         bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
+        // cell-list histogram: cells at least the histogram range plus two grid units wide
+        const long long rcut = (long long)std::ceil(std::sqrt((double)bx.tmax)) + 2;
+        long long side = 1;                       // more cells than atoms gain nothing
+        while (side * side * side < bx.n_atoms) ++side;
+        const long long gn = std::min<long long>(std::min<long long>(bx.L / rcut, side), 512);
+        bx.gc_n = gn >= 3 ? (int)gn : 0;
+        bx.gc0 = h->total_gcells;
+        h->total_gcells += bx.gc_n ? bx.gc_n * bx.gc_n * bx.gc_n : 1;
+        for (int c = 0; c < bx.gc_n * bx.gc_n * bx.gc_n; ++c) h->gc_items_h.push_back(GcItem{b, c});
     }
     // g(r) work list: upper triangle of tile pairs per box
     for (int b = 0; b < n_boxes; ++b) {
         const int nt = (h->hb[b].n_atoms + kGrTile - 1) / kGrTile;
+        h->tile_lo.push_back((long long)h->tiles_h.size());
         for (int i = 0; i < nt; ++i)
             for (int j = i; j < nt; ++j) h->tiles_h.push_back(GrTile{b, i, j, 0});
+        h->tile_hi.push_back((long long)h->tiles_h.size());
     }
     // per-atom arrays
     std::vector<int4> c4(atom0);
@@ -463,7 +483,12 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         (rc = dalloc(&h->sorted_scaled, atom0)) || (rc = dalloc(&h->sorted_coords, atom0)) ||
         (rc = dalloc(&h->mc_sort.key, atom0)) || (rc = dalloc(&h->mc_sort.rank, atom0)) ||
         (rc = dalloc(&h->mc_sort.index, atom0)) || (rc = dalloc(&h->pos_of, atom0)) ||
-        (rc = dalloc(&h->lambda, (size_t)hist0)) || (rc = dalloc(&h->smear_acc, (size_t)hist0))) {
+        (rc = dalloc(&h->lambda, (size_t)hist0)) || (rc = dalloc(&h->smear_acc, (size_t)hist0)) ||
+        (rc = dalloc(&h->gc_items, std::max<size_t>(1, h->gc_items_h.size()))) ||
+        (rc = dalloc(&h->gc_count, (size_t)h->total_gcells + 1)) ||
+        (rc = dalloc(&h->gc_offset, (size_t)h->total_gcells + 1)) ||
+        (rc = dalloc(&h->gc_block, ((size_t)h->total_gcells + 1 + 1023) / 1024)) ||
+        (rc = dalloc(&h->gc_scaled, atom0)) || (rc = dalloc(&h->gc_coords, atom0))) {
         delete h;
         return rc;
     }
@@ -479,6 +504,8 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
     CKD(cudaMemcpyAsync(h->thresholds, T.data(), T.size() * sizeof(long long), cudaMemcpyHostToDevice, stream));
     CKD(cudaMemsetAsync(h->ep, 0, (size_t)std::max(ep0, 1) * sizeof(float), stream));
     CKD(cudaMemcpyAsync(h->tiles, h->tiles_h.data(), h->tiles_h.size() * sizeof(GrTile), cudaMemcpyHostToDevice, stream));
+    if (!h->gc_items_h.empty())
+        CKD(cudaMemcpyAsync(h->gc_items, h->gc_items_h.data(), h->gc_items_h.size() * sizeof(GcItem), cudaMemcpyHostToDevice, stream));
     CKD(cudaMemcpyAsync(h->hist_box, h->hist_box_h.data(), n_boxes * sizeof(long long), cudaMemcpyHostToDevice, stream));
     CKD(cudaMemsetAsync(h->stats, 0, n_boxes * sizeof(epsr_mc_stats), stream));
     CKD(cudaMemsetAsync(h->status, 0, sizeof(int), stream));
@@ -853,6 +880,47 @@ extern "C" int epsr_partial_gr_range(epsr_box *box, int64_t tile_begin, int64_t 
                                      uint64_t *hist, epsr_stream_t stream)
 {
     return gr_range(box, tile_begin, tile_end, hist, (cudaStream_t)stream);
+}
+
+extern "C" int epsr_partial_gr_cells(epsr_box *box, uint64_t *hist, float *g, int64_t n_configs,
+                                     epsr_stream_t stream)
+{
+    if (!box || !hist) return set_error(EPSR_EINVAL, "NULL argument");
+    if (g && n_configs < 1) return set_error(EPSR_EINVAL, "n_configs must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = EPSR_OK;
+    if (!box->gc_items_h.empty()) {
+        rc = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
+        if (rc) return rc;
+        SortScratch sc = box->sort;          // per-atom scratch shared with the all-pairs order
+        sc.count = box->gc_count;
+        sc.offset = box->gc_offset;
+        sc.block = box->gc_block;
+        rc = launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
+                                 box->total_gcells + 1, 2, sc, box->gc_scaled, box->gc_coords, nullptr, s);
+        if (rc) return rc;
+        GcArgs a;
+        a.boxes = box->boxes;
+        a.coords = box->gc_coords;
+        a.scaled = box->gc_scaled;
+        a.cell_start = box->gc_offset;
+        a.cell_count = box->gc_count;
+        a.thresholds = box->thresholds;
+        a.items = box->gc_items;
+        a.n_items = (long long)box->gc_items_h.size();
+        a.hist = (unsigned long long *)hist;
+        a.max_pairs_bins = box->ep_cap;
+        a.max_bins1 = box->tbl_cap;
+        const int grid = (int)std::min<long long>(a.n_items, (long long)box->sms * 8);
+        rc = launch_partial_gr_cells(a, std::max(grid, 1), s);
+        if (rc) return rc;
+    }
+    // boxes too small for three cells per side: the all-pairs tiles of those boxes
+    for (int b = 0; b < box->n_boxes; ++b)
+        if (box->hb[b].gc_n == 0 && (rc = gr_range(box, box->tile_lo[b], box->tile_hi[b], hist, s)))
+            return rc;
+    if (g) return epsr_normalize_g(box, hist, g, n_configs, stream);
+    return EPSR_OK;
 }
 
 extern "C" int epsr_normalize_g(epsr_box *box, const uint64_t *hist, float *g, int64_t n_configs,

@@ -54,6 +54,9 @@ struct BoxDev {
     int32_t cells_p3;     // cells per box in the sort key space (power of two cubed)
     int32_t mc_cell0;     // first key of this box in the type-major sort
     int32_t near_fx;      // ceil(sqrt(max(rc2, tmax if an EP is set))), grid units
+    int32_t gc_n;         // cell-list histogram: cells per side (>= 3, each at least the
+                          // histogram range wide), or 0 when the box is too small for it
+    int32_t gc0;          // first key of this box in the cell-list sort
     int32_t type_start[kMaxTypes];  // first type-major sorted position of each type (box-local)
     int64_t count[kMaxTypes];   // atoms per type
     PairRow row[kMaxTypes * kMaxTypes];

@@ -89,6 +89,27 @@ struct GrArgs {
 };
 
 constexpr int kGrTile = 1024;    // atoms per tile (both sides)
+
+// Cell-list histogram: one work item per (box, home cell); pairs of the home cell with itself
+// and with its 13 forward neighbours.
+struct GcItem {
+    int box, cell;
+};
+
+struct GcArgs {
+    const BoxDev *boxes;
+    const int4 *coords;          // [n_atoms_total] in cell-list order
+    const uint4 *scaled;         // [n_atoms_total] in cell-list order
+    const int *cell_start;       // [total cells + 1] first sorted position of each cell
+    const int *cell_count;       // [total cells]
+    const long long *thresholds;
+    const GcItem *items;
+    long long n_items;
+    unsigned long long *hist;
+    int max_pairs_bins, max_bins1;
+};
+
+int launch_partial_gr_cells(const GcArgs &args, int grid, cudaStream_t stream);
 constexpr int kMcCells = 512;    // cells per (type, CTA) block of the Monte Carlo order
 
 int launch_scale_coords(const BoxDev *boxes, const int *atom_box, const int4 *coords,

@@ -77,7 +77,11 @@ __global__ void cell_key_kernel(const BoxDev *boxes, const int *atom_box, const 
         const unsigned nc = (unsigned)b.cells;
         const unsigned cx = __umulhi(s.x, nc), cy = __umulhi(s.y, nc), cz = __umulhi(s.z, nc);
         int k;
-        if (type_major) {
+        if (type_major == 2) {
+            // cell-list order: cells of at least the histogram range per side, x fastest
+            const unsigned n = (unsigned)(b.gc_n > 0 ? b.gc_n : 1);
+            k = b.gc0 + (int)((__umulhi(s.z, n) * n + __umulhi(s.y, n)) * n + __umulhi(s.x, n));
+        } else if (type_major) {
             // Monte Carlo partition: atom i of the box goes to CTA (i mod G) of its group;
             // inside a CTA's share of a type, atoms are ordered by an 8^3 Morton cell.
             const unsigned c8x = __umulhi(s.x, 8u), c8y = __umulhi(s.y, 8u), c8z = __umulhi(s.z, 8u);
@@ -184,10 +188,10 @@ __global__ void scatter_index_kernel(const int *key, const int *rank, const int 
 // the final order depends only on the coordinates.
 __global__ void cell_order_kernel(const int *count, const int *offset, int total_cells,
                                   int *idx, const uint4 *scaled, const int4 *coords,
-                                  uint4 *s_scaled, int4 *s_coords, int *pos_of)
+                                  uint4 *s_scaled, int4 *s_coords, int *pos_of, int in_order)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < total_cells; c += gridDim.x * blockDim.x) {
-        const int b = offset[c], n = count[c];
+        const int b = offset[c], n = in_order ? count[c] : 0;
         for (int a = 1; a < n; ++a) {
             const int v = idx[b + a];
             int k = a - 1;
@@ -197,12 +201,23 @@ __global__ void cell_order_kernel(const int *count, const int *offset, int total
             }
             idx[b + k + 1] = v;
         }
-        for (int a = 0; a < n; ++a) {
+        for (int a = 0, na = count[c]; a < na; ++a) {
             const int i = idx[b + a];
             if (s_scaled) s_scaled[b + a] = scaled[i];
             if (s_coords) s_coords[b + a] = coords[i];
             if (pos_of) pos_of[i] = b + a;
         }
+    }
+}
+
+__global__ void gather_sorted_kernel(const int *idx, const uint4 *scaled, const int4 *coords,
+                                     uint4 *s_scaled, int4 *s_coords, long long n)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = idx[p];
+        if (s_scaled) s_scaled[p] = scaled[i];
+        if (s_coords) s_coords[p] = coords[i];
     }
 }
 
@@ -228,8 +243,15 @@ int launch_spatial_sort(const BoxDev *boxes, const int *atom_box, const uint4 *s
     scatter_index_kernel<<<grid, 256, 0, stream>>>(sc.key, sc.rank, sc.offset, sc.index, n);
     note_launch();
     const int cgrid = (total_cells + 255) / 256 < 4096 ? (total_cells + 255) / 256 : 4096;
-    cell_order_kernel<<<cgrid, 256, 0, stream>>>(sc.count, sc.offset, total_cells, sc.index, scaled,
-                                                 coords, s_scaled, s_coords, pos_of);
+    if (type_major == 2) {
+        // the cell-list order only feeds integer counts: the order inside a cell does not
+        // matter there and its cells are large, so the scatter's order is kept and the
+        // coordinates are gathered by position, in parallel
+        gather_sorted_kernel<<<grid, 256, 0, stream>>>(sc.index, scaled, coords, s_scaled, s_coords, n);
+    } else {
+        cell_order_kernel<<<cgrid, 256, 0, stream>>>(sc.count, sc.offset, total_cells, sc.index, scaled,
+                                                     coords, s_scaled, s_coords, pos_of, 1);
+    }
     note_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "spatial sort");
@@ -363,6 +385,122 @@ int launch_partial_gr(const GrArgs &args, int grid, cudaStream_t stream)
     note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "partial_gr launch");
+}
+
+// ---- cell-list histogram (a counting order of the same pairs) ----------------------------------
+// Every pair closer than the histogram range lies in the same cell or in neighbouring cells
+// (cells are at least the range wide plus two grid units, and there are at least 3 per side,
+// so the 13 forward offsets and their negatives reach 26 distinct cells). A work item counts
+// the pairs of one home cell with itself (i < j in the sorted order) and with its 13 forward
+// neighbours, each pair once; the pair test, bins and counts are those of partial_gr_kernel,
+// so the histogram is the same integer array.
+constexpr int kGcThreads = 128;
+constexpr int kGcStage = 512;            // neighbour atoms staged in shared memory at once
+
+__constant__ int c_fwd[14][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 1, 0},  {0, 1, 0},   {1, 1, 0},
+                                 {-1, -1, 1}, {0, -1, 1},  {1, -1, 1},  {-1, 0, 1},  {0, 0, 1},
+                                 {1, 0, 1},  {-1, 1, 1},   {0, 1, 1},   {1, 1, 1}};
+
+// Bin of a pair from its FP32 squared distance g2 (relative error below 2^-21.7 from the
+// int32 separations), falling back to the exact integer test only where that error could
+// matter: the bin is floor(sqrt(d2) / w) exactly (d2 >= T[k] <=> d2 >= (k w)^2 for integer
+// d2), and x = sqrt(g2) / w carries a relative error below 2^-21, so floor(x) is the bin
+// unless x lies within x 2^-20 of an integer. Returns -1 outside the histogram range.
+__device__ __forceinline__ int bin_of_fast(Sep sp, float g2, const long long *T, int nb, float inv,
+                                           long long tmax, float tmax_lo, float tmax_hi)
+{
+    if (g2 >= tmax_hi) return -1;
+    if (g2 >= tmax_lo && d2_of(sp) >= tmax) return -1;
+    const float x = sqrtf(g2) * inv;
+    const int k = (int)x;
+    const float f = x - (float)k, eps = x * 0x1p-20f;
+    if (f > eps && f < 1.f - eps && k < nb) return k;
+    return bin_of(d2_of(sp), g2, T, nb, inv);
+}
+
+__global__ void __launch_bounds__(kGcThreads) partial_gr_cells_kernel(GcArgs A)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    int4 *s_true = reinterpret_cast<int4 *>(dyn);
+    long long *s_T = reinterpret_cast<long long *>(s_true + kGcStage);
+    unsigned *s_hist = reinterpret_cast<unsigned *>(s_T + A.max_bins1);
+    __shared__ BoxDev bx;
+    __shared__ int cur_box;
+    const int tid = threadIdx.x;
+    if (tid == 0) cur_box = -1;
+    for (int k = tid; k < A.max_pairs_bins; k += kGcThreads) s_hist[k] = 0u;
+    __syncthreads();
+
+    for (long long w = blockIdx.x; w < A.n_items; w += gridDim.x) {
+        const GcItem it = A.items[w];
+        __syncthreads();
+        if (it.box != cur_box) {
+            if (cur_box >= 0) flush_hist(s_hist, bx.n_pairs * bx.n_bins, A.hist + bx.hist_off);
+            __syncthreads();
+            if (tid == 0) {
+                bx = A.boxes[it.box];
+                cur_box = it.box;
+            }
+            __syncthreads();
+            for (int k = tid; k <= bx.n_bins; k += kGcThreads) s_T[k] = A.thresholds[bx.tbl_off + k];
+            __syncthreads();
+        }
+        const int n = bx.gc_n, L = bx.L, nb = bx.n_bins, nt = bx.n_types;
+        const long long tmax = bx.tmax;
+        const float tmax_lo = bx.tmax_lo, tmax_hi = bx.tmax_hi, inv = bx.inv_dr_fx;
+        const int hc = it.cell, hx = hc % n, hy = (hc / n) % n, hz = hc / (n * n);
+        const int hs = A.cell_start[bx.gc0 + hc], nh = A.cell_count[bx.gc0 + hc];
+        for (int i0 = 0; i0 < nh; i0 += kGcThreads) {
+            const int ip = i0 + tid < nh ? hs + i0 + tid : -1;        // sorted position of my atom
+            const int4 pi = ip >= 0 ? A.coords[ip] : make_int4(0, 0, 0, 0);
+            for (int t = 0; t < 14; ++t) {
+                const int cx = (hx + c_fwd[t][0] + n) % n, cy = (hy + c_fwd[t][1] + n) % n,
+                          cz = (hz + c_fwd[t][2] + n) % n;
+                const int c = bx.gc0 + (cz * n + cy) * n + cx;
+                const int cs = A.cell_start[c], nc = A.cell_count[c];
+                for (int j0 = 0; j0 < nc; j0 += kGcStage) {
+                    const int nj = min(kGcStage, nc - j0);
+                    __syncthreads();
+                    for (int j = tid; j < nj; j += kGcThreads) s_true[j] = A.coords[cs + j0 + j];
+                    __syncthreads();
+                    if (ip < 0) continue;
+                    // own cell: only partners after me in the sorted order (each pair once)
+                    const int jstart = t == 0 ? max(0, ip + 1 - (cs + j0)) : 0;
+                    for (int j = jstart; j < nj; ++j) {
+                        const int4 pj = s_true[j];
+                        const Sep sp = sep(pi, pj, L);
+                        const float g2 = g2_of(sp);
+                        if (g2 < tmax_hi) {
+                            const int k = bin_of_fast(sp, g2, s_T, nb, inv, tmax, tmax_lo, tmax_hi);
+                            if (k >= 0) atomicAdd(&s_hist[pair_index(pi.w, pj.w, nt) * nb + k], 1u);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (cur_box >= 0) flush_hist(s_hist, bx.n_pairs * bx.n_bins, A.hist + bx.hist_off);
+}
+
+int launch_partial_gr_cells(const GcArgs &args, int grid, cudaStream_t stream)
+{
+    if (args.n_items <= 0) return EPSR_OK;
+    const size_t smem = (size_t)kGcStage * sizeof(int4) + (size_t)args.max_bins1 * sizeof(long long) +
+                        (size_t)args.max_pairs_bins * sizeof(unsigned);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(partial_gr_cells_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(gr cells)");
+        attr_set = true;
+    }
+    if (smem > 200 * 1024)
+        return set_error(EPSR_EINVAL, "partial_gr_cells: n_pairs*n_bins too large for shared memory");
+    partial_gr_cells_kernel<<<grid, kGcThreads, smem, stream>>>(args);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "partial_gr_cells launch");
 }
 
 // g_ab(k) = H V / (n_configs P_ab (4 pi / 3)(r_{k+1}^3 - r_k^3)), r_k = k dr.

@@ -35,7 +35,7 @@ EXPORTS = [
     "epsr_noalloc_scratch_bytes", "epsr_partial_gr_noalloc", "epsr_ep_update",
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
-    "epsr_mc_set_cells", "epsr_sq_plan_status",
+    "epsr_mc_set_cells", "epsr_sq_plan_status", "epsr_partial_gr_cells",
 ]
 
 
@@ -102,6 +102,7 @@ def lib():
             "epsr_mc_set_ctas": ([vp, i32], C.c_int),
             "epsr_debug_barrier_fault": ([vp, i32, dbl], C.c_int),
             "epsr_partial_gr": ([vp, vp, vp, i64, vp], C.c_int),
+            "epsr_partial_gr_cells": ([vp, vp, vp, i64, vp], C.c_int),
             "epsr_partial_gr_tiles": ([vp, P(i64)], C.c_int),
             "epsr_partial_gr_range": ([vp, i64, i64, vp, vp], C.c_int),
             "epsr_normalize_g": ([vp, vp, vp, i64, vp], C.c_int),
@@ -307,6 +308,10 @@ class Box:
     def epsr_partial_gr(self, hist, g=None, n_configs: int = 1, stream=None):
         _check(lib().epsr_partial_gr(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
                                      _stream(stream)), "epsr_partial_gr")
+
+    def epsr_partial_gr_cells(self, hist, g=None, n_configs: int = 1, stream=None):
+        _check(lib().epsr_partial_gr_cells(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
+                                           _stream(stream)), "epsr_partial_gr_cells")
 
     def epsr_partial_gr_tiles(self) -> int:
         n = C.c_int64()

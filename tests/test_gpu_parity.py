@@ -87,9 +87,44 @@ def test_histogram_tile_ranges_sum_to_full():
 @pytest.mark.parametrize("which", ["water", "silica"])
 def test_histogram_bit_exact_paper_size(which):
     s = synth.paper_water() if which == "water" else synth.paper_silica()
-    H = gpu_hist(epsr.Box(s)).reshape(3, s.n_bins)
+    box = epsr.Box(s)
+    H = gpu_hist(box).reshape(3, s.n_bins)
     ref = oracle.Box(s).histogram(threads=0)
     assert np.array_equal(H, ref)
+    Hc = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    box.epsr_partial_gr_cells(Hc)
+    torch.cuda.synchronize()
+    assert np.array_equal(Hc.cpu().numpy().astype(np.uint64).reshape(3, s.n_bins), ref)
+
+
+@pytest.mark.parametrize("n,L,cut_bins", [(3000, 44.8, 333), (2000, 31.0, 200), (5000, 40.0, 100)])
+def test_cell_list_histogram_bit_exact(n, L, cut_bins):
+    """Cell lists of 4, 3 and 9 cells per side (water; a gas with 0.04 A bins to 8 A; a gas
+    with a 4 A range): the same integer counts as the oracle."""
+    if n == 3000:
+        s = synth.water_box(1000, seed=71, L_A=L)
+    else:
+        s = synth.uniform_gas(n, L, seed=n, n_types=3)
+        s.bin_p, s.bin_q, s.n_bins = 1, 25, cut_bins
+    box = epsr.Box(s)
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    box.epsr_partial_gr_cells(H)
+    torch.cuda.synchronize()
+    ref = oracle.Box(s).histogram(threads=8)
+    assert np.array_equal(H.cpu().numpy().astype(np.uint64).reshape(ref.shape), ref)
+
+
+def test_cell_list_histogram_batch_with_small_boxes():
+    """A handle mixing boxes with cell lists and boxes too small for three cells (counted
+    by the all-pairs kernel): identical to epsr_partial_gr on the whole handle."""
+    systems = [synth.water_box(300, seed=72, L_A=20.8), synth.water_box(3000, seed=73),
+               synth.silica_box(600, seed=74), synth.silica_box(4000, seed=75)]
+    box = epsr.Box(systems)
+    H1 = gpu_hist(box)
+    H2 = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    box.epsr_partial_gr_cells(H2)
+    torch.cuda.synchronize()
+    assert np.array_equal(H1, H2.cpu().numpy().astype(np.uint64))
 
 
 def test_g_normalisation(small_water):
