@@ -272,6 +272,93 @@ def run_sweep(args):
     return 0
 
 
+def run_smeared(args):
+    """The differentiable form on the 99,999-atom water box (seed 4): chi^2 of the smeared
+    g(r) against a target S(Q) (a seed-5 box plus N(0, 0.005^2) noise) and its gradients with
+    respect to every coordinate and the EP coefficients, timed forward and backward, beside
+    the exact histogram of the same box."""
+    import torch
+    from paper_1904_08756_gb300 import build, epsr, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if not os.path.exists(epsr.LIB_PATH):
+        build.build()
+    s = synth.paper_water(seed=4)
+    t = synth.paper_water(seed=5)
+    sigma, P = 0.05, 3
+    box, tbox = epsr.Box(s), epsr.Box(t)
+    w_cols, flat = box.epsr_sq_weights(0)
+    rho = s.n_atoms / s.L ** 3
+    W = np.asarray(w_cols) / (4.0 * np.pi * rho)
+    plan = epsr.SqPlan(s.Q, s.n_bins, s.dr, epsr.SQ_FP32, max_cols=P)
+    H = torch.zeros(tbox.hist_len, dtype=torch.int64, device=dev)
+    g = torch.zeros(tbox.hist_len, dtype=torch.float32, device=dev)
+    tbox.epsr_partial_gr(H, g, 1)
+    St = torch.zeros((1, len(s.Q)), dtype=torch.float32, device=dev)
+    plan.epsr_sq_exec(g.view(P, -1), w_cols, P, np.array([flat]), None, St)
+    noise = torch.from_numpy(np.random.default_rng(5).normal(size=len(s.Q)) * 0.005).float().to(dev)
+    target = St[0] + noise
+    F = epsr.smeared_chi2_function()
+    C_ = torch.tensor(np.random.default_rng(6).normal(size=(P, 20)) * 0.001, dtype=torch.float64,
+                      device=dev, requires_grad=True)
+    pos = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device=dev, requires_grad=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def once(ev=None):
+        pos.grad = None
+        C_.grad = None
+        if ev:
+            ev[0].record(stream)
+        chi2 = F.apply(pos, C_, box, plan, sigma, W, w_cols, flat, target, 0.5, rho)
+        if ev:
+            ev[1].record(stream)
+        chi2.backward()
+        if ev:
+            ev[2].record(stream)
+        return chi2
+
+    launches0 = epsr.epsr_launch_count()
+    for _ in range(args.warmup):
+        once()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = epsr.epsr_launch_count()
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            chi2 = once(evs[k])
+        torch.cuda.synchronize()
+    launches = epsr.epsr_launch_count() - launches0
+    t_f = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    t_b = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    Hx = torch.zeros(box.hist_len, dtype=torch.int64, device=dev)
+    ge = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a_ev, b_ev in ge:
+        Hx.zero_()
+        flush.fill_(3.0)
+        a_ev.record(stream)
+        box.epsr_partial_gr(Hx)
+        b_ev.record(stream)
+    torch.cuda.synchronize()
+    t_h = sum(a.elapsed_time(b) for a, b in ge) / len(ge)
+    pairs = s.n_atoms * (s.n_atoms - 1) // 2
+    line = {"metric": "chi^2 and dchi^2/dx evaluations/s (differentiable form) at 100k atoms", "value": 1e3 / (t_f + t_b),
+            "unit": "evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_f + t_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32 (fixed-point 2^-32 accumulation, fp64 chi^2)", "data": "synthetic",
+            "config": {"workload": "99,999-atom water (seed 4), sigma 0.05 A Gaussian-smeared g(r) (333 x 0.03 A), "
+                                   "S(Q) on 1000 Q, chi^2 against a seed-5 target + noise, gradients for all "
+                                   "coordinates and 60 EP coefficients via torch.autograd",
+                       "l2": "flushed before every evaluation outside the timed events"},
+            "ms_breakdown": {"forward": t_f, "backward": t_b, "exact_histogram_same_box": t_h},
+            "pair_distances_per_s_forward": pairs / (t_f * 1e-3),
+            "chi2": float(chi2.item()), "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_replicas(args):
     import torch
     from paper_1904_08756_gb300 import build, epsr, synth
@@ -353,10 +440,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water", choices=["water", "silica", "replicas", "sweep"],
+    ap.add_argument("--workload", default="water", choices=["water", "silica", "replicas", "sweep", "smeared"],
                     help="water: the paper-scale water box (default line); silica: the paper-scale "
                          "SiO2 box with single-atom moves; replicas: 64 uneven boxes; sweep: MC "
-                         "moves/s at the paper's Table 1 atom counts")
+                         "moves/s at the paper's Table 1 atom counts; smeared: chi^2 and gradients of "
+                         "the differentiable form")
     ap.add_argument("--max-atoms", type=int, default=0, help="sweep: largest atom count (0: all)")
     ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
                     help="moves per step (profiling runs only; the benchmark uses 10,000)")
@@ -369,6 +457,8 @@ def main():
         return run_replicas(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "smeared":
+        return run_smeared(args)
 
     import torch
     from paper_1904_08756_gb300 import build, epsr, shard, synth
@@ -486,9 +576,13 @@ def main():
         mc_achieved = mc_ops / (t_mc * 1e-3)
         gr_achieved = pairs * OPS_PER_PAIR_DIST / (t_gr * 1e-3)
         traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-        traffic = None
+        traffic = traffic_gr = None
         if os.path.exists(traffic_file):
-            traffic = json.load(open(traffic_file)).get("mc_sweep_kernel_bytes_per_launch")
+            tj = json.load(open(traffic_file))
+            traffic = tj.get("mc_sweep_kernel_bytes_per_launch")
+            traffic_gr = tj.get("partial_gr_kernel_bytes_per_launch")
+        if args.workload != "water" or moves != MOVES_PER_STEP:
+            traffic = traffic_gr = None          # the counters were taken on the water step
         line = {
             "metric": METRIC, "value": moves_per_s, "unit": "moves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
@@ -507,7 +601,8 @@ def main():
                          "kernel": "mc_sweep_kernel",
                          "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src} max clock)"},
             "roofline_gr": {"bound": "alu", "achieved": gr_achieved / 1e12, "peak": alu_peak / 1e12,
-                            "unit": "Tops/s", "frac": gr_achieved / alu_peak, "kernel": "partial_gr_kernel"},
+                            "unit": "Tops/s", "frac": gr_achieved / alu_peak, "traffic": traffic_gr,
+                            "kernel": "partial_gr_kernel"},
             "gr_cell_list": {"ms": t_gc, "pairs_in_range": in_range,
                              "pairs_in_range_per_s": in_range / (t_gc * 1e-3),
                              "speedup_vs_all_pairs": t_gr / t_gc,
