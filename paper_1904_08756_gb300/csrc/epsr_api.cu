@@ -434,7 +434,8 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
         const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
         bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
         // cell-list histogram: cells at least the histogram range plus two grid units wide
-        const long long rcut = (long long)std::ceil(std::sqrt((double)bx.tmax)) + 2;
+        const long long rcut = (long long)std::ceil(std::sqrt((double)bx.tmax)) + 2 +
+                               (long long)std::ceil(kCellSmearMarginA * std::ldexp(1.0, descs[b].scale_log2));
         long long side = 1;                       // more cells than atoms gain nothing
         while (side * side * side < bx.n_atoms) ++side;
         const long long gn = std::min<long long>(std::min<long long>(bx.L / rcut, side), 512);
@@ -971,6 +972,7 @@ struct epsr_sq_plan {
     float *Kt = nullptr;
     float *Sp_scratch = nullptr;
     double *res = nullptr;      // chi^2 residuals [nQ]
+    double *chiF = nullptr;     // chi^2 basis values [max basis][nQ] (allocated on first use)
     // tensor-core modes
     unsigned char *a_packed = nullptr, *b_packed = nullptr;
     int *tc_status = nullptr;
@@ -978,7 +980,7 @@ struct epsr_sq_plan {
     int prod_a[8] = {0}, prod_b[8] = {0};
     ~epsr_sq_plan()
     {
-        void *ptrs[] = {Q, Kt, Sp_scratch, res, a_packed, b_packed, tc_status};
+        void *ptrs[] = {Q, Kt, Sp_scratch, res, chiF, a_packed, b_packed, tc_status};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -1210,11 +1212,29 @@ extern "C" int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t
 }
 
 // ---- differentiable form: smeared histogram, adjoints, chi^2 ----------------------------------
+// The cell-list form serves when every box has a cell list and 5 sigma fits in the cells'
+// margin; otherwise the all-pairs tiles (any sigma, any box).
+static bool smear_uses_cells(const epsr_box *box, double sigma)
+{
+    if (box->gc_items_h.empty() || 5.0 * sigma > kCellSmearMarginA) return false;
+    for (const auto &b : box->hb)
+        if (b.gc_n == 0) return false;
+    return true;
+}
+
 static int smear_common(epsr_box *box, double sigma, cudaStream_t s)
 {
     if (!(sigma > 0) || sigma > 2.0) return set_error(EPSR_EINVAL, "smeared g: sigma must be in (0, 2] A");
     int rc = launch_scale_coords(box->boxes, box->atom_box, box->coords, box->scaled, box->n_atoms, s);
     if (rc) return rc;
+    if (smear_uses_cells(box, sigma)) {
+        SortScratch sc = box->sort;
+        sc.count = box->gc_count;
+        sc.offset = box->gc_offset;
+        sc.block = box->gc_block;
+        return launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
+                                   box->total_gcells + 1, 2, sc, box->gc_scaled, box->gc_coords, nullptr, s);
+    }
     return launch_spatial_sort(box->boxes, box->atom_box, box->scaled, box->coords, box->n_atoms,
                                box->total_cells, 0, box->sort, box->sorted_scaled, box->sorted_coords,
                                nullptr, s);
@@ -1225,14 +1245,29 @@ static SmearArgs smear_args(epsr_box *box, double sigma)
     SmearArgs a;
     memset(&a, 0, sizeof(a));
     a.boxes = box->boxes;
-    a.coords = box->sorted_coords;
-    a.scaled = box->sorted_scaled;
     a.index = box->sort.index;
-    a.tiles = box->tiles;
-    a.n_tiles = (long long)box->tiles_h.size();
     a.sigma = sigma;
     a.max_pairs_bins = box->ep_cap;
+    if (smear_uses_cells(box, sigma)) {
+        a.coords = box->gc_coords;
+        a.scaled = box->gc_scaled;
+        a.items = box->gc_items;
+        a.n_items = (long long)box->gc_items_h.size();
+        a.cell_start = box->gc_offset;
+        a.cell_count = box->gc_count;
+    } else {
+        a.coords = box->sorted_coords;
+        a.scaled = box->sorted_scaled;
+        a.tiles = box->tiles;
+        a.n_tiles = (long long)box->tiles_h.size();
+    }
     return a;
+}
+
+static int smear_launch(epsr_box *box, const SmearArgs &a, bool backward, cudaStream_t s)
+{
+    if (a.items) return launch_smear_cells(a, backward, (int)std::min<long long>(a.n_items, (long long)box->sms * 8), s);
+    return launch_smear(a, backward, box->sms * 2, s);
 }
 
 extern "C" int epsr_gr_smeared_fwd(epsr_box *box, double sigma, double *Ht, float *gt, epsr_stream_t stream)
@@ -1244,7 +1279,7 @@ extern "C" int epsr_gr_smeared_fwd(epsr_box *box, double sigma, double *Ht, floa
     CK(cudaMemsetAsync(box->smear_acc, 0, (size_t)box->hist_len * sizeof(unsigned long long), s));
     SmearArgs a = smear_args(box, sigma);
     a.acc = box->smear_acc;
-    rc = launch_smear(a, false, box->sms * 2, s);
+    rc = smear_launch(box, a, false, s);
     if (rc) return rc;
     return launch_smear_norm(box->boxes, box->n_boxes, box->smear_acc, Ht, gt, box->hist_len,
                              box->hist_box, s);
@@ -1263,7 +1298,7 @@ extern "C" int epsr_gr_smeared_bwd(epsr_box *box, double sigma, const float *dgt
     SmearArgs a = smear_args(box, sigma);
     a.lambda = box->lambda;
     a.grad = grad;
-    return launch_smear(a, true, box->sms * 2, s);
+    return smear_launch(box, a, true, s);
 }
 
 extern "C" int epsr_sq_exec_adjoint(epsr_sq_plan *plan, const float *dS_total, int32_t n_cols,
@@ -1299,6 +1334,13 @@ extern "C" int epsr_chi2(epsr_sq_plan *plan, const float *S, const float *target
     prm.rho = rho;
     for (int p = 0; p < P; ++p) prm.W[p] = W[p];
     prm.res_scratch = plan->res;
+    if (C && !plan->chiF) {
+        if (cudaMalloc(&plan->chiF, (size_t)kEpMaxBasis * plan->nQ * sizeof(double)) != cudaSuccess) {
+            plan->chiF = nullptr;
+            return set_error(EPSR_ENOMEM, "chi2: basis scratch");
+        }
+    }
+    prm.F_scratch = plan->chiF;
     return launch_chi2(S, target, plan->Q, plan->nQ, prm, C, chi2, dS, C ? dC : nullptr,
                        (cudaStream_t)stream);
 }

@@ -143,12 +143,19 @@ struct SmearArgs {
     const GrTile *tiles;
     long long n_tiles;
     double sigma;
-    unsigned long long *acc;   // forward output: weights * 2^32, accumulated
+    unsigned long long *acc;   // forward output: weights * 2^24, accumulated
     const float *lambda;       // backward input: dL/dHt [hist_len]
     float *grad;               // backward output [n_atoms_total][3] (accumulated)
     int max_pairs_bins;
+    // cell-list form (coords, index in cell order): items and cell ranges
+    const GcItem *items;
+    long long n_items;
+    const int *cell_start, *cell_count;
 };
 int launch_smear(const SmearArgs &a, bool backward, int grid, cudaStream_t stream);
+int launch_smear_cells(const SmearArgs &a, bool backward, int grid, cudaStream_t stream);
+// cell-list cells are widened by this margin so that smearing with 5 sigma up to it fits
+constexpr double kCellSmearMarginA = 0.5;
 int launch_smear_norm(const BoxDev *boxes, int n_boxes, const unsigned long long *acc, double *Ht,
                       float *gt, long long hist_len, const long long *hist_box, cudaStream_t stream);
 int launch_smear_lambda(const BoxDev *boxes, int n_boxes, const float *dgt, float *lam, long long hist_len,
@@ -177,6 +184,7 @@ struct ChiParams {
     double s, rho;
     double W[kEpMaxPairs];     // Eq. (1) weights (2 - delta) c_a c_b b_a b_b, barn
     double *res_scratch;       // [nQ] residuals
+    double *F_scratch;         // [n_basis][nQ] basis values F_n(Q)
 };
 int launch_chi2(const float *S, const float *target, const float *Q, int nQ, const ChiParams &prm,
                 const double *C, double *chi2, float *dS, double *dC, cudaStream_t stream);

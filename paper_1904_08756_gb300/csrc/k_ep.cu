@@ -158,12 +158,22 @@ ep_update_kernel(EpArgs A)
 }
 
 // ---- chi^2 of the differentiable form: chi2 = sum_Q [S(Q) + sum_p W_p sum_n C_pn F_n(Q) - T(Q)]^2
-// One CTA (deterministic FP64 reduction order); dS = 2 res, dC_pn = 2 W_p sum_Q res F_n(Q).
+// The basis values F_n(Q) (FP64 transcendentals, slow on GB300's narrow FP64 unit) are
+// evaluated once per call by a grid-wide kernel; one CTA then forms the residuals and the
+// sums in a fixed FP64 order (deterministic): dS = 2 res, dC_pn = 2 W_p sum_Q res F_n(Q).
 constexpr int kChiThreads = 512;
 constexpr int kChiMaxQ = 8192;
 
+__global__ void chi2_basis_kernel(const float *Q, int nQ, int n_basis, double s, double rho, double *F)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_basis * nQ; e += gridDim.x * blockDim.x) {
+        const int n = e / nQ, i = e % nQ;
+        F[e] = poisson_F(n + 1, s, (double)Q[i], rho);
+    }
+}
+
 __global__ void __launch_bounds__(kChiThreads, 1)
-chi2_kernel(const float *S, const float *T, const float *Q, int nQ, ChiParams prm, const double *C,
+chi2_kernel(const float *S, const float *T, int nQ, ChiParams prm, const double *C, const double *F,
             double *chi2, float *dS, double *dC)
 {
     __shared__ double red[kChiThreads / 32];
@@ -173,8 +183,7 @@ chi2_kernel(const float *S, const float *T, const float *Q, int nQ, ChiParams pr
         if (C)
             for (int p = 0; p < prm.P; ++p) {
                 double v = 0.0;
-                for (int n = 1; n <= prm.n_basis; ++n)
-                    v += C[p * prm.n_basis + n - 1] * poisson_F(n, prm.s, (double)Q[i], prm.rho);
+                for (int n = 0; n < prm.n_basis; ++n) v += C[p * prm.n_basis + n] * F[n * nQ + i];
                 img += prm.W[p] * v;
             }
         const double res = (double)S[i] + img - (double)T[i];
@@ -187,9 +196,9 @@ chi2_kernel(const float *S, const float *T, const float *Q, int nQ, ChiParams pr
     __syncthreads();
     if (dC)
         for (int e = threadIdx.x; e < prm.P * prm.n_basis; e += kChiThreads) {
-            const int p = e / prm.n_basis, n = e % prm.n_basis + 1;
+            const int p = e / prm.n_basis, n = e % prm.n_basis;
             double v = 0.0;
-            for (int i = 0; i < nQ; ++i) v += prm.res_scratch[i] * poisson_F(n, prm.s, (double)Q[i], prm.rho);
+            for (int i = 0; i < nQ; ++i) v += prm.res_scratch[i] * F[n * nQ + i];
             dC[e] = 2.0 * prm.W[p] * v;
         }
 }
@@ -206,7 +215,12 @@ int launch_chi2(const float *S, const float *target, const float *Q, int nQ, con
                 const double *C, double *chi2, float *dS, double *dC, cudaStream_t stream)
 {
     if (nQ > kChiMaxQ) return set_error(EPSR_EINVAL, "chi2: nQ above %d", kChiMaxQ);
-    chi2_kernel<<<1, kChiThreads, 0, stream>>>(S, target, Q, nQ, prm, C, chi2, dS, dC);
+    if (C) {
+        const int n = prm.n_basis * nQ;
+        chi2_basis_kernel<<<(n + 255) / 256, 256, 0, stream>>>(Q, nQ, prm.n_basis, prm.s, prm.rho, prm.F_scratch);
+        note_launch();
+    }
+    chi2_kernel<<<1, kChiThreads, 0, stream>>>(S, target, nQ, prm, C, prm.F_scratch, chi2, dS, dC);
     note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "chi2");

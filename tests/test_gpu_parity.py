@@ -462,8 +462,10 @@ def test_smeared_chi2_and_gradients_small_box():
     assert rel <= 1e-4, rel
 
 
-def test_smeared_histogram_matches_oracle():
-    s = synth.water_box(400, seed=42, L_A=23.0)
+@pytest.mark.parametrize("n_mol,L", [(400, 23.0), (3000, 44.8)], ids=["tiles", "cell-lists"])
+def test_smeared_histogram_matches_oracle(n_mol, L):
+    """The 23 A box has no cell list (all-pairs tiles); the 44.8 A box has 4 cells per side."""
+    s = synth.water_box(n_mol, seed=42, L_A=L)
     box = epsr.Box(s)
     Ht = torch.zeros(box.hist_len, dtype=torch.float64, device=DEV)
     box.epsr_gr_smeared_fwd(0.05, Ht)
@@ -471,6 +473,26 @@ def test_smeared_histogram_matches_oracle():
     ref = oracle.Box(s).smeared_hist(0.05)
     got = Ht.cpu().numpy().reshape(ref.shape)
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_smeared_gradient_cell_lists_medium_box():
+    """chi^2 gradients through the cell-list form (9,000 atoms, 4 cells per side) against
+    the oracle for every atom."""
+    s = synth.water_box(3000, seed=43, L_A=44.8)
+    sigma = 0.05
+    box, plan, W, flat, rho, w_cols, Q, target, C_ = _diff_setup(s, 5, sigma)
+    F = epsr.smeared_chi2_function()
+    pos = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device=DEV, requires_grad=True)
+    Ct = torch.tensor(C_, dtype=torch.float64, device=DEV, requires_grad=True)
+    tgt = torch.tensor(target, dtype=torch.float32, device=DEV)
+    chi2 = F.apply(pos, Ct, box, plan, sigma, W, w_cols, flat, tgt, 0.5, rho)
+    chi2.backward()
+    ob = oracle.Box(s)
+    tgt64 = tgt.cpu().numpy().astype(np.float64)
+    c_ref, dC_ref, gx_ref, _, _ = oracle.chi2_and_grads(ob, sigma, Q, tgt64, C_, 0.5)
+    assert abs(chi2.item() - c_ref) <= 1e-4 * abs(c_ref)
+    g = pos.grad.cpu().numpy()
+    assert np.linalg.norm(g - gx_ref) <= 1e-4 * np.linalg.norm(gx_ref)
 
 
 def test_smeared_gradient_paper_size_sampled():
