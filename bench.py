@@ -153,7 +153,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "paper-scale water, 99,999 atoms, 10,000 moves + g(r) + S(Q) per step"},
+            "config": {"workload": workload_name(system, MOVES_PER_STEP),
+                       "n_atoms": system.n_atoms, "moves_per_step": MOVES_PER_STEP},
             "cpu_baseline": {"value": v, "unit": "moves/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": v, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
