@@ -567,6 +567,12 @@ def main():
     t_gc = sum(a_ev.elapsed_time(b_ev) for a_ev, b_ev in gc_ev) / len(gc_ev)
     in_range = int(Hc.sum().item())
 
+    # ---- bounds of the sweep measured on this GPU: grid-barrier floor, issue rates ------------
+    sms_dev = torch.cuda.get_device_properties(dev).multi_processor_count
+    barrier_ns = epsr.epsr_bench_barrier_floor(sms_dev, 4000)
+    int_rate = epsr.epsr_bench_alu_rate(0)
+    fma_rate = epsr.epsr_bench_alu_rate(1)
+
     if rank == 0:
         peaks, src = measured_peaks()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -604,6 +610,13 @@ def main():
             "roofline_gr": {"bound": "alu", "achieved": gr_achieved / 1e12, "peak": alu_peak / 1e12,
                             "unit": "Tops/s", "frac": gr_achieved / alu_peak, "traffic": traffic_gr,
                             "kernel": "partial_gr_kernel"},
+            "measured_bounds": {
+                "grid_barrier_floor_us": barrier_ns * 1e-3,
+                "mc_ceiling_moves_per_s_at_32_per_barrier": 32.0 / (barrier_ns * 1e-9),
+                "int32_xor_add_lane_ops_per_s": int_rate, "fp32_fma_lane_ops_per_s": fma_rate,
+                "note": "epsr_bench_barrier_floor (152 CTAs, the sweep's exchange alone) and "
+                        "epsr_bench_alu_rate (independent xor+add / FMA chains); the roofline peak stays "
+                        "the unit-count figure"},
             "gr_cell_list": {"ms": t_gc, "pairs_in_range": in_range,
                              "pairs_in_range_per_s": in_range / (t_gc * 1e-3),
                              "speedup_vs_all_pairs": t_gr / t_gc,

@@ -36,6 +36,7 @@ EXPORTS = [
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
     "epsr_mc_set_cells", "epsr_sq_plan_status", "epsr_partial_gr_cells",
+    "epsr_bench_barrier_floor", "epsr_bench_alu_rate",
 ]
 
 
@@ -117,6 +118,8 @@ def lib():
             "epsr_checkpoint_size": ([vp, P(C.c_size_t)], C.c_int),
             "epsr_launch_count": ([P(C.c_uint64)], C.c_int),
             "epsr_mc_set_cells": ([vp, C.c_int32, C.c_int32], C.c_int),
+            "epsr_bench_barrier_floor": ([C.c_int32, C.c_int32, P(C.c_double), vp], C.c_int),
+            "epsr_bench_alu_rate": ([C.c_int32, P(C.c_double), vp], C.c_int),
             "epsr_sq_plan_status": ([vp, P(C.c_int32), vp], C.c_int),
             "epsr_checkpoint_save": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_checkpoint_load": ([vp, vp, C.c_size_t, vp], C.c_int),
@@ -189,6 +192,20 @@ def epsr_strerror(status: int) -> str:
 
 def epsr_version() -> int:
     return lib().epsr_version()
+
+
+def epsr_bench_barrier_floor(ctas: int, iters: int = 2000, stream=None) -> float:
+    """ns per grid barrier of the sweep's exchange with `ctas` co-resident CTAs."""
+    v = C.c_double()
+    _check(lib().epsr_bench_barrier_floor(ctas, iters, C.byref(v), _stream(stream)), "epsr_bench_barrier_floor")
+    return v.value
+
+
+def epsr_bench_alu_rate(kind: int, stream=None) -> float:
+    """Lane-operations/s: kind 0 = int32 adds, 1 = FP32 FMAs."""
+    v = C.c_double()
+    _check(lib().epsr_bench_alu_rate(kind, C.byref(v), _stream(stream)), "epsr_bench_alu_rate")
+    return v.value
 
 
 def epsr_launch_count() -> int:

@@ -589,3 +589,16 @@ def test_checkpoint_resume_is_bit_exact():
     bad[0] ^= 1
     with pytest.raises(epsr.EpsrError):
         c.epsr_checkpoint_load(bytes(bad))
+
+
+def test_measurement_kernels():
+    """The grid-barrier floor and the issue-rate kernels run, return finite rates and stay
+    below the nominal ceilings (152 SMs x 128 lanes x 2.07 GHz)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ns = epsr.epsr_bench_barrier_floor(sms, 500)
+    assert 100.0 < ns < 1e6
+    for kind in (0, 1):
+        r = epsr.epsr_bench_alu_rate(kind)
+        assert 1e12 < r < 1.2 * sms * 128 * 2.1e9
+    with pytest.raises(epsr.EpsrError):
+        epsr.epsr_bench_barrier_floor(100000, 10)
