@@ -47,7 +47,9 @@ class OrcSystem(C.Structure):
                 ("q", C.c_double * MAX_TYPES), ("sigma", C.c_double * MAX_TYPES),
                 ("eps", C.c_double * MAX_TYPES), ("r_coul", C.c_double),
                 ("bin_p", C.c_int32), ("bin_q", C.c_int32), ("n_bins", C.c_int32),
-                ("rigid", C.c_int32), ("temperature", C.c_double),
+                ("rigid", C.c_int32), ("flexible", C.c_int32),
+                ("bond_k", C.c_double * (MAX_TYPES * MAX_TYPES)),
+                ("bond_d", C.c_double * (MAX_TYPES * MAX_TYPES)), ("temperature", C.c_double),
                 ("max_translation", C.c_double), ("max_rotation_deg", C.c_double),
                 ("ep", C.POINTER(C.c_double))]
 
@@ -135,6 +137,12 @@ class Box:
         st.r_coul = system.r_coul
         st.bin_p, st.bin_q, st.n_bins = system.bin_p, system.bin_q, system.n_bins
         st.rigid = 1 if system.rigid_molecules else 0
+        st.flexible = 1 if getattr(system, "flexible", False) else 0
+        if st.flexible:
+            for a in range(system.n_types):
+                for b in range(system.n_types):
+                    st.bond_k[a * MAX_TYPES + b] = float(system.bond_k[a][b])
+                    st.bond_d[a * MAX_TYPES + b] = float(system.bond_d[a][b])
         st.temperature = system.temperature
         st.max_translation = system.max_translation
         st.max_rotation_deg = system.max_rotation_deg

@@ -150,8 +150,29 @@ static int64_t mol_of_atom(const orc_system *s, int64_t i)
     return lo;
 }
 
+/* Intra-molecular energy of a flexible molecule (Sec. 3.1: the molecule is held together
+ * by harmonic potentials between every two of its atoms; reading r6 for the form):
+ * sum over atom pairs a < b of k_ab (r_ab - d_ab)^2, r_ab the minimum-image distance of
+ * the coordinates xyz_mol [m][3]. Zero for boxes without flexible molecules. */
+double orc_intra_energy(const orc_system *s, int64_t mol, const int32_t *xyz_mol)
+{
+    if (!s->flexible) return 0.0;
+    const int64_t a0 = s->mol_start[mol], m = s->mol_start[mol + 1] - a0;
+    const double inv_S = ldexp(1.0, -s->scale_log2);
+    double U = 0.0;
+    for (int64_t a = 0; a < m; ++a)
+        for (int64_t b = a + 1; b < m; ++b) {
+            const int t = s->type[a0 + a] * ORC_MAX_TYPES + s->type[a0 + b];
+            if (s->bond_k[t] == 0.0) continue;
+            const double r = sqrt((double)orc_dist2_points(&xyz_mol[3 * a], &xyz_mol[3 * b], s->L_fx)) * inv_S;
+            U += s->bond_k[t] * (r - s->bond_d[t]) * (r - s->bond_d[t]);
+        }
+    return U;
+}
+
 /* Total potential energy: sum over all pairs of atoms in different molecules (the
- * intra-molecular terms of rigid molecules are constant and left out, reading c2). */
+ * intra-molecular terms of rigid molecules are constant and left out, reading c2), plus
+ * the intra-molecular springs of flexible molecules. */
 double orc_total_energy(const orc_system *s)
 {
     double U = 0.0;
@@ -162,6 +183,9 @@ double orc_total_energy(const orc_system *s)
             U += orc_pair_energy(s, s->type[i], s->type[j],
                                  orc_dist2_points(&s->xyz[3 * i], &s->xyz[3 * j], s->L_fx));
     }
+    if (s->flexible)
+        for (int64_t mol = 0; mol < s->n_mol; ++mol)
+            U += orc_intra_energy(s, mol, &s->xyz[3 * s->mol_start[mol]]);
     return U;
 }
 
@@ -219,9 +243,9 @@ void orc_rotation_fixed(double vx, double vy, double vz, int32_t Rq[9])
 void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box_index,
                  int64_t *mol_out, int32_t *trial, double *u_acc)
 {
-    uint32_t w[12];
+    uint32_t w[16];
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    for (uint32_t lane = 0; lane < 3; ++lane) {
+    for (uint32_t lane = 0; lane < (s->flexible ? 4u : 3u); ++lane) {
         const uint32_t ctr[4] = {(uint32_t)move, (uint32_t)(move >> 32), box_index, lane};
         orc_philox4x32_10(ctr, key, &w[4 * lane]);
     }
@@ -233,7 +257,17 @@ void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box
         shift[a] = (int64_t)(w[1 + a] % (uint32_t)(2 * M + 1)) - M;
     const int64_t a0 = s->mol_start[mol], m = s->mol_start[mol + 1] - a0;
     const int64_t L = s->L_fx;
-    if (s->rigid) {
+    /* Flexible molecules (Sec. 3.1: molecule translation, molecule rotation, or the
+     * translation of one atom): kind = w12 mod 3, the atom = w13 mod m (reading r6). */
+    const int kind = s->flexible ? (int)(w[12] % 3u) : -1;
+    if (kind == 0 || kind == 2) {
+        for (int64_t k = 0; k < m; ++k) {
+            const int moved = kind == 0 || k == (int64_t)(w[13] % (uint32_t)m);
+            for (int a = 0; a < 3; ++a)
+                trial[3 * k + a] = (int32_t)wrap((int64_t)s->xyz[3 * (a0 + k) + a] + (moved ? shift[a] : 0), L);
+        }
+    } else if (s->rigid || kind == 1) {
+        if (kind == 1) shift[0] = shift[1] = shift[2] = 0;
         const double pi = 3.14159265358979323846;
         const double h = tan(0.5 * s->max_rotation_deg * pi / 180.0) / sqrt(3.0);
         int32_t Rq[9];
@@ -268,7 +302,8 @@ void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box
 
 /* Energy change of moving molecule `mol` to `trial` (Sec. 2.2 item III:
  * dU = U_after - U_before; Sec. 2.3: it needs the moved molecule against all atoms).
- * Pairs inside the molecule are left out (reading c2). cond (optional) receives the
+ * Non-bonded pairs inside the molecule are left out (reading c2); for flexible molecules
+ * the change of the intra-molecular springs is added (Sec. 3.1, reading r6). cond (optional) receives the
  * condition scale sum |u(new) - u(old)| over the same pairs. */
 double orc_delta_u(const orc_system *s, int64_t mol, const int32_t *trial, double *cond)
 {
@@ -286,6 +321,11 @@ double orc_delta_u(const orc_system *s, int64_t mol, const int32_t *trial, doubl
             dU += un - uo;
             C += fabs(un - uo);
         }
+    }
+    if (s->flexible) {
+        const double di = orc_intra_energy(s, mol, trial) - orc_intra_energy(s, mol, &s->xyz[3 * a0]);
+        dU += di;
+        C += fabs(di);
     }
     if (cond) *cond = C;
     return dU;

@@ -37,6 +37,10 @@ typedef struct {
     int32_t bin_p, bin_q;      /* bin width p/q Angstrom */
     int32_t n_bins;
     int32_t rigid;             /* 1: molecule rotation + translation, 0: translation only */
+    int32_t flexible;          /* 1: flexible molecules (Sec. 3.1): springs between every two
+                                  atoms of a molecule, moves = translation, rotation or one atom */
+    double bond_k[ORC_MAX_TYPES * ORC_MAX_TYPES];  /* spring constant k_ab, kJ/mol/A^2 */
+    double bond_d[ORC_MAX_TYPES * ORC_MAX_TYPES];  /* reference distance d_ab, A */
     double temperature;        /* K */
     double max_translation;    /* A */
     double max_rotation_deg;
@@ -63,6 +67,7 @@ int32_t orc_pair_index(int32_t a, int32_t b, int32_t n_types);
 
 double orc_pair_energy(const orc_system *s, int32_t ta, int32_t tb, int64_t d2);
 double orc_total_energy(const orc_system *s);
+double orc_intra_energy(const orc_system *s, int64_t mol, const int32_t *xyz_mol);
 void orc_rotation_fixed(double vx, double vy, double vz, int32_t Rq[9]);
 void orc_propose(const orc_system *s, uint64_t seed, uint64_t move, uint32_t box_index,
                  int64_t *mol, int32_t *trial /* [m][3] */, double *u_acc);

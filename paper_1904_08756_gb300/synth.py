@@ -55,6 +55,9 @@ class System:
     max_rotation_deg: float = 5.0
     Q: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     seed: int = 0
+    flexible: bool = False           # springs between every two atoms of a molecule (bond_k, bond_d)
+    bond_k: list | None = None       # [n_types][n_types] spring constant (kJ/mol/A^2)
+    bond_d: list | None = None       # [n_types][n_types] reference distance (A)
 
     @property
     def n_atoms(self) -> int:
@@ -297,6 +300,19 @@ def water_lattice(n_mol: int, seed: int, density: float = 0.1) -> System:
     return System(**{**base.__dict__, "L_fx": L_fx, "xyz": xyz.astype(np.int32),
                      "type": np.tile(np.array([0, 1, 1], np.int32), n_mol),
                      "mol_start": np.arange(0, n_atoms + 1, 3, dtype=np.int64), "seed": seed})
+
+
+def flexible_water_box(n_mol: int, seed: int, L_A: float | None = None, k_spring: float = 2000.0,
+                       density: float = 0.1) -> System:
+    """Flexible 3-site water: the placement, potentials and bins of water_box, with the
+    molecule held together by springs k (r - d)^2 between every two of its atoms (O-H with
+    d = 1.0 A, H-H with d = the reference H-H distance) instead of being rigid; moves are
+    molecule translations, molecule rotations and single-atom translations."""
+    base = water_box(n_mol, seed=seed, L_A=L_A, density=density)
+    d_hh = 2.0 * _SIN_HALF_HOH
+    return System(**{**base.__dict__, "name": "flexible water", "rigid_molecules": False, "flexible": True,
+                     "bond_k": [[0.0, k_spring], [k_spring, k_spring]],
+                     "bond_d": [[0.0, 1.0], [1.0, d_hh]]})
 
 
 def silica_box(n_si: int, seed: int, density: float = 0.0662, n_bins: int = 600,

@@ -521,3 +521,98 @@ def test_rotation_matrix_against_scipy():
         L.orc_rotation_fixed(v[0], v[1], v[2], Rq.ctypes.data_as(C.POINTER(C.c_int32)))
         ref = Rotation.from_quat([v[0], v[1], v[2], 1.0]).as_matrix()   # scalar-last
         assert np.abs(Rq.reshape(3, 3) / 2.0 ** 30 - ref).max() <= 2.0 ** -30 + 1e-15
+
+
+# --------------------------------------------------------------------------------------
+# flexible molecules (Sec. 3.1: springs between every two atoms; three kinds of moves)
+# --------------------------------------------------------------------------------------
+
+def _one_molecule(xyz_A, k=2000.0, L_A=20.0):
+    """A single flexible water molecule (O, H, H) at the given positions (A)."""
+    s = synth.flexible_water_box(1, seed=0, L_A=L_A, k_spring=k)
+    s.xyz = np.rint(np.asarray(xyz_A) * S).astype(np.int32) % s.L_fx
+    return s
+
+
+def test_intra_energy_scales_quadratically():
+    """Scaling the reference geometry by lambda about O scales every distance: the spring
+    energy is (lambda - 1)^2 k (d_OH^2 + d_OH^2 + d_HH^2), zero at lambda = 1."""
+    g = synth.water_geometry_A() + 5.0
+    d_hh = 2.0 * 0.8164904309201172
+    for lam in (1.0, 1.01, 0.97, 1.05):
+        xyz = g[0] + lam * (g - g[0])
+        box = oracle.Box(_one_molecule(xyz))
+        expect = (lam - 1.0) ** 2 * 2000.0 * (1.0 + 1.0 + d_hh * d_hh)
+        assert abs(box.total_energy() - expect) <= 1e-3 * max(expect, 1e-3), (lam, box.total_energy(), expect)
+
+
+def test_flexible_delta_u_equals_total_energy_difference():
+    s = synth.flexible_water_box(60, seed=3, L_A=12.0)
+    box = oracle.Box(s)
+    for t in range(60):
+        mol, trial, u = box.propose(7, t)
+        dU, C = box.delta_u(mol, trial)
+        U0 = box.total_energy()
+        saved = box.xyz.copy()
+        box.apply(mol, trial)
+        U1 = box.total_energy()
+        box.xyz[:] = saved
+        assert abs(dU - (U1 - U0)) <= 1e-9 * max(1.0, abs(U0)), (t, dU, U1 - U0)
+        assert C >= abs(dU) - 1e-12
+
+
+def test_flexible_move_kinds():
+    """Each move is one of: all atoms shifted by one vector, a rotation (every atom moves,
+    the centre stays within grid rounding), or exactly one atom shifted; the three kinds
+    occur about equally often."""
+    s = synth.flexible_water_box(50, seed=4, L_A=12.0)
+    box = oracle.Box(s)
+    L = s.L_fx
+    seen = {"translate": 0, "rotate": 0, "atom": 0}
+    for t in range(1500):
+        mol, trial, u = box.propose(13, t)
+        old = s.xyz[3 * mol:3 * mol + 3].astype(np.int64)
+        d = trial.astype(np.int64) - old
+        d = np.where(2 * d > L, d - L, np.where(2 * d <= -L, d + L, d))
+        moved = (d != 0).any(axis=1)
+        if moved.sum() <= 1:
+            seen["atom"] += 1
+            assert np.abs(d).max() <= round(0.1 * S)
+        elif (d == d[0]).all():
+            seen["translate"] += 1
+        else:
+            seen["rotate"] += 1
+            assert np.abs(d.mean(axis=0)).max() <= 2
+    for k, v in seen.items():
+        assert abs(v - 500) < 4 * math.sqrt(1500 * (1 / 3) * (2 / 3)), seen
+
+
+def test_spring_boltzmann_distribution():
+    """One flexible two-atom molecule (no non-bonded terms) sampled by Metropolis: the bond
+    length density is proportional to r^2 exp(-k (r - d)^2 / kT) (chi^2 test over bins)."""
+    k = 200.0
+    base = synth.flexible_water_box(1, seed=0, L_A=30.0, k_spring=k)
+    s = synth.System(**{**base.__dict__,
+                        "xyz": (np.rint(np.array([[5.0, 5.0, 5.0], [6.0, 5.0, 5.0]]) * S)).astype(np.int32),
+                        "type": np.array([0, 1], np.int32), "mol_start": np.array([0, 2], np.int64),
+                        "q": [0.0, 0.0], "eps": [0.0, 0.0], "temperature": 300.0})
+    box = oracle.Box(s)
+    L = s.L_fx
+    edges = np.linspace(0.75, 1.25, 16)
+    counts = np.zeros(len(edges) - 1)
+    for blk in range(600):
+        box.mc_sweep(60, seed=9, move0=blk * 60)
+        d = box.xyz[1].astype(np.int64) - box.xyz[0].astype(np.int64)
+        d = np.where(2 * d > L, d - L, np.where(2 * d <= -L, d + L, d))
+        r = math.sqrt(float((d * d).sum())) / S
+        j = np.searchsorted(edges, r) - 1
+        if 0 <= j < len(counts):
+            counts[j] += 1
+    kT = oracle.gas_constant() * 300.0
+    r = np.linspace(edges[0], edges[-1], 20001)
+    dens = r * r * np.exp(-k * (r - 1.0) ** 2 / kT)
+    expect = np.array([np.trapezoid(dens[(r >= a) & (r <= b)], r[(r >= a) & (r <= b)])
+                       for a, b in zip(edges[:-1], edges[1:])])
+    expect *= counts.sum() / expect.sum()
+    chi2 = float(((counts - expect) ** 2 / np.maximum(expect, 1)).sum())
+    assert chi2 < 50.0, (chi2, counts, expect)
