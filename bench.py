@@ -101,7 +101,8 @@ def dist_env():
 
 def workload_name(system, moves: int) -> str:
     m = int(system.mol_start[1] - system.mol_start[0])
-    kind = (f"{system.n_mol} rigid {m}-site molecules" if m > 1 else "single-atom moves")
+    kind = ((f"{system.n_mol} flexible {m}-site molecules" if getattr(system, "flexible", False)
+             else f"{system.n_mol} rigid {m}-site molecules") if m > 1 else "single-atom moves")
     return (f"paper-scale {system.name}, {system.n_atoms:,} atoms ({kind}), {moves:,} MC moves + full "
             f"g_ab(r) ({system.n_bins} x {system.dr:g} A) + S(Q) ({len(system.Q)} Q) per step")
 
@@ -441,9 +442,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water", choices=["water", "silica", "replicas", "sweep", "smeared"],
+    ap.add_argument("--workload", default="water", choices=["water", "silica", "flexible", "replicas", "sweep", "smeared"],
                     help="water: the paper-scale water box (default line); silica: the paper-scale "
-                         "SiO2 box with single-atom moves; replicas: 64 uneven boxes; sweep: MC "
+                         "SiO2 box with single-atom moves; flexible: the water box with flexible "
+                         "molecules (springs, three kinds of moves); replicas: 64 uneven boxes; sweep: MC "
                          "moves/s at the paper's Table 1 atom counts; smeared: chi^2 and gradients of "
                          "the differentiable form")
     ap.add_argument("--max-atoms", type=int, default=0, help="sweep: largest atom count (0: all)")
@@ -473,7 +475,12 @@ def main():
     if not os.path.exists(epsr.LIB_PATH):
         build.build()
 
-    system = synth.paper_silica(seed=2 + rank) if args.workload == "silica" else synth.paper_water(seed=1 + rank)
+    if args.workload == "silica":
+        system = synth.paper_silica(seed=2 + rank)
+    elif args.workload == "flexible":
+        system = synth.flexible_water_box(33333, seed=1 + rank)
+    else:
+        system = synth.paper_water(seed=1 + rank)
     N = system.n_atoms
     m_atoms = int(system.mol_start[1] - system.mol_start[0])
     moves = args.moves

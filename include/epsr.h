@@ -56,6 +56,9 @@ typedef struct CUstream_st *epsr_stream_t; /* same object as cudaStream_t */
 
 #define EPSR_MOVE_ATOM 0            /* translate one atom (single-atom molecules) */
 #define EPSR_MOVE_RIGID_MOLECULE 1  /* rotate then translate one rigid molecule */
+#define EPSR_MOVE_FLEXIBLE_MOLECULE 2  /* Sec. 3.1: springs k_ab (r - d_ab)^2 between every two atoms
+                                          of a molecule; each move translates the molecule, rotates
+                                          it, or translates one of its atoms (one third each) */
 
 #define EPSR_SQ_FP32 0    /* CUDA-core FP32 contraction */
 #define EPSR_SQ_TF32X3 1  /* tensor cores (tcgen05), TF32 hi/lo split, 3 products */
@@ -82,10 +85,15 @@ typedef struct {
     double r_coul;            /* Coulomb cutoff (A) */
     int32_t bin_p, bin_q;     /* bin width = bin_p / bin_q Angstrom */
     int32_t n_bins;           /* 1 .. EPSR_MAX_BINS */
-    int32_t move_kind;        /* EPSR_MOVE_ATOM or EPSR_MOVE_RIGID_MOLECULE */
+    int32_t move_kind;        /* EPSR_MOVE_ATOM, _RIGID_MOLECULE or _FLEXIBLE_MOLECULE */
     double temperature;       /* K */
     double max_translation;   /* A, per axis */
     double max_rotation_deg;  /* rigid-molecule rotation limit */
+    /* EPSR_MOVE_FLEXIBLE_MOLECULE only: spring constant (kJ/mol/A^2) and reference distance
+     * (A) of the intra-molecular spring between atoms of types a and b, at [a * EPSR_MAX_TYPES
+     * + b] (symmetric; k = 0: no spring). Non-bonded terms inside a molecule are left out. */
+    double bond_k[EPSR_MAX_TYPES * EPSR_MAX_TYPES];
+    double bond_d[EPSR_MAX_TYPES * EPSR_MAX_TYPES];
 } epsr_box_desc;
 
 typedef struct epsr_box epsr_box;   /* opaque: one box or a batch of boxes */
@@ -169,7 +177,8 @@ int epsr_box_get_ep(epsr_box *box, int32_t b, float *ep, epsr_stream_t stream);
 
 /* Total potential energy of every box from scratch (Sec. 2.2 item III defines dU as
  * U_after - U_before; this is U): sum over all pairs of atoms in different molecules
- * of the pair energy, FP32 per pair, FP64 accumulation. U_host [n_boxes]. Synchronises. */
+ * of the pair energy, FP32 per pair, FP64 accumulation, plus (flexible molecules) the
+ * intra-molecular springs in FP64. U_host [n_boxes]. Synchronises. */
 int epsr_box_total_energy(epsr_box *box, double *U_host, epsr_stream_t stream);
 
 /* ---- Monte Carlo (Sec. 2.2 item III; Sec. 2.3: dU from the moved molecule against

@@ -197,8 +197,17 @@ static int validate_desc(const epsr_box_desc &d, int b)
         return set_error(EPSR_EINVAL, "box %d: n_types %d out of range", b, d.n_types);
     if (d.bin_p < 1 || d.bin_q < 1 || d.n_bins < 1 || d.n_bins > EPSR_MAX_BINS)
         return set_error(EPSR_EINVAL, "box %d: bins (%d/%d, %d) invalid", b, d.bin_p, d.bin_q, d.n_bins);
-    if (d.move_kind != EPSR_MOVE_ATOM && d.move_kind != EPSR_MOVE_RIGID_MOLECULE)
+    if (d.move_kind != EPSR_MOVE_ATOM && d.move_kind != EPSR_MOVE_RIGID_MOLECULE &&
+        d.move_kind != EPSR_MOVE_FLEXIBLE_MOLECULE)
         return set_error(EPSR_EINVAL, "box %d: move_kind %d invalid", b, d.move_kind);
+    if (d.move_kind == EPSR_MOVE_FLEXIBLE_MOLECULE)
+        for (int a = 0; a < d.n_types; ++a)
+            for (int c = 0; c < d.n_types; ++c) {
+                const double k = d.bond_k[a * EPSR_MAX_TYPES + c], r0 = d.bond_d[a * EPSR_MAX_TYPES + c];
+                if (!(k >= 0) || !std::isfinite(k) || !(r0 >= 0) || !std::isfinite(r0) ||
+                    k != d.bond_k[c * EPSR_MAX_TYPES + a] || r0 != d.bond_d[c * EPSR_MAX_TYPES + a])
+                    return set_error(EPSR_EINVAL, "box %d: spring of types %d-%d invalid or not symmetric", b, a, c);
+            }
     if (!(d.temperature > 0) || !(d.max_translation >= 0) || !(d.max_rotation_deg >= 0) ||
         !(d.max_rotation_deg < 180) || !(d.r_coul >= 0))
         return set_error(EPSR_EINVAL, "box %d: temperature/move/cutoff parameters invalid", b);
@@ -243,6 +252,11 @@ static void fill_boxdev(const epsr_box_desc &d, const int *type, BoxDev &b)
     b.rc2 = rc * rc;
     const double pi = 3.14159265358979323846;
     b.h_rot = std::tan(0.5 * d.max_rotation_deg * pi / 180.0) / std::sqrt(3.0);
+    if (d.move_kind == EPSR_MOVE_FLEXIBLE_MOLECULE)
+        for (int i = 0; i < EPSR_MAX_TYPES * EPSR_MAX_TYPES; ++i) {
+            b.bond_k[i] = d.bond_k[i];
+            b.bond_d[i] = d.bond_d[i];
+        }
     b.kT = gas_r() * d.temperature;
     const double LA = (double)d.L_fx / S;
     b.volume = LA * LA * LA;
@@ -669,6 +683,10 @@ extern "C" int epsr_box_total_energy(epsr_box *box, double *U_host, epsr_stream_
     int rc = launch_total_energy(box->boxes, box->coords, box->atom_mol, box->thresholds, box->ep,
                                  box->tiles, (long long)box->tiles_h.size(), box->U, box->sms * 2, s);
     if (rc) return rc;
+    bool flexible = false;
+    for (const auto &b : box->hb) flexible |= b.move_kind == EPSR_MOVE_FLEXIBLE_MOLECULE;
+    if (flexible && (rc = launch_intra_energy(box->boxes, box->n_boxes, box->coords, box->mol_start, box->U, s)))
+        return rc;
     CK(cudaMemcpyAsync(U_host, box->U, box->n_boxes * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return EPSR_OK;
@@ -731,11 +749,11 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
     int types_cap = 1;
     for (auto &b : box->hb) types_cap = std::max(types_cap, b.n_types);
-    // shared memory: thresholds, EP table, cell index [types][513] (uint32), and, when they
+    // shared memory: thresholds, EP table, cell index [types][513] (uint32), correction items, and, when they
     // fit, the partner slice (int4 per slot) and the home cell of every slot (uint16);
     // otherwise the slices and home cells live in global memory
     const size_t tables = (size_t)box->tbl_cap * sizeof(long long) + (size_t)box->ep_cap * sizeof(float) +
-                          (size_t)types_cap * (kMcCells + 1) * sizeof(unsigned);
+                          (size_t)types_cap * (kMcCells + 1) * sizeof(unsigned) + (size_t)kMcCorrItems * sizeof(float);
     const size_t per_slot = sizeof(int4) + sizeof(unsigned short);
     size_t smem = (((size_t)slice_cap * per_slot + tables) + 15) & ~(size_t)15;
     const bool gslice = smem > kMcMaxDynSmem;

@@ -60,6 +60,9 @@ struct BoxDev {
     int32_t type_start[kMaxTypes];  // first type-major sorted position of each type (box-local)
     int64_t count[kMaxTypes];   // atoms per type
     PairRow row[kMaxTypes * kMaxTypes];
+    // flexible molecules: intra-molecular spring constant and reference distance per type pair
+    double bond_k[kMaxTypes * kMaxTypes];
+    double bond_d[kMaxTypes * kMaxTypes];
 };
 
 __host__ __device__ __forceinline__ int pair_index(int a, int b, int n_types)
@@ -274,7 +277,8 @@ struct __align__(16) MoveRec {
     float thr;       // FP32 rounded up from -kT ln u_acc
     double u_acc;
     int a0, m;       // first atom (box-local) and atom count of the molecule
-    int pad[2];
+    int kind;        // 0 translate every atom, 1 rotate (and translate), 2 translate atom `atom`
+    int atom;
 };
 
 // ---- device status word ------------------------------------------------------------------

@@ -20,10 +20,12 @@ int set_cuda_error(cudaError_t e, const char *what);
 void note_launch();
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
-constexpr size_t kMcMaxDynSmem = 176 * 1024;   // with ~48 KB static: under the 227 KB per CTA
+constexpr size_t kMcMaxDynSmem = 192 * 1024;   // with ~33 KB static: under the 227 KB per CTA
 // per-CTA barrier slot: the batch's partial dU (32 moves), then the pair-energy corrections
 // this CTA computed (at most 32 * 31 / 2 = 496 pairs)
 constexpr int kMcSlotStride = 32 + 496;
+// correction items of one batch in shared memory (>= 496 pairs x 8 atoms)
+constexpr int kMcCorrItems = 4096;
 
 struct McArgs {
     const BoxDev *boxes;
@@ -65,6 +67,8 @@ int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stre
 int launch_mc_moves(const BoxDev *boxes, const int *mol_start, int n_boxes, long long chunk,
                     long long n, unsigned long long seed, unsigned long long move0, MoveRec *out,
                     cudaStream_t stream);
+int launch_intra_energy(const BoxDev *boxes, int n_boxes, const int4 *coords, const int *mol_start, double *U,
+                        cudaStream_t stream);
 int mc_threads();
 int micro_barrier_floor(int ctas, int iters, double timeout_ms, double *ns_per_barrier, cudaStream_t stream);
 int micro_alu_rate(int kind, double *lane_ops_per_s, cudaStream_t stream);

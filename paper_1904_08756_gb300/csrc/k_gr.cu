@@ -638,4 +638,34 @@ int launch_total_energy(const BoxDev *boxes, const int4 *coords, const int *atom
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "total_energy launch");
 }
 
+// Intra-molecular springs of flexible molecules (added to the total energy): one thread per
+// molecule of box blockIdx.y, FP64.
+__global__ void intra_energy_kernel(const BoxDev *boxes, const int4 *coords, const int *mol_start, double *U)
+{
+    const BoxDev &bx = boxes[blockIdx.y];
+    if (bx.move_kind != EPSR_MOVE_FLEXIBLE_MOLECULE) return;
+    double e = 0.0;
+    for (int mol = blockIdx.x * blockDim.x + threadIdx.x; mol < bx.n_mol; mol += gridDim.x * blockDim.x) {
+        const int a0 = mol_start[bx.mol0 + mol], a1 = mol_start[bx.mol0 + mol + 1];
+        for (int i = a0; i < a1; ++i)
+            for (int j = i + 1; j < a1; ++j) {
+                const int4 pi = coords[bx.atom0 + i], pj = coords[bx.atom0 + j];
+                const int t = pi.w * kMaxTypes + pj.w;
+                if (bx.bond_k[t] == 0.0) continue;
+                const double r = sqrt((double)dist2(pi, pj, bx.L) * (double)bx.inv_s2);
+                e += bx.bond_k[t] * (r - bx.bond_d[t]) * (r - bx.bond_d[t]);
+            }
+    }
+    if (e != 0.0) atomicAdd(&U[blockIdx.y], e);
+}
+
+int launch_intra_energy(const BoxDev *boxes, int n_boxes, const int4 *coords, const int *mol_start, double *U,
+                        cudaStream_t stream)
+{
+    intra_energy_kernel<<<dim3(64, n_boxes), 256, 0, stream>>>(boxes, coords, mol_start, U);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "intra energy");
+}
+
 }  // namespace epsr

@@ -33,7 +33,7 @@ constexpr int kMcThreads = 512;
 constexpr int kMcWarps = kMcThreads / 32;
 constexpr int kBatchMax = 32;                  // moves per batch: warp w takes moves w and w + 16
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
-constexpr int kCorrItems = 4096;               // >= 496 pairs x 8 atoms (coarse items at G = 1)
+constexpr int kCorrItems = kMcCorrItems;       // >= 496 pairs x 8 atoms (coarse items at G = 1)
 constexpr int kEscMax = 256;                   // escapee list capacity per CTA (at most)
 constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
 static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
@@ -51,9 +51,11 @@ __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n
         if (t >= n) continue;
         const BoxDev &bx = boxes[b];
         const unsigned long long mv = move0 + (unsigned long long)t;
-        uint32_t w[12];
+        const bool flex = bx.move_kind == EPSR_MOVE_FLEXIBLE_MOLECULE;
+        uint32_t w[16];
 #pragma unroll
-        for (int lane = 0; lane < 3; ++lane) {
+        for (int lane = 0; lane < 4; ++lane) {
+            if (lane == 3 && !flex) break;
             const U32x4 r = philox4x32_10((uint32_t)mv, (uint32_t)(mv >> 32), (uint32_t)b,
                                           (uint32_t)lane, (uint32_t)seed, (uint32_t)(seed >> 32));
 #pragma unroll
@@ -65,7 +67,13 @@ __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n
         m.m = mol_start[bx.mol0 + m.mol + 1] - m.a0;
         const unsigned span = 2u * (unsigned)bx.max_shift + 1u;
         for (int a = 0; a < 3; ++a) m.shift[a] = (int)(w[1 + a] % span) - bx.max_shift;
-        if (bx.move_kind == EPSR_MOVE_RIGID_MOLECULE) {
+        // kind: 0 translate every atom, 1 rotate about the centre (then translate, for rigid
+        // molecules), 2 translate one atom; flexible molecules draw the kind from w12 and the
+        // atom from w13, and their rotations are not translated
+        m.kind = flex ? (int)(w[12] % 3u) : (bx.move_kind == EPSR_MOVE_RIGID_MOLECULE ? 1 : 0);
+        m.atom = flex ? (int)(w[13] % (uint32_t)m.m) : 0;
+        if (flex && m.kind == 1) m.shift[0] = m.shift[1] = m.shift[2] = 0;
+        if (m.kind == 1) {
             const double vx = __dmul_rn(bx.h_rot, __dsub_rn(__dmul_rn(2.0, uniform53(w[4], w[5])), 1.0));
             const double vy = __dmul_rn(bx.h_rot, __dsub_rn(__dmul_rn(2.0, uniform53(w[6], w[7])), 1.0));
             const double vz = __dmul_rn(bx.h_rot, __dsub_rn(__dmul_rn(2.0, uniform53(w[8], w[9])), 1.0));
@@ -118,7 +126,7 @@ struct McShared {
     double u_acc[kBatchMax];
     float part[kBatchMax];
     float base[kBatchMax];
-    float corr_part[kCorrItems];
+    float intra[kBatchMax];                 // flexible molecules: change of the springs
     int mm;                                  // largest molecule of the batch
     MoveRec mv[kMoveBlock];                  // staged move records [mv_base, mv_base + kMoveBlock)
     float acc_du[kMoveBlock];                // rank 0: dU of each decided move if accepted, else 0
@@ -429,7 +437,6 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     const int rank = cta - bx.cta0;
     const int L = bx.L;
     const int nt = bx.n_types;
-    const bool rigid = bx.move_kind == EPSR_MOVE_RIGID_MOLECULE;
     // Partners of this CTA: the atoms i of the box with i mod G == rank (an even share of
     // every region and type), grouped by type and ordered in space within each type.
     if (tid == 0) {
@@ -466,8 +473,9 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     // home cell of every slot, cell boundaries; cell queries only where some pair row has
     // no Lennard-Jones term but a Coulomb or empirical-potential one
     unsigned *cst = reinterpret_cast<unsigned *>(ep + A.ep_cap);
+    float *corr_part = reinterpret_cast<float *>(cst + A.types_cap * (kMcCells + 1));   // [kCorrItems]
     unsigned short *home = GSLICE ? A.home_g + (size_t)cta * A.slice_cap
-                                  : reinterpret_cast<unsigned short *>(cst + A.types_cap * (kMcCells + 1));
+                                  : reinterpret_cast<unsigned short *>(corr_part + kCorrItems);
     for (int t = 0; t < nt; ++t) {
         const int key0 = bx.mc_cell0 + (t * G + rank) * kMcCells;
         for (int c = tid; c <= kMcCells; c += kMcThreads)
@@ -553,7 +561,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 const int kk = lane / 3, a = lane - 3 * kk;
                 const int4 *op = sh.oldp[k];
                 int coord;
-                if (rigid) {
+                if (mr.kind == 1) {
                     const int base[3] = {op[0].x, op[0].y, op[0].z};
                     long long sum[3] = {0, 0, 0}, mine[3] = {0, 0, 0};
                     for (int i = 0; i < m; ++i) {
@@ -571,13 +579,32 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     coord = wrap_coord((long long)base[a] + floordiv32(hi, m) + mr.shift[a], L);
                 } else {
                     const int c[3] = {op[kk].x, op[kk].y, op[kk].z};
-                    coord = wrap_coord((long long)c[a] + mr.shift[a], L);
+                    const bool moved = mr.kind != 2 || kk == mr.atom;
+                    coord = wrap_coord((long long)c[a] + (moved ? mr.shift[a] : 0), L);
                 }
                 int *dst = reinterpret_cast<int *>(&sh.newp[par][k][kk]);
                 dst[a] = coord;
                 if (a == 0) dst[3] = op[kk].w;
             }
+            __syncwarp();
             if (lane == 0) {
+                // flexible molecules: change of the intra-molecular springs, written without
+                // cancellation: k[(r' - d)^2 - (r - d)^2] = k (r' - r)(r' + r - 2d), with
+                // r' - r = (r'^2 - r^2) / (r' + r) from the exact integer squared distances
+                float di = 0.f;
+                if (bx.move_kind == EPSR_MOVE_FLEXIBLE_MOLECULE)
+                    for (int i = 0; i < m; ++i)
+                        for (int j = i + 1; j < m; ++j) {
+                            const int4 ni = sh.newp[par][k][i], nj = sh.newp[par][k][j];
+                            const int t = ni.w * kMaxTypes + nj.w;
+                            if (bx.bond_k[t] == 0.0) continue;
+                            const long long d2n = dist2(ni, nj, L), d2o = dist2(sh.oldp[k][i], sh.oldp[k][j], L);
+                            if (d2n == d2o) continue;
+                            const float rn = sqrtf((float)d2n * bx.inv_s2), ro = sqrtf((float)d2o * bx.inv_s2);
+                            const float dr = (float)(d2n - d2o) * bx.inv_s2 / (rn + ro);
+                            di = fmaf((float)bx.bond_k[t] * dr, rn + ro - 2.f * (float)bx.bond_d[t], di);
+                        }
+                sh.intra[k] = di;
                 atomicMax(&sh.mm, m);
                 sh.natoms[k] = m;
                 sh.a0[k] = a0;
@@ -621,7 +648,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     const int4 p1 = side ? sh.oldp[k1][b] : sh.newp[par][k1][b];
                     v = pair_du_cold(sep(na, p1, L), sep(oa, p1, L), bx.row[na.w * kMaxTypes + p1.w], bx, T, ep);
                 }
-                sh.corr_part[it] = v;
+                corr_part[it] = v;
             }
         } else {                                  // large molecules and few CTAs: items (pair, a)
             for (int it = tid; it < n_local * mm; it += kMcThreads) {
@@ -639,7 +666,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                               pair_du_cold(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
                     }
                 }
-                sh.corr_part[it] = ca;
+                corr_part[it] = ca;
             }
         }
         const bool fine = n_items <= kCorrItems;
@@ -681,7 +708,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 float *slot = A.slots + ((size_t)(seq & 1u) * A.grid + cta) * kMcSlotStride;
                 if (cta != A.skip_arrival_cta) {
                     for (int k = 0; k < nb; ++k) slot[k] = sh.part[k];
-                    for (int u = 0; u < n_local; ++u) slot[kBatchMax + u] = corr_sum(sh.corr_part, u, mm, fine);
+                    for (int u = 0; u < n_local; ++u) slot[kBatchMax + u] = corr_sum(corr_part, u, mm, fine);
                     red_add_release_gpu(&A.flags[box], 1u);
                 }
                 const unsigned target = seq * (unsigned)G;
@@ -722,13 +749,13 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 int k = 1;
                 while ((k + 1) * k / 2 <= pq) ++k;
-                sh.corr[pq - k * (k - 1) / 2][k] = corr_sum(sh.corr_part, pq, mm, fine);
+                sh.corr[pq - k * (k - 1) / 2][k] = corr_sum(corr_part, pq, mm, fine);
             }
         }
         __syncthreads();
         // ---- F. Metropolis decisions of the batch, in order (warp 0, lane k = move k) -------
         if (warp == 0) {
-            float d = lane < nb ? sh.base[lane] : 0.f;
+            float d = lane < nb ? sh.base[lane] + sh.intra[lane] : 0.f;
             const float thr = lane < nb ? sh.thr[lane] : 0.f;
             float cj[kBatchMax];
 #pragma unroll

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libepsr.so")
 EPSR_OK, EPSR_EINVAL, EPSR_ENOMEM, EPSR_ECUDA, EPSR_ELAUNCH, EPSR_ETIMEOUT, EPSR_ENUMERIC = range(7)
 MAX_TYPES = 8
 MAX_MOL_ATOMS = 8
-MOVE_ATOM, MOVE_RIGID_MOLECULE = 0, 1
+MOVE_ATOM, MOVE_RIGID_MOLECULE, MOVE_FLEXIBLE_MOLECULE = 0, 1, 2
 SQ_FP32, SQ_TF32X3, SQ_BF16X3, SQ_BF16X6 = 0, 1, 2, 3
 
 # Every symbol include/epsr.h declares (checked by the CPU test suite).
@@ -47,7 +47,9 @@ class BoxDesc(C.Structure):
                 ("eps", C.c_double * MAX_TYPES), ("b", C.c_double * MAX_TYPES),
                 ("r_coul", C.c_double), ("bin_p", C.c_int32), ("bin_q", C.c_int32),
                 ("n_bins", C.c_int32), ("move_kind", C.c_int32), ("temperature", C.c_double),
-                ("max_translation", C.c_double), ("max_rotation_deg", C.c_double)]
+                ("max_translation", C.c_double), ("max_rotation_deg", C.c_double),
+                ("bond_k", C.c_double * (MAX_TYPES * MAX_TYPES)),
+                ("bond_d", C.c_double * (MAX_TYPES * MAX_TYPES))]
 
 
 class McStats(C.Structure):
@@ -180,6 +182,12 @@ def box_desc(system) -> BoxDesc:
     d.r_coul = system.r_coul
     d.bin_p, d.bin_q, d.n_bins = system.bin_p, system.bin_q, system.n_bins
     d.move_kind = MOVE_RIGID_MOLECULE if system.rigid_molecules else MOVE_ATOM
+    if getattr(system, "flexible", False):
+        d.move_kind = MOVE_FLEXIBLE_MOLECULE
+        for a in range(system.n_types):
+            for b in range(system.n_types):
+                d.bond_k[a * MAX_TYPES + b] = float(system.bond_k[a][b])
+                d.bond_d[a * MAX_TYPES + b] = float(system.bond_d[a][b])
     d.temperature = system.temperature
     d.max_translation = system.max_translation
     d.max_rotation_deg = system.max_rotation_deg

@@ -197,6 +197,34 @@ def test_mc_replay_small_water(small_water, batch):
     assert abs(sdu - float(log[0]["dU"][log[0]["accepted"] == 1].astype(np.float64).sum())) < 1e-6 * max(1, abs(sdu))
 
 
+@pytest.mark.parametrize("batch", [0, 16, 1])
+def test_mc_replay_flexible_water(batch):
+    """Flexible water (Sec. 3.1): molecule translations, rotations and single-atom moves,
+    springs between every two atoms of a molecule; trial coordinates bit-exact, dU within
+    tolerance (the spring change is FP64 on both sides), final coordinates bit-exact."""
+    s = synth.flexible_water_box(300, seed=5, L_A=20.8)
+    box = epsr.Box(s)
+    box.epsr_mc_set_batch(batch)
+    U0 = box.epsr_box_total_energy()[0]
+    stats, log = run_logged(box, 2000, seed=4242)
+    att, acc, nonfin, sdu = stats[0]
+    assert att == 2000 and nonfin == 0 and 0 < acc < 2000
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 4242)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+    assert flips <= 2
+    U1 = box.epsr_box_total_energy()[0]
+    assert abs(U1 - ob.total_energy()) <= 1e-5 * abs(U1) + 1e-3
+    assert abs((U1 - U0) - sdu) <= 1e-4 * abs(U0) + 1.0
+
+
+def test_mc_replay_flexible_paper_size_sampled():
+    s = synth.flexible_water_box(33333, seed=6)
+    box = epsr.Box(s)
+    stats, log = run_logged(box, 3000, seed=77)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 77, check_every=30)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
 def test_mc_replay_multi_cta_water():
     """A box split over several CTAs exercises the grid barrier and the gathered sums."""
     s = synth.water_box(3000, seed=42, density=0.1)
