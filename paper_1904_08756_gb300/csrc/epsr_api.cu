@@ -759,6 +759,7 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     const bool gslice = smem > kMcMaxDynSmem;
     if (gslice) {
         smem = (tables + 15) & ~(size_t)15;
+        smem += (size_t)kMcStageChunk * sizeof(int4);            // staged chunk of partners
         if (smem > kMcMaxDynSmem)
             return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of tables per CTA (limit %zu)", smem, kMcMaxDynSmem);
         const size_t slots = (size_t)box->cta_box_len * slice_cap;

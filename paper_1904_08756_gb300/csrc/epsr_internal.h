@@ -26,6 +26,8 @@ constexpr size_t kMcMaxDynSmem = 192 * 1024;   // with ~33 KB static: under the 
 constexpr int kMcSlotStride = 32 + 496;
 // correction items of one batch in shared memory (>= 496 pairs x 8 atoms)
 constexpr int kMcCorrItems = 4096;
+// partners staged per chunk in shared memory when the slices live in global memory
+constexpr int kMcStageChunk = 2048;
 
 struct McArgs {
     const BoxDev *boxes;

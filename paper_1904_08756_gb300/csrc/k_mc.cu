@@ -34,6 +34,7 @@ constexpr int kMcWarps = kMcThreads / 32;
 constexpr int kBatchMax = 32;                  // moves per batch: warp w takes moves w and w + 16
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
 constexpr int kCorrItems = kMcCorrItems;       // >= 496 pairs x 8 atoms (coarse items at G = 1)
+constexpr int kStageChunk = kMcStageChunk;     // partners per staged chunk (slices in global memory)
 constexpr int kEscMax = 256;                   // escapee list capacity per CTA (at most)
 constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
 static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
@@ -260,7 +261,7 @@ __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, co
 // around old atom 0 (half width hw), so its partners come from a cell query when the cube
 // meets at most 32 cells, else from the full scan with the cube test. M is a compile-time
 // bound so the atom loop unrolls into independent dependency chains.
-template <int M, bool CELLS>
+template <int M, bool CELLS, bool SKIP_LJ = false>
 __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int m, int a0, int hw,
                                              const int4 *slice, const int *blk, const CellIndex &ci,
                                              const BoxDev &bx, const long long *T, const float *ep,
@@ -295,6 +296,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
             if (pr[a]->c12 != 0.f || pr[a]->c6 != 0.f) lj |= 1u << a;
             else if (pr[a]->kqq != 0.f || bx.has_ep) nr |= 1u << a;
         }
+        if (SKIP_LJ) lj = 0u;                            // Lennard-Jones rows done by the caller
         if (!(lj | nr)) continue;
         const bool cells = nr && use_cells;
         const unsigned scan_nr = cells ? 0u : nr;
@@ -373,6 +375,40 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
                     acc += pair_du_cold(sep(np[a], pj, L), sep(op[a], pj, L), r, bx, T, ep);
             }
         }
+    return acc;
+}
+
+// Lennard-Jones rows of one move against a staged chunk of partners of type t (the chunk
+// is shared by all warps of the CTA; used when the slices live in global memory).
+template <int M>
+__device__ __forceinline__ float lj_chunk(const int4 *np, const int4 *op, int m, int a0, const int4 *stage,
+                                          int nc, int t, const BoxDev &bx, const long long *T, const float *ep,
+                                          int lane)
+{
+    unsigned lj = 0u;
+    int4 pn[M], po[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        pn[a] = a < m ? np[a] : make_int4(0, 0, 0, 0);
+        po[a] = a < m ? op[a] : make_int4(0, 0, 0, 0);
+        if (a < m) {
+            const PairRow &r = bx.row[pn[a].w * kMaxTypes + t];
+            if (r.c12 != 0.f || r.c6 != 0.f) lj |= 1u << a;
+        }
+    }
+    if (!lj) return 0.f;
+    const int L = bx.L;
+    float acc = 0.f;
+#pragma unroll 2
+    for (int j = lane; j < nc; j += 32) {
+        const int4 pj = stage[j];
+        const int jatom = (pj.w & 0x7fffffff) >> 3;
+        if (jatom >= a0 && jatom < a0 + m) continue;
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            if ((lj >> a) & 1u)
+                acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), bx.row[pn[a].w * kMaxTypes + t], bx, T, ep);
+    }
     return acc;
 }
 
@@ -474,6 +510,10 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     // no Lennard-Jones term but a Coulomb or empirical-potential one
     unsigned *cst = reinterpret_cast<unsigned *>(ep + A.ep_cap);
     float *corr_part = reinterpret_cast<float *>(cst + A.types_cap * (kMcCells + 1));   // [kCorrItems]
+    // GSLICE: staged chunk of partners [kStageChunk], on the next 16-byte boundary (the host
+    // sizes the dynamic shared memory as the 16-byte-rounded tables plus the chunk)
+    int4 *stage = reinterpret_cast<int4 *>((reinterpret_cast<uintptr_t>(corr_part + kCorrItems) + 15) &
+                                           ~static_cast<uintptr_t>(15));
     unsigned short *home = GSLICE ? A.home_g + (size_t)cta * A.slice_cap
                                   : reinterpret_cast<unsigned short *>(corr_part + kCorrItems);
     for (int t = 0; t < nt; ++t) {
@@ -671,6 +711,54 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         }
         const bool fine = n_items <= kCorrItems;
         // ---- C. partial dU of move `warp` against this CTA's slice ---------------------------
+        if (GSLICE && sh.mm <= 3) {
+            // slices in global memory: the Lennard-Jones partners are staged chunk by chunk in
+            // shared memory and every warp scans each chunk for its moves, so a batch reads the
+            // slice once instead of once per move; then each move's near-only rows
+            float accL[2] = {0.f, 0.f};
+            for (int t = 0; t < nt; ++t) {
+                for (int c0 = sh.blk[t]; c0 < sh.blk[t + 1]; c0 += kStageChunk) {
+                    const int nc = min(kStageChunk, sh.blk[t + 1] - c0);
+                    __syncthreads();
+                    for (int i = tid; i < nc; i += kMcThreads) stage[i] = __ldcg(&slice[c0 + i]);
+                    __syncthreads();
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int k = warp + q * kMcWarps;
+                        if (k >= nb) continue;
+                        const int m = sh.natoms[k];
+                        accL[q] += m == 1 ? lj_chunk<1>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], stage, nc, t, bx, T, ep, lane)
+                                          : lj_chunk<3>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], stage, nc, t, bx, T, ep, lane);
+                    }
+                }
+            }
+            CellIndex ci;
+            ci.cst = cst;
+            ci.cb = sh.cb;
+            ci.esc = sh.esc;
+            ci.n_esc = min(sh.n_esc, A.esc_cap);
+            ci.margin = A.cell_margin;
+            ci.on = sh.cells_on != 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = warp + q * kMcWarps;
+                if (k >= nb) continue;
+                const int m = sh.natoms[k];
+                float acc = accL[q];
+                if (m == 1)
+                    acc += ci.on ? partner_sum<1, true, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
+                                                              slice, sh.blk, ci, bx, T, ep, lane)
+                                 : partner_sum<1, false, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
+                                                               slice, sh.blk, ci, bx, T, ep, lane);
+                else
+                    acc += ci.on ? partner_sum<3, true, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                                                              slice, sh.blk, ci, bx, T, ep, lane)
+                                 : partner_sum<3, false, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                                                               slice, sh.blk, ci, bx, T, ep, lane);
+                acc = warp_sum(acc);
+                if (lane == 0) sh.part[k] = acc;
+            }
+        } else
         for (int k = warp; k < nb; k += kMcWarps) {
             const int m = sh.natoms[k];
             float acc;
