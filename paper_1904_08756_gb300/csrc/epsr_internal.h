@@ -23,7 +23,8 @@ void note_launch();
 constexpr size_t kMcMaxDynSmem = 192 * 1024;   // with ~33 KB static: under the 227 KB per CTA
 // per-CTA barrier slot: the batch's partial dU (32 moves), then the pair-energy corrections
 // this CTA computed (at most 32 * 31 / 2 = 496 pairs)
-constexpr int kMcSlotStride = 32 + 496;
+constexpr int kMcCorrPerCta = 496;        // batch-pair corrections (32 moves)
+constexpr int kMcSlotStride = 32 + kMcCorrPerCta;
 // correction items of one batch in shared memory (>= 496 pairs x 8 atoms)
 constexpr int kMcCorrItems = 4096;
 // partners staged per chunk in shared memory when the slices live in global memory
@@ -36,7 +37,8 @@ struct McArgs {
     const long long *thresholds;  // concatenated [n_bins + 1] per box
     const float *ep;              // concatenated [n_pairs * n_bins] per box
     const int *cta_box;           // [grid]
-    float *slots;                 // [2][grid][kMcSlotStride] partial dU and pair corrections per CTA
+    float *slots;                 // [2][grid * kMcSlotStride]: partials [kBatchMax][grid], then corrections
+                                  // [grid][kMcCorrPerCta] (a box group uses cta0 * kMcCorrPerCta onwards)
     unsigned *flags;              // [grid] arrival sequence numbers (zeroed per launch)
     epsr_mc_stats *stats;         // [n_boxes] running totals (device)
     epsr_move_log *log;           // nullable [n_boxes][log_stride]

@@ -37,7 +37,9 @@ constexpr int kCorrItems = kMcCorrItems;       // >= 496 pairs x 8 atoms (coarse
 constexpr int kStageChunk = kMcStageChunk;     // partners per staged chunk (slices in global memory)
 constexpr int kEscMax = 256;                   // escapee list capacity per CTA (at most)
 constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
-static_assert(kMcSlotStride == kBatchMax + kBatchMax * (kBatchMax - 1) / 2, "barrier slot layout");
+static_assert(kMcCorrPerCta == kBatchMax * (kBatchMax - 1) / 2 && kMcSlotStride == kBatchMax + kMcCorrPerCta,
+              "barrier slot layout");
+static_assert(kMcThreads == 16 * kBatchMax, "gather: 16 threads per move");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
 __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n_boxes,
@@ -787,50 +789,61 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         }
         __syncthreads();
         // ---- D. gather the partials of the box's CTA group (one bounded grid barrier) -------
-        // Arrival: the partials, then a release add on the group's counter. Wait: one thread
-        // polls the counter with relaxed loads (no serialising acquires), then one acquire
-        // fence orders the reads of the other CTAs' partials after the observed arrivals.
+        // Slot buffer, per parity: partials [kBatchMax][grid] (one move's partials of the group
+        // are contiguous), then corrections, the box's pair pq at cta0 * kMcCorrPerCta + pq.
+        // Arrival: warp 0 writes the CTA's partials and corrections in parallel, then lane 0
+        // makes a release add on the group's counter and polls it with acquire loads.
         ++seq;
         if (G > 1) {
-            if (tid == 0) {
-                float *slot = A.slots + ((size_t)(seq & 1u) * A.grid + cta) * kMcSlotStride;
-                if (cta != A.skip_arrival_cta) {
-                    for (int k = 0; k < nb; ++k) slot[k] = sh.part[k];
-                    for (int u = 0; u < n_local; ++u) slot[kBatchMax + u] = corr_sum(corr_part, u, mm, fine);
-                    red_add_release_gpu(&A.flags[box], 1u);
+            float *ps = A.slots + (size_t)(seq & 1u) * A.grid * kMcSlotStride;
+            float *cs = ps + (size_t)kBatchMax * A.grid + (size_t)bx.cta0 * kMcCorrPerCta;
+            if (warp == 0) {
+                const bool arrive = cta != A.skip_arrival_cta;
+                if (arrive) {
+                    if (lane < nb) ps[(size_t)lane * A.grid + cta] = sh.part[lane];
+                    for (int u = lane; u < n_local; u += 32) cs[rank + u * G] = corr_sum(corr_part, u, mm, fine);
                 }
-                const unsigned target = seq * (unsigned)G;
-                const uint64_t t_start = globaltimer_ns();
-                long long it = 0;
-                bool timed_out = false;
-                while (ld_relaxed_gpu_u32(&A.flags[box]) < target) {
-                    if ((++it & 255) == 0 &&
-                        ((globaltimer_ns() - t_start > A.timeout_ns) || it > A.max_spin ||
-                         ld_relaxed_gpu(A.status) != 0)) {
-                        timed_out = true;
-                        break;
+                __syncwarp();
+                if (lane == 0) {
+                    if (arrive) red_add_release_gpu(&A.flags[box], 1u);
+                    const unsigned target = seq * (unsigned)G;
+                    const uint64_t t_start = globaltimer_ns();
+                    long long it = 0;
+                    bool timed_out = false;
+                    while (ld_acquire_gpu(&A.flags[box]) < target) {
+                        if ((++it & 255) == 0 &&
+                            ((globaltimer_ns() - t_start > A.timeout_ns) || it > A.max_spin ||
+                             ld_relaxed_gpu(A.status) != 0)) {
+                            timed_out = true;
+                            break;
+                        }
                     }
-                }
-                fence_acq_rel_gpu();
-                if (timed_out) {
-                    atomicOr(A.status, kStatusTimeout);
-                    sh.abort_flag = 1;
+                    if (timed_out) {
+                        atomicOr(A.status, kStatusTimeout);
+                        sh.abort_flag = 1;
+                    }
                 }
             }
             __syncthreads();
             if (sh.abort_flag) return;
-            const float *bs = A.slots + (size_t)(seq & 1u) * A.grid * kMcSlotStride;
-            for (int k = warp; k < nb; k += kMcWarps) {
+            {
+                // 16 threads per move, each summing every 16th CTA's partial, then a fixed
+                // shuffle tree: the order of the FP32 sum is the same in every run
+                const int k = tid >> 4, sub = tid & 15;
                 float v = 0.f;
-                for (int r = lane; r < G; r += 32) v += __ldcg(&bs[(size_t)(bx.cta0 + r) * kMcSlotStride + k]);
-                v = warp_sum(v);
-                if (lane == 0) sh.base[k] = v;
+                if (k < nb) {
+                    const float *pk = ps + (size_t)k * A.grid + bx.cta0;
+#pragma unroll 4
+                    for (int r = sub; r < G; r += 16) v += __ldcg(&pk[r]);
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (sub == 0 && k < nb) sh.base[k] = v;
             }
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 int k = 1;
                 while ((k + 1) * k / 2 <= pq) ++k;
-                sh.corr[pq - k * (k - 1) / 2][k] =
-                    __ldcg(&bs[(size_t)(bx.cta0 + pq % G) * kMcSlotStride + kBatchMax + pq / G]);
+                sh.corr[pq - k * (k - 1) / 2][k] = __ldcg(&cs[pq]);
             }
         } else {
             for (int k = tid; k < nb; k += kMcThreads) sh.base[k] = sh.part[k];

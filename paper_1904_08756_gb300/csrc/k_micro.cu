@@ -1,8 +1,8 @@
 // k_micro.cu -- two measurements that bound the Monte Carlo sweep on this GPU, run by the
 // library's own kernels so that they see the same code generation as the sweep:
 //  - the grid-barrier floor: a cooperative persistent grid that does nothing but the sweep's
-//    per-batch exchange (partials to a slot, release add on a counter, relaxed poll, acquire
-//    fence, fixed-order gather of 16 partials per CTA), i.e. the least time per batch;
+//    per-batch exchange (32 partials and the pair corrections to the slot buffer, release add
+//    on a counter, acquire poll, fixed-order gather), i.e. the least time per batch;
 //  - the integer and FP32 issue rates: independent dependency chains of 32-bit adds or FP32
 //    fused multiply-adds in every lane, counted as lane-operations per second.
 #include "epsr_device.cuh"
@@ -11,54 +11,68 @@
 namespace epsr {
 
 constexpr int kMicroThreads = 512;
-constexpr int kMicroPartials = 16;
+constexpr int kMicroPartials = 32;             // partials per CTA (moves per batch)
+constexpr int kMicroCorr = 496;                // batch-pair corrections per group
+static_assert(kMicroThreads == 16 * kMicroPartials, "16 threads per partial");
 
+// Slot buffer per parity: partials [kMicroPartials][G], then kMicroCorr corrections, pair pq
+// written by CTA pq mod G; the layout and the order of operations are the sweep's.
 __global__ void __launch_bounds__(kMicroThreads, 1)
 barrier_floor_kernel(unsigned *counter, float *slots, int iters, unsigned long long timeout_ns, int *status,
                      float *sink)
 {
     __shared__ float part[kMicroPartials];
+    __shared__ float base[kMicroPartials];
+    __shared__ float corr[kMicroCorr];
     __shared__ int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, cta = blockIdx.x;
     if (tid == 0) abort_flag = 0;
     if (tid < kMicroPartials) part[tid] = (float)(cta + tid);
     __syncthreads();
+    const int n_local = kMicroCorr > cta ? (kMicroCorr - cta + G - 1) / G : 0;
     float acc = 0.f;
     for (int it = 0; it < iters; ++it) {
-        if (tid == 0) {
-            float *slot = slots + ((size_t)(it & 1) * G + cta) * kMicroPartials;
-            for (int k = 0; k < kMicroPartials; ++k) slot[k] = part[k];
-            red_add_release_gpu(counter, 1u);
-            const unsigned target = (unsigned)(it + 1) * (unsigned)G;
-            const uint64_t t0 = globaltimer_ns();
-            long long spins = 0;
-            bool timed_out = false;
-            while (ld_relaxed_gpu_u32(counter) < target) {
-                if ((++spins & 255) == 0 && (globaltimer_ns() - t0 > timeout_ns || ld_relaxed_gpu(status) != 0)) {
-                    timed_out = true;
-                    break;
+        float *ps = slots + (size_t)(it & 1) * ((size_t)kMicroPartials * G + kMicroCorr);
+        float *cs = ps + (size_t)kMicroPartials * G;
+        if (warp == 0) {
+            ps[(size_t)lane * G + cta] = part[lane];
+            for (int u = lane; u < n_local; u += 32) cs[cta + u * G] = (float)u;
+            __syncwarp();
+            if (lane == 0) {
+                red_add_release_gpu(counter, 1u);
+                const unsigned target = (unsigned)(it + 1) * (unsigned)G;
+                const uint64_t t0 = globaltimer_ns();
+                long long spins = 0;
+                bool timed_out = false;
+                while (ld_acquire_gpu(counter) < target) {
+                    if ((++spins & 255) == 0 && (globaltimer_ns() - t0 > timeout_ns || ld_relaxed_gpu(status) != 0)) {
+                        timed_out = true;
+                        break;
+                    }
                 }
-            }
-            fence_acq_rel_gpu();
-            if (timed_out) {
-                atomicOr(status, kStatusTimeout);
-                abort_flag = 1;
+                if (timed_out) {
+                    atomicOr(status, kStatusTimeout);
+                    abort_flag = 1;
+                }
             }
         }
         __syncthreads();
         if (abort_flag) return;
-        if (warp < kMicroPartials) {
-            const float *bs = slots + (size_t)(it & 1) * G * kMicroPartials;
+        {
+            const int k = tid >> 4, sub = tid & 15;
             float v = 0.f;
-            for (int r = lane; r < G; r += 32) v += __ldcg(&bs[(size_t)r * kMicroPartials + warp]);
+#pragma unroll 4
+            for (int r = sub; r < G; r += 16) v += __ldcg(&ps[(size_t)k * G + r]);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc += v;
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (sub == 0) base[k] = v;
         }
+        for (int pq = tid; pq < kMicroCorr; pq += kMicroThreads) corr[pq] = __ldcg(&cs[pq]);
         __syncthreads();
+        if (tid < kMicroPartials) acc += base[tid] + corr[tid];
     }
-    if (lane == 0 && acc == -1.f) sink[cta] = acc;   // keeps the gather live
+    if (tid < kMicroPartials && acc == -1.f) sink[cta] = acc;   // keeps the gather live
 }
 
 // 8 independent chains per lane; kind 0: 32-bit exclusive-or and add (two lane-operations
@@ -110,7 +124,7 @@ int micro_barrier_floor(int ctas, int iters, double timeout_ms, double *ns_per_b
     int rc = EPSR_OK;
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaMalloc(&counter, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&slots, (size_t)2 * ctas * kMicroPartials * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&slots, (size_t)2 * ((size_t)kMicroPartials * ctas + kMicroCorr) * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&sink, (size_t)ctas * sizeof(float)) != cudaSuccess) {
         rc = set_error(EPSR_ENOMEM, "barrier floor scratch");
     }
