@@ -150,6 +150,37 @@ __device__ __forceinline__ float pair_u(Sep s, const PairRow &pr, const BoxDev &
     return u;
 }
 
+// The part of u(r') - u(r) shared by every term: squared distances in grid units, r^2 and
+// r'^2 in A^2, their difference r^2 - r'^2 from the exact integer factors, and 1/r, 1/r'.
+struct DuCore {
+    float g2n, g2o, r2n, r2o, dr2, an, ao;
+};
+
+__device__ __forceinline__ DuCore du_core(Sep sn, Sep so, float inv_s2)
+{
+    const float fxn = (float)sn.x, fyn = (float)sn.y, fzn = (float)sn.z;
+    const float fxo = (float)so.x, fyo = (float)so.y, fzo = (float)so.z;
+    DuCore c;
+    c.g2n = fmaf(fxn, fxn, fmaf(fyn, fyn, fzn * fzn));
+    c.g2o = fmaf(fxo, fxo, fmaf(fyo, fyo, fzo * fzo));
+    c.r2n = c.g2n * inv_s2;
+    c.r2o = c.g2o * inv_s2;
+    c.dr2 = fmaf(fxo - fxn, fxo + fxn, fmaf(fyo - fyn, fyo + fyn, (fzo - fzn) * (fzo + fzn))) * inv_s2;
+    c.an = rsqrtf(c.r2n);
+    c.ao = rsqrtf(c.r2o);
+    return c;
+}
+
+// Lennard-Jones change c12 (s'^2 - s^2) - c6 (s' - s), s = r^-6, without cancellation.
+__device__ __forceinline__ float lj_du(const DuCore &c, float c12, float c6)
+{
+    const float in = c.an * c.an, io = c.ao * c.ao;
+    const float s6n = in * in * in, s6o = io * io * io;
+    const float poly = fmaf(c.r2o, c.r2o, fmaf(c.r2o, c.r2n, c.r2n * c.r2n));
+    const float ds = ((c.dr2 * poly) * s6n) * s6o;
+    return ds * fmaf(c12, s6n + s6o, -c6);
+}
+
 // u(r') - u(r) for one partner seen from a moved atom's new (sn) and old (so) positions,
 // written so that neither the Lennard-Jones nor the Coulomb difference cancels: both are
 // proportional to r^2 - r'^2 = sum over axes (|do| - |dn|)(|do| + |dn|), whose factors are
@@ -161,23 +192,11 @@ __device__ __forceinline__ float pair_u(Sep s, const PairRow &pr, const BoxDev &
 __device__ __forceinline__ float pair_du(Sep sn, Sep so, const PairRow &pr, const BoxDev &bx,
                                          const long long *T, const float *ep)
 {
-    const float fxn = (float)sn.x, fyn = (float)sn.y, fzn = (float)sn.z;
-    const float fxo = (float)so.x, fyo = (float)so.y, fzo = (float)so.z;
-    const float g2n = fmaf(fxn, fxn, fmaf(fyn, fyn, fzn * fzn));
-    const float g2o = fmaf(fxo, fxo, fmaf(fyo, fyo, fzo * fzo));
+    const DuCore c = du_core(sn, so, bx.inv_s2);
+    const float g2n = c.g2n, g2o = c.g2o, an = c.an, ao = c.ao, dr2 = c.dr2;
     if (g2n == 0.f) return __int_as_float(0x7f800000);
-    const float r2n = g2n * bx.inv_s2, r2o = g2o * bx.inv_s2;
-    const float dr2 = fmaf(fxo - fxn, fxo + fxn, fmaf(fyo - fyn, fyo + fyn, (fzo - fzn) * (fzo + fzn))) *
-                      bx.inv_s2;
-    const float an = rsqrtf(r2n), ao = rsqrtf(r2o);
     float du = 0.f;
-    if (pr.c12 != 0.f || pr.c6 != 0.f) {
-        const float in = an * an, io = ao * ao;
-        const float s6n = in * in * in, s6o = io * io * io;
-        const float poly = fmaf(r2o, r2o, fmaf(r2o, r2n, r2n * r2n));
-        const float ds = ((dr2 * poly) * s6n) * s6o;
-        du = ds * fmaf(pr.c12, s6n + s6o, -pr.c6);
-    }
+    if (pr.c12 != 0.f || pr.c6 != 0.f) du = lj_du(c, pr.c12, pr.c6);
     const bool cn = below(g2n, sn, bx.rc2, bx.rc2_lo, bx.rc2_hi);
     const bool co = below(g2o, so, bx.rc2, bx.rc2_lo, bx.rc2_hi);
     if (cn && co) {

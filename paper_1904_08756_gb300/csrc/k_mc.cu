@@ -40,6 +40,7 @@ constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: 
 static_assert(kMcCorrPerCta == kBatchMax * (kBatchMax - 1) / 2 && kMcSlotStride == kBatchMax + kMcCorrPerCta,
               "barrier slot layout");
 static_assert(kMcThreads == 16 * kBatchMax, "gather: 16 threads per move");
+static_assert(kBatchMax == 2 * kMcWarps, "phase B: two moves per warp");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
 __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n_boxes,
@@ -256,6 +257,46 @@ __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, co
     return pair_du(sn, so, pr, bx, T, ep);
 }
 
+// Lennard-Jones rows (bit a of lj: atom a of the move) against partners [j0, j1) of type t,
+// added to acc in the order of a lane-strided scan. A lane takes two partners, j and j + 32,
+// per step. A pair whose squared distances both exceed far2 has no Coulomb and no EP term,
+// so its dU is the Lennard-Jones change alone, computed as straight-line code for both
+// partners at once; a pair that is not that far takes the full pair_du (same value).
+template <int M>
+__device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const int4 (&po)[M], unsigned lj, int a0,
+                                         int m, const int4 *part, int j0, int j1, int t, const BoxDev &bx,
+                                         const long long *T, const float *ep, int lane)
+{
+    const int L = bx.L;
+    const float far2 = fmaxf(bx.rc2_hi, bx.has_ep ? bx.tmax_hi : 0.f);
+    for (int j = j0 + lane; j < j1; j += 64) {
+        const bool in1 = j + 32 < j1;
+        const int4 p0 = part[j];
+        const int4 p1 = part[in1 ? j + 32 : j];
+        const int i0 = (p0.w & 0x7fffffff) >> 3, i1 = (p1.w & 0x7fffffff) >> 3;
+        const bool v0 = !(i0 >= a0 && i0 < a0 + m);
+        const bool v1 = in1 && !(i1 >= a0 && i1 < a0 + m);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            if (a >= m || !((lj >> a) & 1u)) continue;
+            const PairRow &r = bx.row[pn[a].w * kMaxTypes + t];
+            const Sep n0 = sep(pn[a], p0, L), o0 = sep(po[a], p0, L);
+            const Sep n1 = sep(pn[a], p1, L), o1 = sep(po[a], p1, L);
+            const DuCore c0 = du_core(n0, o0, bx.inv_s2), c1 = du_core(n1, o1, bx.inv_s2);
+            float d0 = lj_du(c0, r.c12, r.c6), d1 = lj_du(c1, r.c12, r.c6);
+            const bool s0 = v0 && !(c0.g2n > far2 && c0.g2o > far2);
+            const bool s1 = v1 && !(c1.g2n > far2 && c1.g2o > far2);
+            if (s0 || s1) {
+                if (s0) d0 = pair_du(n0, o0, r, bx, T, ep);
+                if (s1) d1 = pair_du(n1, o1, r, bx, T, ep);
+            }
+            if (v0) acc += d0;
+            if (v1) acc += d1;
+        }
+    }
+    return acc;
+}
+
 // Partial dU of one move (atoms np/op, m <= M) against the partners of this CTA, lane-
 // strided. Per partner type the kind of each moved atom's pair row is uniform across the
 // warp: a Lennard-Jones row (LJ is not cut) is evaluated against every partner of the type;
@@ -302,7 +343,9 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
         if (!(lj | nr)) continue;
         const bool cells = nr && use_cells;
         const unsigned scan_nr = cells ? 0u : nr;
-        if (lj | scan_nr) {
+        if (lj && !scan_nr) {
+            acc = lj_rows<M>(acc, pn, po, lj, a0, m, slice, blk[t], blk[t + 1], t, bx, T, ep, lane);
+        } else if (lj | scan_nr) {
             const int jb = blk[t + 1];
 #pragma unroll 2
             for (int j = blk[t] + lane; j < jb; j += 32) {
@@ -399,19 +442,7 @@ __device__ __forceinline__ float lj_chunk(const int4 *np, const int4 *op, int m,
         }
     }
     if (!lj) return 0.f;
-    const int L = bx.L;
-    float acc = 0.f;
-#pragma unroll 2
-    for (int j = lane; j < nc; j += 32) {
-        const int4 pj = stage[j];
-        const int jatom = (pj.w & 0x7fffffff) >> 3;
-        if (jatom >= a0 && jatom < a0 + m) continue;
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-            if ((lj >> a) & 1u)
-                acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), bx.row[pn[a].w * kMaxTypes + t], bx, T, ep);
-    }
-    return acc;
+    return lj_rows<M>(0.f, pn, po, lj, a0, m, stage, 0, nc, t, bx, T, ep, lane);
 }
 
 // The same for any molecule size (atoms read from shared memory; out-of-line pair function).
@@ -585,20 +616,42 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         __syncthreads();
         const int nb = sh.nb[par];
         // ---- B. current and trial coordinates of each moved molecule (integer arithmetic) ----
-        for (int k = warp; k < nb; k += kMcWarps) {
-            const MoveRec &mr = sh.mv[t0 + k - mv_base];
-            const int mol = sh.mol[par][k];
-            const int a0 = mr.a0, m = mr.m;
-            const int q = par ^ 1;
-            int pidx = -1;
-            for (int p = 0; p < sh.nb[q]; ++p)
-                if (sh.acc[q][p] && sh.mol[q][p] == mol) pidx = p;
-            if (lane < m) {
-                sh.oldp[k][lane] = pidx >= 0 ? sh.newp[q][pidx][lane]
-                                             : __ldcg(&A.coords[bx.atom0 + a0 + lane]);
-                sh.spos[k][lane] = A.pos_of[bx.atom0 + a0 + lane] - (int)bx.atom0;
+        // Current coordinates of a warp's two molecules, loaded together: from the previous
+        // batch's accepted move of the molecule if there is one (its global update may not be
+        // visible yet), else from the global coordinates.
+        {
+            int4 oc[2];
+            int sp[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = warp + h * kMcWarps;
+                oc[h] = make_int4(0, 0, 0, 0);
+                sp[h] = 0;
+                if (k < nb) {
+                    const MoveRec &mr = sh.mv[t0 + k - mv_base];
+                    const int q = par ^ 1;
+                    const bool hit = lane < sh.nb[q] && sh.acc[q][lane] && sh.mol[q][lane] == sh.mol[par][k];
+                    const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                    const int pidx = hb ? 31 - __clz(hb) : -1;   // molecules of a batch are distinct
+                    if (lane < mr.m) {
+                        oc[h] = pidx >= 0 ? sh.newp[q][pidx][lane] : __ldcg(&A.coords[bx.atom0 + mr.a0 + lane]);
+                        sp[h] = A.pos_of[bx.atom0 + mr.a0 + lane] - (int)bx.atom0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = warp + h * kMcWarps;
+                if (k < nb && lane < sh.mv[t0 + k - mv_base].m) {
+                    sh.oldp[k][lane] = oc[h];
+                    sh.spos[k][lane] = sp[h];
+                }
             }
             __syncwarp();
+        }
+        for (int k = warp; k < nb; k += kMcWarps) {
+            const MoveRec &mr = sh.mv[t0 + k - mv_base];
+            const int a0 = mr.a0, m = mr.m;
             if (lane < 3 * m) {
                 const int kk = lane / 3, a = lane - 3 * kk;
                 const int4 *op = sh.oldp[k];
