@@ -165,6 +165,16 @@ __device__ __forceinline__ void block_sum_du(const float *v, int n, int lane, do
 // Correction of local pair u: the sum over atoms a of move k of the sum over atoms b of move
 // k1 of [du(a; b new) - du(a; b old)], in that order. `fine` items hold each du separately;
 // otherwise each item already holds the sum over b (same operations, same order).
+// Later move k of batch pair pq = k (k - 1) / 2 + k1 (0 <= k1 < k): a float estimate of
+// the root of k (k - 1) / 2 = pq, corrected by one step either way.
+__device__ __forceinline__ int pair_hi(int pq)
+{
+    int k = (int)((1.f + sqrtf(8.f * (float)pq + 1.f)) * 0.5f);
+    if (k * (k - 1) / 2 > pq) --k;
+    if ((k + 1) * k / 2 <= pq) ++k;
+    return k;
+}
+
 __device__ __forceinline__ float corr_sum(const float *part, int u, int mm, bool fine)
 {
     float c = 0.f;
@@ -649,11 +659,19 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             }
             __syncwarp();
         }
-        for (int k = warp; k < nb; k += kMcWarps) {
-            const MoveRec &mr = sh.mv[t0 + k - mv_base];
-            const int a0 = mr.a0, m = mr.m;
-            if (lane < 3 * m) {
-                const int kk = lane / 3, a = lane - 3 * kk;
+        // Trial coordinates: with molecules of at most 5 atoms the two moves of a warp run side
+        // by side in its half-warps, otherwise one after the other with the whole warp.
+        const int m_lo = warp < nb ? sh.mv[t0 + warp - mv_base].m : 0;
+        const int m_hi = warp + kMcWarps < nb ? sh.mv[t0 + warp + kMcWarps - mv_base].m : 0;
+        const bool halves = m_lo <= 5 && m_hi <= 5;
+        for (int rr = 0; rr < (halves ? 1 : 2); ++rr) {
+            const int k = warp + (halves ? lane >> 4 : rr) * kMcWarps;
+            const int sl = halves ? lane & 15 : lane;
+            const bool act = k < nb;
+            const MoveRec &mr = sh.mv[t0 + (act ? k : 0) - mv_base];
+            const int a0 = mr.a0, m = act ? mr.m : 0;
+            if (sl < 3 * m) {
+                const int kk = sl / 3, a = sl - 3 * kk;
                 const int4 *op = sh.oldp[k];
                 int coord;
                 if (mr.kind == 1) {
@@ -682,7 +700,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 if (a == 0) dst[3] = op[kk].w;
             }
             __syncwarp();
-            if (lane == 0) {
+            if (act && sl == 0) {
                 // flexible molecules: change of the intra-molecular springs, written without
                 // cancellation: k[(r' - d)^2 - (r - d)^2] = k (r' - r)(r' + r - 2d), with
                 // r' - r = (r'^2 - r^2) / (r' + r) from the exact integer squared distances
@@ -709,14 +727,15 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             __syncwarp();
             // near cube: every old and new atom position lies within `reach` of old atom 0
             int reach = 0;
-            if (lane < 2 * m) {
-                const int4 p = lane < m ? sh.oldp[k][lane] : sh.newp[par][k][lane - m];
+            if (sl < 2 * m) {
+                const int4 p = sl < m ? sh.oldp[k][sl] : sh.newp[par][k][sl - m];
                 const int4 o = sh.oldp[k][0];
                 reach = max(mi_abs(p.x - o.x, L), max(mi_abs(p.y - o.y, L), mi_abs(p.z - o.z, L)));
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) reach = max(reach, __shfl_xor_sync(0xffffffffu, reach, o));
-            if (lane == 0) sh.hw[k] = bx.near_fx + reach + 2;
+            for (int o = 16; o > 0; o >>= 1)
+                if (o < 16 || !halves) reach = max(reach, __shfl_xor_sync(0xffffffffu, reach, o));
+            if (act && sl == 0) sh.hw[k] = bx.near_fx + reach + 2;
         }
         __syncthreads();
         // ---- E. pair-energy corrections between the batch's moved molecules -----------------
@@ -734,8 +753,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             for (int it = tid; it < n_items; it += kMcThreads) {
                 const int side = it & 1, b = (it >> 1) % mm, a = ((it >> 1) / mm) % mm;
                 const int pq = rank + ((it >> 1) / mm / mm) * G;
-                int k = 1;
-                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k = pair_hi(pq);
                 const int k1 = pq - k * (k - 1) / 2;
                 float v = 0.f;
                 if (a < sh.natoms[k] && b < sh.natoms[k1]) {
@@ -748,8 +766,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         } else {                                  // large molecules and few CTAs: items (pair, a)
             for (int it = tid; it < n_local * mm; it += kMcThreads) {
                 const int a = it % mm, pq = rank + (it / mm) * G;
-                int k = 1;
-                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k = pair_hi(pq);
                 const int k1 = pq - k * (k - 1) / 2;
                 float ca = 0.f;
                 if (a < sh.natoms[k]) {
@@ -894,15 +911,13 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 if (sub == 0 && k < nb) sh.base[k] = v;
             }
             for (int pq = tid; pq < npq; pq += kMcThreads) {
-                int k = 1;
-                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k = pair_hi(pq);
                 sh.corr[pq - k * (k - 1) / 2][k] = __ldcg(&cs[pq]);
             }
         } else {
             for (int k = tid; k < nb; k += kMcThreads) sh.base[k] = sh.part[k];
             for (int pq = tid; pq < npq; pq += kMcThreads) {
-                int k = 1;
-                while ((k + 1) * k / 2 <= pq) ++k;
+                const int k = pair_hi(pq);
                 sh.corr[pq - k * (k - 1) / 2][k] = corr_sum(corr_part, pq, mm, fine);
             }
         }
