@@ -444,9 +444,7 @@ static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *x
             ts += bx.count[t];
         }
         set_near(bx);
-        const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
-        const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
-        bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
+        set_prefilter(bx);
         // cell-list histogram: cells at least the histogram range plus two grid units wide
         const long long rcut = (long long)std::ceil(std::sqrt((double)bx.tmax)) + 2 +
                                (long long)std::ceil(kCellSmearMarginA * std::ldexp(1.0, descs[b].scale_log2));

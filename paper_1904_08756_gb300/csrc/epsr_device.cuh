@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "epsr.h"
 
 namespace epsr {
@@ -47,6 +49,9 @@ struct BoxDev {
     float inv_s2;         // 2^(-2 scale_log2): grid units^2 -> A^2
     float inv_dr_fx;      // 1 / (bin width in grid units)
     uint32_t pre_r;       // g(r) prefilter half width on the 2^32-periodic scaled grid
+    uint32_t pre16_bias;  // all-pairs histogram prefilter on the 2^16-periodic grid: bias B = R16 + 1
+    uint32_t pre16_t;     // threshold T = 2 R16 + 1 in both halfwords
+    int32_t pre16_all;    // 1: the cube covers the whole period (every pair takes the exact path)
     int32_t cells;        // spatial-sort cells per side (g(r) work order)
     float rc2_lo, rc2_hi; // rc2 * (1 -/+ 2^-20) as floats: the exact test runs only between
     float tmax_lo, tmax_hi;   // tmax * (1 -/+ 2^-20)
@@ -345,6 +350,30 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int *p)
     int v;
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Host side: prefilter half widths of the all-pairs histogram. Every counted pair has
+// |dx| < R = ceil(sqrt(tmax)) + 1 grid units on each axis. On the 2^32-periodic grid
+// (x' = floor(x 2^32 / L)) that is |dx'| < R' = ceil(R 2^32 / L) + 2; on the 2^16-periodic
+// grid (x16 = x' >> 16) |dx16| <= R16 = ceil(R 2^16 / L) + 1, tested as the biased value
+// (x16_i + R16 + 1 - x16_j) mod 2^16 <= 2 R16 + 1. A pair at exactly |dx16| = R16 has
+// |dx| > R and is never counted.
+inline void set_prefilter(BoxDev &bx)
+{
+    const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
+    const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
+    bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
+    const double R16 = std::ceil(R * 65536.0 / (double)bx.L) + 1.0;
+    if (2.0 * R16 + 1.0 <= 65534.0) {
+        const uint32_t r16 = (uint32_t)R16, t = 2u * r16 + 1u;
+        bx.pre16_bias = r16 + 1u;
+        bx.pre16_t = t | (t << 16);
+        bx.pre16_all = 0;
+    } else {
+        bx.pre16_bias = 0u;
+        bx.pre16_t = 0xFFFFFFFFu;
+        bx.pre16_all = 1;
+    }
 }
 
 }  // namespace epsr

@@ -135,9 +135,7 @@ extern "C" int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, 
     bx.tmax = T[n_bins];
     bx.tmax_lo = (float)((double)bx.tmax * (1.0 - 0x1p-20));
     bx.tmax_hi = (float)((double)bx.tmax * (1.0 + 0x1p-20));
-    const double R = std::ceil(std::sqrt((double)bx.tmax)) + 1.0;
-    const double Rs = std::ceil(R * 4294967296.0 / (double)bx.L) + 2.0;
-    bx.pre_r = Rs >= 2147483647.0 ? 2147483647u : (unsigned)Rs;
+    set_prefilter(bx);
     int nc = (int)std::floor((double)L_fx / S / 3.0);
     nc = std::max(1, std::min(nc, 32));
     int p2 = 1;

@@ -7,14 +7,17 @@
 // shared load serves kGrR pair tests.
 //
 // Prefilter: a second copy of the coordinates is scaled so that the box side maps to
-// 2^32 (x' = floor(x 2^32 / L)). Differences then wrap modulo 2^32 exactly as minimum
-// images wrap modulo L, and |min-image dx| <= R implies |x'_i - x'_j| < R' with
-// R' = ceil(R 2^32 / L) + 2. The test is one subtraction per axis and one unsigned compare
-// of their three-way maximum: max((x'_i + R') - x'_j, ...) < 2 R'; the four i-atoms of a
-// thread are tested against one j before a single branch on the combined hit mask. Pairs that pass take the exact path: integer minimum
-// image on the true grid coordinates, exact 64-bit squared distance, bin from the
-// threshold table. Counts go to a per-CTA shared-memory histogram (32-bit) and are
-// flushed to the caller's 64-bit histogram with one atomic per non-empty bin.
+// 2^32 (x' = floor(x 2^32 / L)); its top 16 bits x16 = floor(x 2^16 / L) wrap modulo 2^16
+// as minimum images wrap modulo L. Each thread packs the biased 16-bit coordinates of two
+// of its i-atoms per axis in one word, so one 32-bit subtraction per axis gives both
+// differences, a three-way halfword maximum (__vimax3_u16x2) the per-atom maxima over the
+// axes, and two halfword minima and one compare decide whether any of the thread's four
+// i-atoms is inside the cube around j. Four j are tested per step before one branch.
+// Pairs that pass take the exact path: integer minimum image on the true grid coordinates;
+// the bin from the FP32 squared distance, with the exact 64-bit squared distance and the
+// threshold table only within the FP32 error of a bin edge or of the range. Counts go to a
+// per-CTA shared-memory histogram (32-bit) and are flushed to the caller's 64-bit histogram
+// with one atomic per non-empty bin.
 #include "epsr_device.cuh"
 #include "epsr_internal.h"
 
@@ -268,11 +271,31 @@ __device__ __forceinline__ void flush_hist(unsigned *sh_hist, int n, unsigned lo
     }
 }
 
+// Bin of a pair from its FP32 squared distance g2 (relative error below 2^-21.7 from the
+// int32 separations), falling back to the exact integer test only where that error could
+// matter: the bin is floor(sqrt(d2) / w) exactly (d2 >= T[k] <=> d2 >= (k w)^2 for integer
+// d2), and x = sqrt(g2) / w carries a relative error below 2^-21, so floor(x) is the bin
+// unless x lies within x 2^-20 of an integer. Returns -1 outside the histogram range.
+__device__ __forceinline__ int bin_of_fast(Sep sp, float g2, const long long *T, int nb, float inv,
+                                           long long tmax, float tmax_lo, float tmax_hi)
+{
+    if (g2 >= tmax_hi) return -1;
+    if (g2 >= tmax_lo && d2_of(sp) >= tmax) return -1;
+    const float x = sqrtf(g2) * inv;
+    const int k = (int)x;
+    const float f = x - (float)k, eps = x * 0x1p-20f;
+    if (f > eps && f < 1.f - eps && k < nb) return k;
+    return bin_of(d2_of(sp), g2, T, nb, inv);
+}
+
+static_assert(kGrR == 4, "the prefilter packs the four i-atoms of a thread in pairs");
+static_assert(kGrTile % 4 == 0, "four j per step");
+
 __global__ void __launch_bounds__(kGrThreads, 4) partial_gr_kernel(GrArgs A)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    uint4 *s_scaled = reinterpret_cast<uint4 *>(dyn);
-    int4 *s_true = reinterpret_cast<int4 *>(s_scaled + kGrTile);
+    uint4 *s_pack = reinterpret_cast<uint4 *>(dyn);         // j: 16-bit x, y, z in both halfwords
+    int4 *s_true = reinterpret_cast<int4 *>(s_pack + kGrTile);
     long long *s_T = reinterpret_cast<long long *>(s_true + kGrTile);
     unsigned *s_hist = reinterpret_cast<unsigned *>(s_T + A.max_bins1);
     __shared__ BoxDev bx;
@@ -302,61 +325,80 @@ __global__ void __launch_bounds__(kGrThreads, 4) partial_gr_kernel(GrArgs A)
         }
         const int L = bx.L;
         const int N = bx.n_atoms;
-        const unsigned R = bx.pre_r, R2 = 2u * bx.pre_r;
+        const unsigned B = bx.pre16_bias, TT = bx.pre16_t, T = TT & 0xFFFFu;
+        const bool all = bx.pre16_all != 0;
         const long long tmax = bx.tmax;
-        const float tmax_hi = bx.tmax_hi;
+        const float tmax_hi = bx.tmax_hi, tmax_lo = bx.tmax_lo;
         const int nb = bx.n_bins, nt = bx.n_types;
         const float inv = bx.inv_dr_fx;
-        // stage the j-tile
+        // stage the j-tile: the 16-bit coordinate (top half of the 2^32-scaled one) in both
+        // halfwords of a word per axis, and the true coordinates for the exact path
         const int j0 = tl.tj * kGrTile;
         const int nj = min(kGrTile, N - j0);
         __syncthreads();
         for (int j = tid; j < nj; j += kGrThreads) {
-            s_scaled[j] = A.scaled[bx.atom0 + j0 + j];
+            const uint4 sc = A.scaled[bx.atom0 + j0 + j];
+            s_pack[j] = make_uint4(__byte_perm(sc.x, 0u, 0x3232), __byte_perm(sc.y, 0u, 0x3232),
+                                     __byte_perm(sc.z, 0u, 0x3232), 0u);
             s_true[j] = A.coords[bx.atom0 + j0 + j];
         }
-        // i-atoms in registers: thread t holds tile rows t, t + 256, ...
+        // i-atoms in registers: thread t holds tile rows t, t + 256, t + 512, t + 768, biased
+        // 16-bit coordinates packed two rows per word (rows 0/2 low halfword, 1/3 high)
         const int i0 = tl.ti * kGrTile;
-        uint32_t xi[kGrR], yi[kGrR], zi[kGrR];
         int il[kGrR];
+        unsigned bxr[kGrR], byr[kGrR], bzr[kGrR];
 #pragma unroll
         for (int r = 0; r < kGrR; ++r) {
             il[r] = tid + r * kGrThreads;
             const int ig = i0 + il[r];
+            bxr[r] = byr[r] = bzr[r] = 0u;
             if (ig < N) {
-                const uint4 s = A.scaled[bx.atom0 + ig];
-                xi[r] = s.x + R; yi[r] = s.y + R; zi[r] = s.z + R;
+                const uint4 sc = A.scaled[bx.atom0 + ig];
+                bxr[r] = ((sc.x >> 16) + B) & 0xFFFFu;
+                byr[r] = ((sc.y >> 16) + B) & 0xFFFFu;
+                bzr[r] = ((sc.z >> 16) + B) & 0xFFFFu;
             } else {
                 il[r] = -1;
-                xi[r] = yi[r] = zi[r] = 0u;
             }
         }
+        const unsigned X01 = bxr[0] | (bxr[1] << 16), Y01 = byr[0] | (byr[1] << 16), Z01 = bzr[0] | (bzr[1] << 16);
+        const unsigned X23 = bxr[2] | (bxr[3] << 16), Y23 = byr[2] | (byr[3] << 16), Z23 = bzr[2] | (bzr[3] << 16);
         const bool diag = tl.ti == tl.tj;
         __syncthreads();
-        for (int j = 0; j < nj; ++j) {
-            const uint4 sj = s_scaled[j];
-            unsigned mask = 0u;
+        // four j per step: their tests are independent, and one branch covers all four
+        for (int jb = 0; jb < nj; jb += 4) {
+            unsigned msk[4], m01s[4], m23s[4];
 #pragma unroll
-            for (int r = 0; r < kGrR; ++r) {
-                const bool hit = __vimax3_u32(xi[r] - sj.x, yi[r] - sj.y, zi[r] - sj.z) < R2;
-                mask |= hit ? 1u << r : 0u;
+            for (int u = 0; u < 4; ++u) {
+                const uint4 pj = s_pack[jb + u];   // jb + u < kGrTile; entries past nj are masked
+                // one 32-bit subtraction per axis and row pair: the low halfword is exact
+                // modulo 2^16, the high one may carry a borrow of one unit, which the bias absorbs;
+                // per-row maxima over the axes, then the least of the four rows in both halfwords
+                const unsigned m01 = __vimax3_u16x2(X01 - pj.x, Y01 - pj.y, Z01 - pj.z);
+                const unsigned m23 = __vimax3_u16x2(X23 - pj.x, Y23 - pj.y, Z23 - pj.z);
+                const unsigned x = __vimin3_u16x2(m01, m23, m23);
+                const unsigned y = __vimin3_u16x2(x, __byte_perm(x, 0u, 0x1032), x);
+                m01s[u] = m01; m23s[u] = m23;
+                msk[u] = (jb + u < nj && (y <= TT || all)) ? 1u : 0u;
             }
-            if (mask == 0u) continue;
+            if (!(msk[0] | msk[1] | msk[2] | msk[3])) continue;
 #pragma unroll
-            for (int r = 0; r < kGrR; ++r) {
-                if ((mask >> r) & 1u) {
-                    if (il[r] < 0 || (diag && j <= il[r])) continue;
-                    const int4 pi = A.coords[bx.atom0 + i0 + il[r]];
-                    const int4 pj = s_true[j];
-                    const Sep sp = sep(pi, pj, L);
-                    const float g2 = g2_of(sp);
-                    if (g2 < tmax_hi) {
-                        const long long d2 = d2_of(sp);
-                        if (d2 < tmax) {
-                            const int k = bin_of(d2, g2, s_T, nb, inv);
-                            const int p = pair_index(pi.w, pj.w, nt);
-                            atomicAdd(&s_hist[p * nb + k], 1u);
-                        }
+            for (int u = 0; u < 4; ++u) {
+                if (!msk[u]) continue;
+                const unsigned m01 = m01s[u], m23 = m23s[u];
+                const unsigned mask = all ? 0xFu
+                                          : ((m01 & 0xFFFFu) <= T ? 1u : 0u) | ((m01 >> 16) <= T ? 2u : 0u) |
+                                                ((m23 & 0xFFFFu) <= T ? 4u : 0u) | ((m23 >> 16) <= T ? 8u : 0u);
+                const int j = jb + u;
+#pragma unroll
+                for (int r = 0; r < kGrR; ++r) {
+                    if ((mask >> r) & 1u) {
+                        if (il[r] < 0 || (diag && j <= il[r])) continue;
+                        const int4 pi = A.coords[bx.atom0 + i0 + il[r]];
+                        const int4 pj = s_true[j];
+                        const Sep sp = sep(pi, pj, L);
+                        const int k = bin_of_fast(sp, g2_of(sp), s_T, nb, inv, tmax, tmax_lo, tmax_hi);
+                        if (k >= 0) atomicAdd(&s_hist[pair_index(pi.w, pj.w, nt) * nb + k], 1u);
                     }
                 }
             }
@@ -400,23 +442,6 @@ constexpr int kGcStage = 512;            // neighbour atoms staged in shared mem
 __constant__ int c_fwd[14][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 1, 0},  {0, 1, 0},   {1, 1, 0},
                                  {-1, -1, 1}, {0, -1, 1},  {1, -1, 1},  {-1, 0, 1},  {0, 0, 1},
                                  {1, 0, 1},  {-1, 1, 1},   {0, 1, 1},   {1, 1, 1}};
-
-// Bin of a pair from its FP32 squared distance g2 (relative error below 2^-21.7 from the
-// int32 separations), falling back to the exact integer test only where that error could
-// matter: the bin is floor(sqrt(d2) / w) exactly (d2 >= T[k] <=> d2 >= (k w)^2 for integer
-// d2), and x = sqrt(g2) / w carries a relative error below 2^-21, so floor(x) is the bin
-// unless x lies within x 2^-20 of an integer. Returns -1 outside the histogram range.
-__device__ __forceinline__ int bin_of_fast(Sep sp, float g2, const long long *T, int nb, float inv,
-                                           long long tmax, float tmax_lo, float tmax_hi)
-{
-    if (g2 >= tmax_hi) return -1;
-    if (g2 >= tmax_lo && d2_of(sp) >= tmax) return -1;
-    const float x = sqrtf(g2) * inv;
-    const int k = (int)x;
-    const float f = x - (float)k, eps = x * 0x1p-20f;
-    if (f > eps && f < 1.f - eps && k < nb) return k;
-    return bin_of(d2_of(sp), g2, T, nb, inv);
-}
 
 __global__ void __launch_bounds__(kGcThreads) partial_gr_cells_kernel(GcArgs A)
 {
