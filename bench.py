@@ -642,7 +642,7 @@ def main():
                             "kernel": "partial_gr_kernel"},
             "measured_bounds": {
                 "grid_barrier_floor_us": barrier_ns * 1e-3,
-                "mc_ceiling_moves_per_s_at_32_per_barrier": 32.0 / (barrier_ns * 1e-9),
+                "mc_ceiling_moves_per_s_at_64_per_barrier": 64.0 / (barrier_ns * 1e-9),
                 "int32_xor_add_lane_ops_per_s": int_rate, "fp32_fma_lane_ops_per_s": fma_rate,
                 "note": "epsr_bench_barrier_floor (152 CTAs, the sweep's exchange alone) and "
                         "epsr_bench_alu_rate (independent xor+add / FMA chains); the roofline peak stays "

@@ -204,8 +204,9 @@ int epsr_mc_sweep_async(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t 
 int epsr_mc_status(epsr_box *box, int32_t *status, epsr_stream_t stream);
 /* Reads the running statistics without running moves (synchronises). */
 int epsr_mc_stats_get(epsr_box *box, epsr_mc_stats *stats, epsr_stream_t stream);
-/* Moves per speculative batch (1 .. 32; 0, the default: 32 for boxes swept by at least 32
- * CTAs, else 16): the sweep evaluates up to this many
+/* Moves per speculative batch (1 .. 64; 0, the default: 64 for boxes swept by at least 64
+ * CTAs, 32 for at least 32, else 16; a box swept by fewer than 8 CTAs takes at most 32):
+ * the sweep evaluates up to this many
  * consecutive moves with distinct molecules per grid barrier and resolves them in order
  * with exact pairwise corrections, so every value gives the sequential Metropolis chain
  * (up to FP32 rounding of dU). Host only. */

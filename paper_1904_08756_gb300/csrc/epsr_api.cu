@@ -751,7 +751,8 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     // fit, the partner slice (int4 per slot) and the home cell of every slot (uint16);
     // otherwise the slices and home cells live in global memory
     const size_t tables = (size_t)box->tbl_cap * sizeof(long long) + (size_t)box->ep_cap * sizeof(float) +
-                          (size_t)types_cap * (kMcCells + 1) * sizeof(unsigned) + (size_t)kMcCorrItems * sizeof(float);
+                          (size_t)types_cap * (kMcCells + 1) * sizeof(unsigned) +
+                          (size_t)kMcBatchMax * kMcBatchMax * sizeof(float) + (size_t)kMcCorrItems * sizeof(float);
     const size_t per_slot = sizeof(int4) + sizeof(unsigned short);
     size_t smem = (((size_t)slice_cap * per_slot + tables) + 15) & ~(size_t)15;
     const bool gslice = smem > kMcMaxDynSmem;

@@ -20,11 +20,12 @@ int set_cuda_error(cudaError_t e, const char *what);
 void note_launch();
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
-constexpr size_t kMcMaxDynSmem = 192 * 1024;   // with ~33 KB static: under the 227 KB per CTA
+constexpr size_t kMcMaxDynSmem = 176 * 1024;   // with about 44 KB of static shared memory, under the 227 KB per CTA
 // per-CTA barrier slot: the batch's partial dU (32 moves), then the pair-energy corrections
 // this CTA computed (at most 32 * 31 / 2 = 496 pairs)
-constexpr int kMcCorrPerCta = 496;        // batch-pair corrections (32 moves)
-constexpr int kMcSlotStride = 32 + kMcCorrPerCta;
+constexpr int kMcBatchMax = 64;           // moves per batch of the sweep, at most
+constexpr int kMcCorrPerCta = kMcBatchMax * (kMcBatchMax - 1) / 2;   // batch-pair corrections
+constexpr int kMcSlotStride = kMcBatchMax + kMcCorrPerCta;
 // correction items of one batch in shared memory (>= 496 pairs x 8 atoms)
 constexpr int kMcCorrItems = 4096;
 // partners staged per chunk in shared memory when the slices live in global memory

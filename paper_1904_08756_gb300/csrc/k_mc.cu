@@ -31,7 +31,8 @@ namespace epsr {
 
 constexpr int kMcThreads = 512;
 constexpr int kMcWarps = kMcThreads / 32;
-constexpr int kBatchMax = 32;                  // moves per batch: warp w takes moves w and w + 16
+constexpr int kBatchMax = kMcBatchMax;         // moves per batch: warp w takes moves w, w + 16, w + 32, w + 48
+constexpr int kPerWarp = kBatchMax / kMcWarps;  // moves per warp and batch
 constexpr int kMoveBlock = 128;                // move records staged in shared memory at once
 constexpr int kCorrItems = kMcCorrItems;       // >= 496 pairs x 8 atoms (coarse items at G = 1)
 constexpr int kStageChunk = kMcStageChunk;     // partners per staged chunk (slices in global memory)
@@ -39,8 +40,8 @@ constexpr int kEscMax = 256;                   // escapee list capacity per CTA 
 constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: escapee
 static_assert(kMcCorrPerCta == kBatchMax * (kBatchMax - 1) / 2 && kMcSlotStride == kBatchMax + kMcCorrPerCta,
               "barrier slot layout");
-static_assert(kMcThreads == 16 * kBatchMax, "gather: 16 threads per move");
-static_assert(kBatchMax == 2 * kMcWarps, "phase B: two moves per warp");
+static_assert(kMcThreads == 8 * kBatchMax, "gather: 8 threads per move");
+static_assert(kPerWarp == 4 && kBatchMax == 64, "phase A / F: two moves per lane of warp 0; phase B: pairs of moves per warp");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
 __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n_boxes,
@@ -134,7 +135,6 @@ struct McShared {
     int mm;                                  // largest molecule of the batch
     MoveRec mv[kMoveBlock];                  // staged move records [mv_base, mv_base + kMoveBlock)
     float acc_du[kMoveBlock];                // rank 0: dU of each decided move if accepted, else 0
-    float corr[kBatchMax][kBatchMax];
     float dU[kBatchMax];
     int abort_flag;
     int cb[9];                               // cell boundaries ceil(j L / 8)
@@ -144,6 +144,8 @@ struct McShared {
     long long st_att, st_acc, st_nonfinite;
     double st_sum;
 };
+static_assert(sizeof(McShared) + kMcMaxDynSmem <= 227 * 1024, "static plus dynamic shared memory per CTA");
+
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -532,7 +534,6 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         sh.blk[nt] = b;
     }
     __syncthreads();
-    const int n_slice = sh.blk[nt];
 
     // shared memory: partner slice {x, y, z, type | atom << 3}, thresholds, empirical potential
     int4 *slice = GSLICE ? A.slice_g + (size_t)cta * A.slice_cap : reinterpret_cast<int4 *>(dyn);
@@ -552,7 +553,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     // home cell of every slot, cell boundaries; cell queries only where some pair row has
     // no Lennard-Jones term but a Coulomb or empirical-potential one
     unsigned *cst = reinterpret_cast<unsigned *>(ep + A.ep_cap);
-    float *corr_part = reinterpret_cast<float *>(cst + A.types_cap * (kMcCells + 1));   // [kCorrItems]
+    float (*corr)[kBatchMax] = reinterpret_cast<float (*)[kBatchMax]>(cst + A.types_cap * (kMcCells + 1));
+    float *corr_part = &corr[kBatchMax][0];                                              // [kCorrItems]
     // GSLICE: staged chunk of partners [kStageChunk], on the next 16-byte boundary (the host
     // sizes the dynamic shared memory as the 16-byte-rounded tables plus the chunk)
     int4 *stage = reinterpret_cast<int4 *>((reinterpret_cast<uintptr_t>(corr_part + kCorrItems) + 15) &
@@ -587,9 +589,11 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     }
     __syncthreads();
 
-    // moves per batch: as set, else 32 for large CTA groups (the per-batch phases amortise
-    // over more moves) and 16 for small ones (corrections grow with the square of the batch)
-    const int batch_k = A.batch_k > 0 ? A.batch_k : (G >= 32 ? kBatchMax : kBatchMax / 2);
+    // moves per batch: as set, else 64 for large CTA groups (the per-batch phases amortise
+    // over more moves), 32 for middling and 16 for small ones (corrections grow with the
+    // square of the batch); above 32 only with 8 or more CTAs per box, so that a CTA's share
+    // of the batch-pair corrections fits its item buffer
+    const int batch_k = min(A.batch_k > 0 ? A.batch_k : (G >= 64 ? 64 : G >= 32 ? 32 : 16), G >= 8 ? kBatchMax : 32);
     const MoveRec *moves = A.moves + (size_t)box * A.chunk;
     unsigned seq = 0;
     int par = 0;
@@ -608,20 +612,27 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             __syncthreads();
         }
         // ---- A. molecules of the batch; it ends before the first repeated molecule -----------
+        // (warp 0: lane l checks moves l and l + 32 against every earlier move of the batch)
         if (warp == 0) {
-            int my = -1 - lane;
-            bool dup = false;
+            const MoveRec *mv = sh.mv + (t0 - mv_base);
+            int my0 = -1 - lane, my1 = -33 - lane;
+            bool dup0 = false, dup1 = false;
             if (lane < kmax) {
-                const MoveRec *mv = sh.mv + (t0 - mv_base);
-                my = mv[lane].mol;
-                for (int k1 = 0; k1 < lane; ++k1) dup |= mv[k1].mol == my;
+                my0 = mv[lane].mol;
+                for (int k1 = 0; k1 < lane; ++k1) dup0 |= mv[k1].mol == my0;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, dup && lane < kmax);
+            if (lane + 32 < kmax) {
+                my1 = mv[lane + 32].mol;
+                for (int k1 = 0; k1 < lane + 32; ++k1) dup1 |= mv[k1].mol == my1;
+            }
+            const unsigned b0 = __ballot_sync(0xffffffffu, dup0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, dup1);
             if (lane == 0) {
-                sh.nb[par] = bal ? __ffs(bal) - 1 : kmax;
+                sh.nb[par] = b0 ? __ffs(b0) - 1 : b1 ? 32 + __ffs(b1) - 1 : kmax;
                 sh.mm = 0;
             }
-            if (lane < kBatchMax) sh.mol[par][lane] = my;
+            sh.mol[par][lane] = my0;
+            sh.mol[par][lane + 32] = my1;
         }
         __syncthreads();
         const int nb = sh.nb[par];
@@ -630,19 +641,22 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         // batch's accepted move of the molecule if there is one (its global update may not be
         // visible yet), else from the global coordinates.
         {
-            int4 oc[2];
-            int sp[2];
+            int4 oc[kPerWarp];
+            int sp[kPerWarp];
+            const int q = par ^ 1;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kPerWarp; ++h) {
                 const int k = warp + h * kMcWarps;
                 oc[h] = make_int4(0, 0, 0, 0);
                 sp[h] = 0;
                 if (k < nb) {
                     const MoveRec &mr = sh.mv[t0 + k - mv_base];
-                    const int q = par ^ 1;
-                    const bool hit = lane < sh.nb[q] && sh.acc[q][lane] && sh.mol[q][lane] == sh.mol[par][k];
-                    const unsigned hb = __ballot_sync(0xffffffffu, hit);
-                    const int pidx = hb ? 31 - __clz(hb) : -1;   // molecules of a batch are distinct
+                    const int mol = sh.mol[par][k];
+                    const bool hit0 = lane < sh.nb[q] && sh.acc[q][lane] && sh.mol[q][lane] == mol;
+                    const bool hit1 = lane + 32 < sh.nb[q] && sh.acc[q][lane + 32] && sh.mol[q][lane + 32] == mol;
+                    const unsigned h0 = __ballot_sync(0xffffffffu, hit0), h1 = __ballot_sync(0xffffffffu, hit1);
+                    // molecules of a batch are distinct: at most one hit
+                    const int pidx = h1 ? 63 - __clz(h1) : h0 ? 31 - __clz(h0) : -1;
                     if (lane < mr.m) {
                         oc[h] = pidx >= 0 ? sh.newp[q][pidx][lane] : __ldcg(&A.coords[bx.atom0 + mr.a0 + lane]);
                         sp[h] = A.pos_of[bx.atom0 + mr.a0 + lane] - (int)bx.atom0;
@@ -650,7 +664,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 }
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kPerWarp; ++h) {
                 const int k = warp + h * kMcWarps;
                 if (k < nb && lane < sh.mv[t0 + k - mv_base].m) {
                     sh.oldp[k][lane] = oc[h];
@@ -659,13 +673,15 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             }
             __syncwarp();
         }
-        // Trial coordinates: with molecules of at most 5 atoms the two moves of a warp run side
-        // by side in its half-warps, otherwise one after the other with the whole warp.
-        const int m_lo = warp < nb ? sh.mv[t0 + warp - mv_base].m : 0;
-        const int m_hi = warp + kMcWarps < nb ? sh.mv[t0 + warp + kMcWarps - mv_base].m : 0;
-        const bool halves = m_lo <= 5 && m_hi <= 5;
-        for (int rr = 0; rr < (halves ? 1 : 2); ++rr) {
-            const int k = warp + (halves ? lane >> 4 : rr) * kMcWarps;
+        // Trial coordinates: with molecules of at most 5 atoms the moves of a warp run two at a
+        // time in its half-warps, otherwise one after the other with the whole warp.
+        int m_max = 0;
+#pragma unroll
+        for (int h = 0; h < kPerWarp; ++h)
+            if (warp + h * kMcWarps < nb) m_max = max(m_max, (int)sh.mv[t0 + warp + h * kMcWarps - mv_base].m);
+        const bool halves = m_max <= 5;
+        for (int rr = 0; rr < (halves ? kPerWarp / 2 : kPerWarp); ++rr) {
+            const int k = warp + (halves ? 2 * rr + (lane >> 4) : rr) * kMcWarps;
             const int sl = halves ? lane & 15 : lane;
             const bool act = k < nb;
             const MoveRec &mr = sh.mv[t0 + (act ? k : 0) - mv_base];
@@ -759,7 +775,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 if (a < sh.natoms[k] && b < sh.natoms[k1]) {
                     const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
                     const int4 p1 = side ? sh.oldp[k1][b] : sh.newp[par][k1][b];
-                    v = pair_du_cold(sep(na, p1, L), sep(oa, p1, L), bx.row[na.w * kMaxTypes + p1.w], bx, T, ep);
+                    v = pair_du(sep(na, p1, L), sep(oa, p1, L), bx.row[na.w * kMaxTypes + p1.w], bx, T, ep);
                 }
                 corr_part[it] = v;
             }
@@ -787,7 +803,9 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             // slices in global memory: the Lennard-Jones partners are staged chunk by chunk in
             // shared memory and every warp scans each chunk for its moves, so a batch reads the
             // slice once instead of once per move; then each move's near-only rows
-            float accL[2] = {0.f, 0.f};
+            float accL[kPerWarp];
+#pragma unroll
+            for (int q = 0; q < kPerWarp; ++q) accL[q] = 0.f;
             for (int t = 0; t < nt; ++t) {
                 for (int c0 = sh.blk[t]; c0 < sh.blk[t + 1]; c0 += kStageChunk) {
                     const int nc = min(kStageChunk, sh.blk[t + 1] - c0);
@@ -795,7 +813,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     for (int i = tid; i < nc; i += kMcThreads) stage[i] = __ldcg(&slice[c0 + i]);
                     __syncthreads();
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
+                    for (int q = 0; q < kPerWarp; ++q) {
                         const int k = warp + q * kMcWarps;
                         if (k >= nb) continue;
                         const int m = sh.natoms[k];
@@ -812,7 +830,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             ci.margin = A.cell_margin;
             ci.on = sh.cells_on != 0;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < kPerWarp; ++q) {
                 const int k = warp + q * kMcWarps;
                 if (k >= nb) continue;
                 const int m = sh.natoms[k];
@@ -870,7 +888,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             if (warp == 0) {
                 const bool arrive = cta != A.skip_arrival_cta;
                 if (arrive) {
-                    if (lane < nb) ps[(size_t)lane * A.grid + cta] = sh.part[lane];
+                    for (int k = lane; k < nb; k += 32) ps[(size_t)k * A.grid + cta] = sh.part[k];
                     for (int u = lane; u < n_local; u += 32) cs[rank + u * G] = corr_sum(corr_part, u, mm, fine);
                 }
                 __syncwarp();
@@ -897,61 +915,80 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             __syncthreads();
             if (sh.abort_flag) return;
             {
-                // 16 threads per move, each summing every 16th CTA's partial, then a fixed
+                // 8 threads per move, each summing every 8th CTA's partial, then a fixed
                 // shuffle tree: the order of the FP32 sum is the same in every run
-                const int k = tid >> 4, sub = tid & 15;
+                const int k = tid >> 3, sub = tid & 7;
                 float v = 0.f;
                 if (k < nb) {
                     const float *pk = ps + (size_t)k * A.grid + bx.cta0;
 #pragma unroll 4
-                    for (int r = sub; r < G; r += 16) v += __ldcg(&pk[r]);
+                    for (int r = sub; r < G; r += 8) v += __ldcg(&pk[r]);
                 }
 #pragma unroll
-                for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (sub == 0 && k < nb) sh.base[k] = v;
             }
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 const int k = pair_hi(pq);
-                sh.corr[pq - k * (k - 1) / 2][k] = __ldcg(&cs[pq]);
+                corr[pq - k * (k - 1) / 2][k] = __ldcg(&cs[pq]);
             }
         } else {
             for (int k = tid; k < nb; k += kMcThreads) sh.base[k] = sh.part[k];
             for (int pq = tid; pq < npq; pq += kMcThreads) {
                 const int k = pair_hi(pq);
-                sh.corr[pq - k * (k - 1) / 2][k] = corr_sum(corr_part, pq, mm, fine);
+                corr[pq - k * (k - 1) / 2][k] = corr_sum(corr_part, pq, mm, fine);
             }
         }
         __syncthreads();
-        // ---- F. Metropolis decisions of the batch, in order (warp 0, lane k = move k) -------
+        // ---- F. Metropolis decisions of the batch, in order (warp 0: lane l holds moves l
+        // and l + 32); move j's dU includes the corrections of every earlier accepted move
         if (warp == 0) {
-            float d = lane < nb ? sh.base[lane] + sh.intra[lane] : 0.f;
-            const float thr = lane < nb ? sh.thr[lane] : 0.f;
-            float cj[kBatchMax];
-#pragma unroll
-            for (int j = 0; j < kBatchMax; ++j) cj[j] = (lane > j && lane < nb) ? sh.corr[j][lane] : 0.f;
-            int accepted = 0;
-#pragma unroll
-            for (int j = 0; j < kBatchMax; ++j) {
+            const bool in0 = lane < nb, in1 = lane + 32 < nb;
+            float d0 = in0 ? sh.base[lane] + sh.intra[lane] : 0.f;
+            float d1 = in1 ? sh.base[lane + 32] + sh.intra[lane + 32] : 0.f;
+            const float thr0 = in0 ? sh.thr[lane] : 0.f, thr1 = in1 ? sh.thr[lane + 32] : 0.f;
+            int acc0 = 0, acc1 = 0;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
                 if (j < nb) {
-                    const int aj = __shfl_sync(0xffffffffu, (d <= 0.f) || (d < thr), j);
-                    if (lane == j) accepted = aj;
-                    if (aj) d += cj[j];
+                    const float c0 = corr[j][lane], c1 = corr[j][lane + 32];
+                    const int aj = __shfl_sync(0xffffffffu, (d0 <= 0.f) || (d0 < thr0), j);
+                    if (lane == j) acc0 = aj;
+                    if (aj) {
+                        if (lane > j) d0 += c0;
+                        d1 += c1;
+                    }
                 }
             }
-            if (lane < nb) {
-                sh.dU[lane] = d;
-                sh.acc[par][lane] = accepted;
+#pragma unroll 8
+            for (int j = 32; j < kBatchMax; ++j) {
+                if (j < nb) {
+                    const float c1 = corr[j][lane + 32];
+                    const int aj = __shfl_sync(0xffffffffu, (d1 <= 0.f) || (d1 < thr1), j - 32);
+                    if (lane == j - 32) acc1 = aj;
+                    if (aj && lane + 32 > j) d1 += c1;
+                }
+            }
+            if (in0) {
+                sh.dU[lane] = d0;
+                sh.acc[par][lane] = acc0;
+            }
+            if (in1) {
+                sh.dU[lane + 32] = d1;
+                sh.acc[par][lane + 32] = acc1;
             }
             if (rank == 0) {
                 // counts now; the FP64 sum of accepted dU once per staged block of moves
-                const unsigned in = lane < nb ? 1u : 0u;
-                const unsigned b_acc = __ballot_sync(0xffffffffu, in && accepted);
-                const unsigned b_nf = __ballot_sync(0xffffffffu, in && !isfinite(d));
-                if (in) sh.acc_du[t0 - mv_base + lane] = accepted ? d : 0.f;
+                const unsigned b_acc = __ballot_sync(0xffffffffu, in0 && acc0) ,
+                               b_acc1 = __ballot_sync(0xffffffffu, in1 && acc1);
+                const unsigned b_nf = __ballot_sync(0xffffffffu, in0 && !isfinite(d0)),
+                               b_nf1 = __ballot_sync(0xffffffffu, in1 && !isfinite(d1));
+                if (in0) sh.acc_du[t0 - mv_base + lane] = acc0 ? d0 : 0.f;
+                if (in1) sh.acc_du[t0 - mv_base + lane + 32] = acc1 ? d1 : 0.f;
                 if (lane == 0) {
                     sh.st_att += nb;
-                    sh.st_acc += __popc(b_acc);
-                    sh.st_nonfinite += __popc(b_nf);
+                    sh.st_acc += __popc(b_acc) + __popc(b_acc1);
+                    sh.st_nonfinite += __popc(b_nf) + __popc(b_nf1);
                 }
             }
         }

@@ -1,7 +1,7 @@
 // k_micro.cu -- two measurements that bound the Monte Carlo sweep on this GPU, run by the
 // library's own kernels so that they see the same code generation as the sweep:
 //  - the grid-barrier floor: a cooperative persistent grid that does nothing but the sweep's
-//    per-batch exchange (32 partials and the pair corrections to the slot buffer, release add
+//    per-batch exchange (64 partials and the pair corrections to the slot buffer, release add
 //    on a counter, acquire poll, fixed-order gather), i.e. the least time per batch;
 //  - the integer and FP32 issue rates: independent dependency chains of 32-bit adds or FP32
 //    fused multiply-adds in every lane, counted as lane-operations per second.
@@ -11,9 +11,9 @@
 namespace epsr {
 
 constexpr int kMicroThreads = 512;
-constexpr int kMicroPartials = 32;             // partials per CTA (moves per batch)
-constexpr int kMicroCorr = 496;                // batch-pair corrections per group
-static_assert(kMicroThreads == 16 * kMicroPartials, "16 threads per partial");
+constexpr int kMicroPartials = kMcBatchMax;    // partials per CTA (moves per batch)
+constexpr int kMicroCorr = kMcCorrPerCta;      // batch-pair corrections per group
+static_assert(kMicroThreads == 8 * kMicroPartials, "8 threads per partial");
 
 // Slot buffer per parity: partials [kMicroPartials][G], then kMicroCorr corrections, pair pq
 // written by CTA pq mod G; the layout and the order of operations are the sweep's.
@@ -36,7 +36,7 @@ barrier_floor_kernel(unsigned *counter, float *slots, int iters, unsigned long l
         float *ps = slots + (size_t)(it & 1) * ((size_t)kMicroPartials * G + kMicroCorr);
         float *cs = ps + (size_t)kMicroPartials * G;
         if (warp == 0) {
-            ps[(size_t)lane * G + cta] = part[lane];
+            for (int k = lane; k < kMicroPartials; k += 32) ps[(size_t)k * G + cta] = part[k];
             for (int u = lane; u < n_local; u += 32) cs[cta + u * G] = (float)u;
             __syncwarp();
             if (lane == 0) {
@@ -60,12 +60,12 @@ barrier_floor_kernel(unsigned *counter, float *slots, int iters, unsigned long l
         __syncthreads();
         if (abort_flag) return;
         {
-            const int k = tid >> 4, sub = tid & 15;
+            const int k = tid >> 3, sub = tid & 7;
             float v = 0.f;
 #pragma unroll 4
-            for (int r = sub; r < G; r += 16) v += __ldcg(&ps[(size_t)k * G + r]);
+            for (int r = sub; r < G; r += 8) v += __ldcg(&ps[(size_t)k * G + r]);
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (sub == 0) base[k] = v;
         }
         for (int pq = tid; pq < kMicroCorr; pq += kMicroThreads) corr[pq] = __ldcg(&cs[pq]);

@@ -197,6 +197,20 @@ def test_mc_replay_small_water(small_water, batch):
     assert abs(sdu - float(log[0]["dU"][log[0]["accepted"] == 1].astype(np.float64).sum())) < 1e-6 * max(1, abs(sdu))
 
 
+@pytest.mark.parametrize("batch", [64, 48])
+def test_mc_replay_small_water_wide_batches(small_water, batch):
+    """Batches above 32 moves (16 CTAs for the 900-atom box): the same sequential chain."""
+    box = epsr.Box(small_water)
+    box.epsr_mc_set_ctas(16)
+    box.epsr_mc_set_batch(batch)
+    stats, log = run_logged(box, 2000, seed=777)
+    att, acc, nonfin, sdu = stats[0]
+    assert att == 2000 and nonfin == 0 and 0 < acc < 2000
+    ob, checked, worst, flips = replay(small_water, small_water.xyz, log[0], 777)
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+    assert flips <= 2
+
+
 @pytest.mark.parametrize("batch", [0, 16, 1])
 def test_mc_replay_flexible_water(batch):
     """Flexible water (Sec. 3.1): molecule translations, rotations and single-atom moves,
