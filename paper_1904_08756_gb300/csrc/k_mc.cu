@@ -41,6 +41,8 @@ constexpr int kEscFlag = (int)0x80000000u;     // bit 31 of a slice entry's .w: 
 static_assert(kMcCorrPerCta == kBatchMax * (kBatchMax - 1) / 2 && kMcSlotStride == kBatchMax + kMcCorrPerCta,
               "barrier slot layout");
 static_assert(kMcThreads == 8 * kBatchMax, "gather: 8 threads per move");
+constexpr int kGatherLoads = 20;                // partials per gather thread in flight (CTA groups up to 160)
+constexpr int kCorrLoads = (kMcCorrPerCta + kMcThreads - 1) / kMcThreads;   // corrections per thread
 static_assert(kPerWarp == 4 && kBatchMax == 64, "phase A / F: two moves per lane of warp 0; phase B: pairs of moves per warp");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
@@ -113,6 +115,7 @@ struct McShared {
     // batch records, double buffered by batch parity: the previous batch's accepted moves
     // are the "pending" updates whose global writes may not yet be visible
     int nb[2];
+    int nb_min;                              // first move of the batch that repeats a molecule
     int mol[2][kBatchMax];
     int acc[2][kBatchMax];
     int4 newp[2][kBatchMax][kMaxMolAtoms];
@@ -167,6 +170,10 @@ __device__ __forceinline__ void block_sum_du(const float *v, int n, int lane, do
 // Correction of local pair u: the sum over atoms a of move k of the sum over atoms b of move
 // k1 of [du(a; b new) - du(a; b old)], in that order. `fine` items hold each du separately;
 // otherwise each item already holds the sum over b (same operations, same order).
+// Metropolis test of a move with energy change d against its threshold thr = -kT ln u:
+// accepted when d <= 0 or d < thr (Sec. 2.2); false for a NaN d.
+__device__ __forceinline__ bool metropolis(float d, float thr) { return (d <= 0.f) || (d < thr); }
+
 // Later move k of batch pair pq = k (k - 1) / 2 + k1 (0 <= k1 < k): a float estimate of
 // the root of k (k - 1) / 2 = pq, corrected by one step either way.
 __device__ __forceinline__ int pair_hi(int pq)
@@ -507,6 +514,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     if (tid == 0) {
         sh.bx = A.boxes[box];
         sh.nb[0] = sh.nb[1] = 0;
+        sh.nb_min = 1 << 30;
         sh.abort_flag = 0;
         sh.st_att = sh.st_acc = sh.st_nonfinite = 0;
         sh.st_sum = 0.0;
@@ -612,30 +620,19 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             __syncthreads();
         }
         // ---- A. molecules of the batch; it ends before the first repeated molecule -----------
-        // (warp 0: lane l checks moves l and l + 32 against every earlier move of the batch)
-        if (warp == 0) {
+        // (every pair of the batch's candidate moves tested once, across the CTA)
+        {
             const MoveRec *mv = sh.mv + (t0 - mv_base);
-            int my0 = -1 - lane, my1 = -33 - lane;
-            bool dup0 = false, dup1 = false;
-            if (lane < kmax) {
-                my0 = mv[lane].mol;
-                for (int k1 = 0; k1 < lane; ++k1) dup0 |= mv[k1].mol == my0;
+            for (int pq = tid; pq < kmax * (kmax - 1) / 2; pq += kMcThreads) {
+                const int k = pair_hi(pq), k1 = pq - k * (k - 1) / 2;
+                if (mv[k].mol == mv[k1].mol) atomicMin(&sh.nb_min, k);
             }
-            if (lane + 32 < kmax) {
-                my1 = mv[lane + 32].mol;
-                for (int k1 = 0; k1 < lane + 32; ++k1) dup1 |= mv[k1].mol == my1;
-            }
-            const unsigned b0 = __ballot_sync(0xffffffffu, dup0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, dup1);
-            if (lane == 0) {
-                sh.nb[par] = b0 ? __ffs(b0) - 1 : b1 ? 32 + __ffs(b1) - 1 : kmax;
-                sh.mm = 0;
-            }
-            sh.mol[par][lane] = my0;
-            sh.mol[par][lane + 32] = my1;
+            if (tid < kBatchMax) sh.mol[par][tid] = tid < kmax ? mv[tid].mol : -1 - tid;
+            if (tid == 0) sh.mm = 0;
         }
         __syncthreads();
-        const int nb = sh.nb[par];
+        const int nb = min(kmax, sh.nb_min);
+        if (tid == 0) sh.nb[par] = nb;
         // ---- B. current and trial coordinates of each moved molecule (integer arithmetic) ----
         // Current coordinates of a warp's two molecules, loaded together: from the previous
         // batch's accepted move of the molecule if there is one (its global update may not be
@@ -917,20 +914,40 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             {
                 // 8 threads per move, each summing every 8th CTA's partial, then a fixed
                 // shuffle tree: the order of the FP32 sum is the same in every run
+                // (the loads of a thread are all issued before the first add: one L2 round trip)
                 const int k = tid >> 3, sub = tid & 7;
                 float v = 0.f;
                 if (k < nb) {
                     const float *pk = ps + (size_t)k * A.grid + bx.cta0;
-#pragma unroll 4
-                    for (int r = sub; r < G; r += 8) v += __ldcg(&pk[r]);
+                    float pv[kGatherLoads];
+#pragma unroll
+                    for (int i = 0; i < kGatherLoads; ++i) {
+                        const int r = sub + 8 * i;
+                        pv[i] = r < G ? __ldcg(&pk[r]) : 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kGatherLoads; ++i) v += pv[i];
+                    for (int r = sub + 8 * kGatherLoads; r < G; r += 8) v += __ldcg(&pk[r]);
                 }
 #pragma unroll
                 for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (sub == 0 && k < nb) sh.base[k] = v;
             }
-            for (int pq = tid; pq < npq; pq += kMcThreads) {
-                const int k = pair_hi(pq);
-                corr[pq - k * (k - 1) / 2][k] = __ldcg(&cs[pq]);
+            {
+                float cv[kCorrLoads];
+#pragma unroll
+                for (int i = 0; i < kCorrLoads; ++i) {
+                    const int pq = tid + i * kMcThreads;
+                    cv[i] = pq < npq ? __ldcg(&cs[pq]) : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < kCorrLoads; ++i) {
+                    const int pq = tid + i * kMcThreads;
+                    if (pq < npq) {
+                        const int k = pair_hi(pq);
+                        corr[pq - k * (k - 1) / 2][k] = cv[i];
+                    }
+                }
             }
         } else {
             for (int k = tid; k < nb; k += kMcThreads) sh.base[k] = sh.part[k];
@@ -941,32 +958,64 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         }
         __syncthreads();
         // ---- F. Metropolis decisions of the batch, in order (warp 0: lane l holds moves l
-        // and l + 32); move j's dU includes the corrections of every earlier accepted move
+        // and l + 32); move j's dU includes the corrections of every earlier accepted move.
+        // Fast path: when no move's decision can change with any subset of the earlier
+        // corrections (|dU - threshold| beyond the sum of their magnitudes plus the FP32
+        // rounding of that many additions), every decision is taken at once and each dU is
+        // summed in the chain's order; otherwise the decisions run one after the other.
         if (warp == 0) {
             const bool in0 = lane < nb, in1 = lane + 32 < nb;
             float d0 = in0 ? sh.base[lane] + sh.intra[lane] : 0.f;
             float d1 = in1 ? sh.base[lane + 32] + sh.intra[lane + 32] : 0.f;
             const float thr0 = in0 ? sh.thr[lane] : 0.f, thr1 = in1 ? sh.thr[lane + 32] : 0.f;
             int acc0 = 0, acc1 = 0;
-#pragma unroll 8
-            for (int j = 0; j < 32; ++j) {
-                if (j < nb) {
+            float s0 = 0.f, s1 = 0.f, s0b = 0.f, s1b = 0.f;   // two accumulators each: shorter chains
+#pragma unroll
+            for (int j = 0; j < kBatchMax - 1; j += 2) {
+                const float c0 = corr[j][lane], c1 = corr[j][lane + 32];
+                const float e0 = corr[j + 1][lane], e1 = corr[j + 1][lane + 32];
+                if (j < lane) s0 += fabsf(c0);
+                if (j < lane + 32) s1 += fabsf(c1);
+                if (j + 1 < lane) s0b += fabsf(e0);
+                if (j + 1 < lane + 32) s1b += fabsf(e1);
+            }
+            s0 += s0b;
+            s1 += s1b;
+            const float w0 = s0 + (fabsf(d0) + s0) * 0x1p-16f, w1 = s1 + (fabsf(d1) + s1) * 0x1p-16f;
+            const bool sure0 = !in0 || metropolis(d0 + w0, thr0) || !metropolis(d0 - w0, thr0);
+            const bool sure1 = !in1 || metropolis(d1 + w1, thr1) || !metropolis(d1 - w1, thr1);
+            if (__all_sync(0xffffffffu, sure0 && sure1)) {
+                acc0 = in0 && metropolis(d0, thr0);
+                acc1 = in1 && metropolis(d1, thr1);
+                const unsigned a0 = __ballot_sync(0xffffffffu, acc0), a1 = __ballot_sync(0xffffffffu, acc1);
+#pragma unroll
+                for (int j = 0; j < kBatchMax - 1; ++j) {
                     const float c0 = corr[j][lane], c1 = corr[j][lane + 32];
-                    const int aj = __shfl_sync(0xffffffffu, (d0 <= 0.f) || (d0 < thr0), j);
-                    if (lane == j) acc0 = aj;
-                    if (aj) {
-                        if (lane > j) d0 += c0;
-                        d1 += c1;
+                    const bool aj = j < 32 ? (a0 >> j) & 1u : (a1 >> (j - 32)) & 1u;
+                    if (aj && j < lane) d0 += c0;
+                    if (aj && j < lane + 32) d1 += c1;
+                }
+            } else {
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) {
+                    if (j < nb) {
+                        const float c0 = corr[j][lane], c1 = corr[j][lane + 32];
+                        const int aj = __shfl_sync(0xffffffffu, metropolis(d0, thr0), j);
+                        if (lane == j) acc0 = aj;
+                        if (aj) {
+                            if (lane > j) d0 += c0;
+                            d1 += c1;
+                        }
                     }
                 }
-            }
 #pragma unroll 8
-            for (int j = 32; j < kBatchMax; ++j) {
-                if (j < nb) {
-                    const float c1 = corr[j][lane + 32];
-                    const int aj = __shfl_sync(0xffffffffu, (d1 <= 0.f) || (d1 < thr1), j - 32);
-                    if (lane == j - 32) acc1 = aj;
-                    if (aj && lane + 32 > j) d1 += c1;
+                for (int j = 32; j < kBatchMax; ++j) {
+                    if (j < nb) {
+                        const float c1 = corr[j][lane + 32];
+                        const int aj = __shfl_sync(0xffffffffu, metropolis(d1, thr1), j - 32);
+                        if (lane == j - 32) acc1 = aj;
+                        if (aj && lane + 32 > j) d1 += c1;
+                    }
                 }
             }
             if (in0) {
@@ -1034,6 +1083,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 lg->trial[a][0] = p.x; lg->trial[a][1] = p.y; lg->trial[a][2] = p.z;
             }
         }
+        if (tid == 0) sh.nb_min = 1 << 30;      // every thread read it before phase B
         __syncthreads();
         t0 += nb;
     }

@@ -61,14 +61,25 @@ barrier_floor_kernel(unsigned *counter, float *slots, int iters, unsigned long l
         if (abort_flag) return;
         {
             const int k = tid >> 3, sub = tid & 7;
-            float v = 0.f;
-#pragma unroll 4
-            for (int r = sub; r < G; r += 8) v += __ldcg(&ps[(size_t)k * G + r]);
+            float v = 0.f, pv[20];
+#pragma unroll
+            for (int i = 0; i < 20; ++i) pv[i] = sub + 8 * i < G ? __ldcg(&ps[(size_t)k * G + sub + 8 * i]) : 0.f;
+#pragma unroll
+            for (int i = 0; i < 20; ++i) v += pv[i];
+            for (int r = sub + 160; r < G; r += 8) v += __ldcg(&ps[(size_t)k * G + r]);
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (sub == 0) base[k] = v;
         }
-        for (int pq = tid; pq < kMicroCorr; pq += kMicroThreads) corr[pq] = __ldcg(&cs[pq]);
+        {
+            constexpr int kLoads = (kMicroCorr + kMicroThreads - 1) / kMicroThreads;
+            float cv[kLoads];
+#pragma unroll
+            for (int i = 0; i < kLoads; ++i) cv[i] = tid + i * kMicroThreads < kMicroCorr ? __ldcg(&cs[tid + i * kMicroThreads]) : 0.f;
+#pragma unroll
+            for (int i = 0; i < kLoads; ++i)
+                if (tid + i * kMicroThreads < kMicroCorr) corr[tid + i * kMicroThreads] = cv[i];
+        }
         __syncthreads();
         if (tid < kMicroPartials) acc += base[tid] + corr[tid];
     }
