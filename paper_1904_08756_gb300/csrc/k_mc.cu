@@ -688,25 +688,31 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 const int4 *op = sh.oldp[k];
                 int coord;
                 if (mr.kind == 1) {
-                    const int base[3] = {op[0].x, op[0].y, op[0].z};
-                    long long sum[3] = {0, 0, 0}, mine[3] = {0, 0, 0};
+                    // minimum-image offsets from atom 0, summed over the molecule, and this atom's
+                    // own (per-axis scalars, so that the lane's axis a selects without an array)
+                    const int4 b0 = op[0];
+                    long long sx = 0, sy = 0, sz = 0, ox = 0, oy = 0, oz = 0;
                     for (int i = 0; i < m; ++i) {
-                        const int c[3] = {op[i].x, op[i].y, op[i].z};
-                        for (int b = 0; b < 3; ++b) {
-                            const long long o = mi_signed((long long)c[b] - base[b], L);
-                            sum[b] += o;
-                            if (i == kk) mine[b] = o;
-                        }
+                        const int4 c = op[i];
+                        const long long dx = mi_signed((long long)c.x - b0.x, L);
+                        const long long dy = mi_signed((long long)c.y - b0.y, L);
+                        const long long dz = mi_signed((long long)c.z - b0.z, L);
+                        sx += dx; sy += dy; sz += dz;
+                        if (i == kk) { ox = dx; oy = dy; oz = dz; }
                     }
-                    long long num = sum[a] * 1073741824LL;
-                    for (int b = 0; b < 3; ++b) num += (long long)mr.R[3 * a + b] * ((long long)m * mine[b] - sum[b]);
+                    const int *Ra = mr.R + 3 * a;
+                    long long num = (a == 0 ? sx : a == 1 ? sy : sz) * 1073741824LL;
+                    num += (long long)Ra[0] * ((long long)m * ox - sx);
+                    num += (long long)Ra[1] * ((long long)m * oy - sy);
+                    num += (long long)Ra[2] * ((long long)m * oz - sz);
                     // floor((num + m 2^29) / 2^30) fits in 32 bits; then floor division by m
                     const int hi = (int)((num + (long long)m * 536870912LL) >> 30);
-                    coord = wrap_coord((long long)base[a] + floordiv32(hi, m) + mr.shift[a], L);
+                    const int base_a = reinterpret_cast<const int *>(op)[a];
+                    coord = wrap_coord((long long)base_a + floordiv32(hi, m) + mr.shift[a], L);
                 } else {
-                    const int c[3] = {op[kk].x, op[kk].y, op[kk].z};
+                    const int c_a = reinterpret_cast<const int *>(op)[4 * kk + a];
                     const bool moved = mr.kind != 2 || kk == mr.atom;
-                    coord = wrap_coord((long long)c[a] + (moved ? mr.shift[a] : 0), L);
+                    coord = wrap_coord((long long)c_a + (moved ? mr.shift[a] : 0), L);
                 }
                 int *dst = reinterpret_cast<int *>(&sh.newp[par][k][kk]);
                 dst[a] = coord;
