@@ -238,8 +238,8 @@ int epsr_launch_count(uint64_t *count);
 /* ---- measurements of this GPU (no counterpart in the paper) ------------------------------
  * epsr_bench_barrier_floor: the least time of one batch exchange of the Monte Carlo sweep:
  * `ctas` co-resident CTAs of 512 threads repeat, `iters` times, nothing but the sweep's grid
- * barrier (16 partials to a slot, release add, relaxed poll, acquire fence, fixed-order
- * gather). Returns ns per barrier; EPSR_EINVAL if the CTAs cannot be co-resident,
+ * barrier (64 partials and the batch-pair corrections to the exchange buffer, release add,
+ * acquire poll, fixed-order gather). Returns ns per barrier; EPSR_EINVAL if the CTAs cannot be co-resident,
  * EPSR_ETIMEOUT if a wait exceeded 2 s. Synchronises.
  * epsr_bench_alu_rate: lane-operations per second of independent chains in every lane on
  * every SM; kind 0 = 32-bit integer exclusive-or/add pairs, 1 = FP32 fused multiply-adds.

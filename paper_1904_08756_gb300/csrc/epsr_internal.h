@@ -21,12 +21,14 @@ void note_launch();
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
 constexpr size_t kMcMaxDynSmem = 176 * 1024;   // with about 44 KB of static shared memory, under the 227 KB per CTA
-// per-CTA barrier slot: the batch's partial dU (32 moves), then the pair-energy corrections
-// this CTA computed (at most 32 * 31 / 2 = 496 pairs)
+// exchange buffer of the sweep, per parity: the partial dU of every move of a batch from every
+// CTA ([kMcBatchMax][grid]), then kMcSlotStride - kMcBatchMax = kMcCorrPerCta floats per CTA of
+// which a box group uses its first CTA's share onwards for the batch-pair corrections
 constexpr int kMcBatchMax = 64;           // moves per batch of the sweep, at most
 constexpr int kMcCorrPerCta = kMcBatchMax * (kMcBatchMax - 1) / 2;   // batch-pair corrections
 constexpr int kMcSlotStride = kMcBatchMax + kMcCorrPerCta;
-// correction items of one batch in shared memory (>= 496 pairs x 8 atoms)
+// correction items of one batch in shared memory (>= 496 pairs x 8 atoms: batches above 32 moves
+// need 8 or more CTAs per box)
 constexpr int kMcCorrItems = 4096;
 // partners staged per chunk in shared memory when the slices live in global memory
 constexpr int kMcStageChunk = 2048;

@@ -14,8 +14,8 @@
 //
 // Batching without changing the chain: moves are taken in batches of up to K
 // consecutive moves with distinct molecules (a batch ends before the first molecule that
-// repeats; K <= 32). Warp w computes the partial dU of moves w and w + 16 against the
-// slice as it stood at the start of the batch. One grid barrier per batch gathers the per-CTA partials; every
+// repeats; K <= 64). Warp w computes the partial dU of moves w, w + 16, w + 32 and w + 48
+// against the slice as it stood at the start of the batch. One grid barrier per batch gathers the per-CTA partials; every
 // CTA sums them in the same fixed order and resolves the batch in order: move k's dU is
 // its batch-start value plus, for every earlier accepted move k' of the batch, the exact
 // change of the pair energies between the two moved molecules,
