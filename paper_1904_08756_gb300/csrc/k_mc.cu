@@ -883,7 +883,9 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         // Slot buffer, per parity: partials [kBatchMax][grid] (one move's partials of the group
         // are contiguous), then corrections, the box's pair pq at cta0 * kMcCorrPerCta + pq.
         // Arrival: warp 0 writes the CTA's partials and corrections in parallel, then lane 0
-        // makes a release add on the group's counter and polls it with acquire loads.
+        // makes a release add on the group's counter and polls it with acquire loads (the warp
+        // barrier orders the other lanes' writes before the release, which is cumulative; the
+        // CTA barrier after the poll orders every thread's reads after the acquire).
         ++seq;
         if (G > 1) {
             float *ps = A.slots + (size_t)(seq & 1u) * A.grid * kMcSlotStride;
