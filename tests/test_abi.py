@@ -80,3 +80,19 @@ def test_null_handles_are_rejected(lib):
     assert lib.epsr_launch_count(None) == epsr.EPSR_EINVAL
     n0 = C.c_uint64()
     assert lib.epsr_launch_count(C.byref(n0)) == epsr.EPSR_OK
+
+
+def test_flexible_descriptor_checked_on_host(lib):
+    """Flexible molecules: the spring tables must be symmetric, finite and non-negative."""
+    s = synth.flexible_water_box(10, seed=1, L_A=10.0)
+    xyz = np.ascontiguousarray(s.xyz, np.int32)
+    typ = np.ascontiguousarray(s.type, np.int32)
+    ms = np.ascontiguousarray(s.mol_start, np.int64)
+    M = epsr.MAX_TYPES
+    bad = []
+    d = epsr.box_desc(s); d.bond_k[0 * M + 1] = d.bond_k[1 * M + 0] + 1.0; bad.append(d)     # not symmetric
+    d = epsr.box_desc(s); d.bond_k[0 * M + 1] = d.bond_k[1 * M + 0] = -1.0; bad.append(d)     # negative
+    d = epsr.box_desc(s); d.bond_d[0 * M + 1] = d.bond_d[1 * M + 0] = float("nan"); bad.append(d)
+    for d in bad:
+        st, h = _create(lib, d, xyz, typ, ms)
+        assert st == epsr.EPSR_EINVAL and not h.value
