@@ -398,9 +398,10 @@ def sine_matrix(Q: np.ndarray, n_bins: int, dr: float) -> np.ndarray:
 def chi2_and_grads(box: Box, sigma: float, Q: np.ndarray, target: np.ndarray,
                    C_: np.ndarray, s_basis: float, grad_atoms: np.ndarray | None = None):
     """chi^2(x, C) = sum_Q [S~(Q; x) + sum_p W_p sum_n C_pn F_n(Q) - T(Q)]^2 (reading
-    c15), with S~ the Eq. (1) transform of the smeared g~. Returns chi^2, dchi2/dC
-    [P][n_basis], dchi2/dx [n_atoms or len(grad_atoms)][3] (per Angstrom), S~ and
-    lambda = dchi2/dHt."""
+    c15), with S~ the Eq. (1) transform of the smeared g~ (orc_sq, the routine that gives
+    S(Q) of an exact histogram; sine_matrix is the K of that sum, used by the adjoint).
+    Returns chi^2, dchi2/dC [P][n_basis], dchi2/dx [n_atoms or len(grad_atoms)][3] (per
+    Angstrom), S~ and lambda = dchi2/dHt."""
     s = box.sys
     W, flat = eq1_weights(s)
     rho = number_density(s)
@@ -408,8 +409,8 @@ def chi2_and_grads(box: Box, sigma: float, Q: np.ndarray, target: np.ndarray,
     g, fac = smeared_g(box, Ht)
     K = sine_matrix(Q, s.n_bins, s.dr)
     wcol = 4.0 * math.pi * rho * W
-    Sp = (wcol[:, None] * ((g - 1.0) @ K.T))              # [P][nQ]
-    S_t = flat + Sp.sum(axis=0)
+    _, St = sq(g, s.dr, Q, wcol, len(W), np.array([flat]))   # Eq. (1) through orc_sq
+    S_t = St[0]
     F = ep_basis_matrix(C_.shape[1], s_basis, Q, rho)     # [nQ][n_basis]
     ep_img = (W[:, None] * (C_ @ F.T)).sum(axis=0)
     res = S_t + ep_img - target

@@ -616,3 +616,74 @@ def test_spring_boltzmann_distribution():
     expect *= counts.sum() / expect.sum()
     chi2 = float(((counts - expect) ** 2 / np.maximum(expect, 1)).sum())
     assert chi2 < 50.0, (chi2, counts, expect)
+
+
+# --------------------------------------------------------------------------------------
+# Pair resolution with gamma > 0 (reading c16), the smeared g~ normalisation and the
+# chi^2 value of the differentiable form (reading c15)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_data,P", [(1, 3), (2, 3), (3, 6), (5, 3)])
+def test_pair_resolve_with_gamma_solves_the_regularised_normal_equations(n_data, P):
+    """The pseudo-inverse of [w; gamma I] applied to [dS; 0] minimises
+    ||w x - dS||^2 + gamma^2 ||x||^2, so x solves (w^T w + gamma^2 I) x = w^T dS. A wrong
+    right-hand side of the stacked rows or gamma in place of gamma^2 fails this."""
+    rng = np.random.default_rng(10 * n_data + P)
+    w = rng.uniform(0.05, 1.0, (n_data, P))
+    dS = rng.normal(size=(n_data, 40))
+    for gamma in (0.3, 1.0, 2.5):
+        x = oracle.pair_resolve(dS, w, gamma)
+        assert x.shape == (P, 40)
+        lhs = (w.T @ w + gamma * gamma * np.eye(P)) @ x
+        assert np.allclose(lhs, w.T @ dS, rtol=0, atol=1e-12 * np.abs(w.T @ dS).max())
+
+
+def test_pair_resolve_with_gamma_scalar_closed_form_and_small_gamma_limit():
+    # one dataset, one pair: x = w dS / (w^2 + gamma^2)
+    dS = np.array([[0.7, -1.3, 2.0]])
+    for wv, gamma in ((0.4, 1.0), (2.0, 0.5)):
+        x = oracle.pair_resolve(dS, np.array([[wv]]), gamma)
+        assert np.allclose(x, wv * dS / (wv * wv + gamma * gamma), rtol=1e-14, atol=0)
+    # square, well-conditioned w: gamma -> 0 approaches the exact inverse
+    rng = np.random.default_rng(3)
+    w = np.eye(3) + rng.uniform(-0.2, 0.2, (3, 3))
+    dSp = rng.normal(size=(3, 20))
+    for gamma, tol in ((1e-2, 1e-3), (1e-4, 1e-7)):
+        x = oracle.pair_resolve(w @ dSp, w, gamma)
+        assert np.abs(x - dSp).max() < tol * np.abs(dSp).max()
+
+
+def test_smeared_g_of_integer_counts_equals_normalize_g(small_water):
+    """g~ applies the normalisation of g (reading c7) to real-valued counts: on an integer
+    histogram it equals the C oracle's g (P_aa = N_a (N_a - 1) / 2 there), and the factor it
+    returns is the one that multiplies the counts."""
+    ob = oracle.Box(small_water)
+    H = ob.histogram()
+    g_ref = ob.normalize_g(H)
+    g, fac = oracle.smeared_g(ob, H.astype(np.float64))
+    assert np.allclose(g, g_ref, rtol=1e-12, atol=0)   # rounding order of the shell volume
+    assert np.allclose(g, H * fac, rtol=1e-15, atol=0)
+
+
+def test_chi2_value_against_eq1_and_the_ep_image():
+    """The chi^2 value: with C = 0 and the target equal to the Eq. (1) S~ of g~ (orc_sq on
+    the smeared g~), chi^2 = 0; one planted coefficient C_pn adds the image W_p C_pn F_n(Q),
+    so chi^2 = (W_p C_pn)^2 sum_Q F_n(Q)^2 (F_n the closed-form Poisson transform)."""
+    s = synth.water_box(30, seed=33, L_A=9.0, n_bins=100, bin_p=5, bin_q=100)
+    Q = 0.5 + np.arange(60) * 0.25
+    box = oracle.Box(s)
+    sigma = 0.05
+    W, flat = oracle.eq1_weights(s)
+    rho = oracle.number_density(s)
+    g, _ = oracle.smeared_g(box, box.smeared_hist(sigma))
+    _, St = oracle.sq(g, s.dr, Q, 4.0 * math.pi * rho * W, 3, np.array([flat]))
+    C0 = np.zeros((3, 4))
+    chi2, dC, _, S_t, _ = oracle.chi2_and_grads(box, sigma, Q, St[0], C0, 0.5)
+    assert np.array_equal(S_t, St[0])
+    assert chi2 < 1e-24 and np.abs(dC).max() < 1e-12
+    for p, n, c in ((0, 1, 0.3), (2, 3, -0.05), (1, 4, 1.2)):
+        Cp = C0.copy()
+        Cp[p, n - 1] = c
+        chi2p = oracle.chi2_and_grads(box, sigma, Q, St[0], Cp, 0.5)[0]
+        Fn = oracle.poisson_F(n, 0.5, Q, rho)
+        assert abs(chi2p - (W[p] * c) ** 2 * (Fn * Fn).sum()) <= 1e-12 * chi2p
