@@ -268,7 +268,9 @@ int epsr_checkpoint_load(epsr_box *box, const void *buf, size_t len, epsr_stream
  *   g     device float [hist_len] or NULL: g_ab(k) = hist V / (n_configs P_ab shell_k),
  *         P_ab = N_a N_b (a != b) or N_a (N_a - 1)/2, shell_k = 4 pi/3 (r_{k+1}^3 - r_k^3).
  *   n_configs  number of configurations accumulated in hist (>= 1) for g.
- * Asynchronous. Errors: EINVAL, ECUDA.                                                 */
+ * Bins beyond half the box side are only partly sampled (minimum-image distances cover a
+ * shell of radius r > L/2 only in part), so g falls below 1 there; the counts are still
+ * the exact minimum-image counts. Asynchronous. Errors: EINVAL, ECUDA.                   */
 int epsr_partial_gr(epsr_box *box, uint64_t *hist, float *g, int64_t n_configs,
                     epsr_stream_t stream);
 /* The same histogram counted over cell lists: cells at least the histogram range wide
@@ -338,23 +340,26 @@ int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t n_data, co
 
 /* ---- pair histogram without device allocation -----------------------------------------
  * The paper has no counterpart: this entry point exists for callers that must not
- * allocate device memory when they need the counts -- code running while a CUDA graph
- * is being captured, plug-ins whose host framework's caching allocator owns the device
- * memory, or real-time loops that may not call cudaMalloc/cudaFree after start-up.
+ * allocate device memory when they need the counts -- plug-ins whose host framework's
+ * caching allocator owns the device memory and hands them none, or real-time loops that
+ * may not call cudaMalloc/cudaFree (which can synchronise the device) after start-up.
  *
  * epsr_partial_gr_noalloc adds to hist the same counts epsr_partial_gr adds for a
  * one-box handle with the same coordinates, types and bins, and allocates nothing: all
  * working memory is one fixed __device__ array of epsr_noalloc_scratch_bytes() bytes
  * (about 12.6 MB) that every GPU loading the library holds until the process exits.
  *   xyz, type   HOST int32 [n_atoms][3] in [0, L_fx) and [n_atoms] in [0, n_types)
- *               (validated; copied into the array, so they may be reused on return)
+ *               (validated; staged by the copy calls before they return, so they may be
+ *               reused on return)
  *   n_atoms     1 .. EPSR_NOALLOC_MAX_ATOMS; larger boxes are rejected with EPSR_EINVAL
  *   hist        device uint64 [n_types (n_types + 1) / 2][n_bins], accumulated
  * The first call on a device, made while that device is current, looks the array's
- * address up (cudaGetSymbolAddress); make that first call before any stream capture.
+ * address up (cudaGetSymbolAddress) and caches it for the life of that device's primary
+ * context: after cudaDeviceReset the cached address is stale, so do not call this entry
+ * point after a reset. Make the first call on a device before any stream capture.
  * Every call shares the array, so calls whose GPU work overlaps (other streams, other
  * host threads on the same device) race and corrupt each other's counts: serialise them.
- * Work is enqueued on `stream`; the host arrays are consumed before the call returns. */
+ * Work is enqueued on `stream`. */
 #define EPSR_NOALLOC_MAX_ATOMS 131072
 size_t epsr_noalloc_scratch_bytes(void);
 int epsr_partial_gr_noalloc(const int32_t *xyz, const int32_t *type, int64_t n_atoms,

@@ -1,17 +1,16 @@
 // epsr_noalloc.cu -- the pair histogram of one box without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a histogram:
-// code running while a CUDA graph is being captured, plug-ins that are handed a fixed
-// memory budget by a host framework whose caching allocator owns the device, or
-// real-time loops that must not call cudaMalloc/cudaFree after start-up. For them,
-// epsr_partial_gr_noalloc computes the same counts as epsr_partial_gr on a one-box
-// handle, with every piece of working memory carved from one file-scope __device__ array
-// of fixed size. The array exists on every GPU that loads the library until the process
-// exits.
+// plug-ins that are handed no device memory by a host framework whose caching allocator
+// owns the device, or real-time loops that must not call cudaMalloc/cudaFree (which can
+// synchronise the whole device) after start-up. For them, epsr_partial_gr_noalloc computes
+// the same counts as epsr_partial_gr on a one-box handle, with every piece of working
+// memory carved from one file-scope __device__ array of fixed size. The array exists on
+// every GPU that loads the library until the process exits.
 //
 // Host code cannot use the array's name as a device address; its address is obtained
 // per device with cudaGetSymbolAddress on the first call made while that device is
-// current, and cached.
+// current, and cached for the life of the device's primary context.
 #include <cuda_runtime.h>
 
 #include <algorithm>

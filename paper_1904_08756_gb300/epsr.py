@@ -159,6 +159,33 @@ def _dev_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _buf(t, dtypes, min_numel: int, name: str):
+    """Device pointer of a caller buffer that a kernel writes: checks its element type, its
+    length and that it lives on the current device, so that a short or misplaced buffer is a
+    ValueError here instead of an out-of-bounds write on the GPU."""
+    if t is None:
+        return None
+    import torch
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: expected dtype {' or '.join(str(d) for d in dtypes)}, got {t.dtype}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {min_numel} needed")
+    if t.is_cuda and t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    return _dev_ptr(t)
+
+
+def _hist_ptr(t, n: int, name: str = "hist"):
+    import torch
+    return _buf(t, (torch.int64, torch.uint64), n, name)
+
+
+def _g_ptr(t, n: int, name: str = "g"):
+    import torch
+    return _buf(t, (torch.float32,), n, name)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -331,12 +358,14 @@ class Box:
 
     # -- histograms -------------------------------------------------------------------------------
     def epsr_partial_gr(self, hist, g=None, n_configs: int = 1, stream=None):
-        _check(lib().epsr_partial_gr(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
-                                     _stream(stream)), "epsr_partial_gr")
+        _check(lib().epsr_partial_gr(self.h, _hist_ptr(hist, self.hist_len),
+                                     _g_ptr(g, self.hist_len), n_configs, _stream(stream)),
+               "epsr_partial_gr")
 
     def epsr_partial_gr_cells(self, hist, g=None, n_configs: int = 1, stream=None):
-        _check(lib().epsr_partial_gr_cells(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
-                                           _stream(stream)), "epsr_partial_gr_cells")
+        _check(lib().epsr_partial_gr_cells(self.h, _hist_ptr(hist, self.hist_len),
+                                           _g_ptr(g, self.hist_len), n_configs, _stream(stream)),
+               "epsr_partial_gr_cells")
 
     def epsr_partial_gr_tiles(self) -> int:
         n = C.c_int64()
@@ -344,12 +373,13 @@ class Box:
         return n.value
 
     def epsr_partial_gr_range(self, t0: int, t1: int, hist, stream=None):
-        _check(lib().epsr_partial_gr_range(self.h, t0, t1, _dev_ptr(hist), _stream(stream)),
-               "epsr_partial_gr_range")
+        _check(lib().epsr_partial_gr_range(self.h, t0, t1, _hist_ptr(hist, self.hist_len),
+                                           _stream(stream)), "epsr_partial_gr_range")
 
     def epsr_normalize_g(self, hist, g, n_configs: int = 1, stream=None):
-        _check(lib().epsr_normalize_g(self.h, _dev_ptr(hist), _dev_ptr(g), n_configs,
-                                      _stream(stream)), "epsr_normalize_g")
+        _check(lib().epsr_normalize_g(self.h, _hist_ptr(hist, self.hist_len),
+                                      _g_ptr(g, self.hist_len), n_configs, _stream(stream)),
+               "epsr_normalize_g")
 
     def epsr_ep_update(self, b: int, dS, w: np.ndarray, Q: np.ndarray, n_basis: int = 20,
                        s_basis: float = 0.5, gamma: float = 0.0, alpha: float = 1.0, stream=None):
@@ -511,6 +541,8 @@ def epsr_partial_gr_noalloc(system, hist, stream=None):
     coordinates and types are taken from host arrays of a synth.System-like object."""
     xyz = np.ascontiguousarray(system.xyz, np.int32)
     typ = np.ascontiguousarray(system.type, np.int32)
+    n_pairs = system.n_types * (system.n_types + 1) // 2
+    hp = _hist_ptr(hist, n_pairs * system.n_bins)
     _check(lib().epsr_partial_gr_noalloc(_np_ptr(xyz), _np_ptr(typ), xyz.shape[0], system.L_fx, 20,
                                          system.n_types, system.bin_p, system.bin_q, system.n_bins,
-                                         _dev_ptr(hist), _stream(stream)), "epsr_partial_gr_noalloc")
+                                         hp, _stream(stream)), "epsr_partial_gr_noalloc")

@@ -96,3 +96,18 @@ def test_flexible_descriptor_checked_on_host(lib):
     for d in bad:
         st, h = _create(lib, d, xyz, typ, ms)
         assert st == epsr.EPSR_EINVAL and not h.value
+
+
+def test_histogram_buffers_checked_before_any_launch():
+    """A histogram or g buffer that is too short, of the wrong type or on another device is
+    refused by the binding before the library sees it (the kernels would write past it)."""
+    torch = pytest.importorskip("torch")
+    from paper_1904_08756_gb300 import epsr
+    with pytest.raises(ValueError):
+        epsr._hist_ptr(torch.zeros(5, dtype=torch.int64), 6)
+    with pytest.raises(ValueError):
+        epsr._hist_ptr(torch.zeros(10, dtype=torch.float32), 6)
+    with pytest.raises(ValueError):
+        epsr._g_ptr(torch.zeros(10, dtype=torch.float64), 6)
+    with pytest.raises(ValueError):          # right length and type, but host memory
+        epsr._hist_ptr(torch.zeros(10, dtype=torch.int64), 6)

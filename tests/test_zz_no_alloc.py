@@ -1,5 +1,5 @@
 """The allocation-free histogram entry point (for callers that may not allocate device
-memory, e.g. inside graph capture or under a framework-owned allocator) against the
+memory, e.g. plug-ins under a framework-owned allocator or real-time loops) against the
 regular entry point, through the C ABI on the GPU. Collected last on purpose: it must
 pass both alone in a fresh process (the first call sets the scratch address up) and
 after every other test."""
