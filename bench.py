@@ -111,76 +111,91 @@ def workload_name(system, moves: int) -> str:
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
 
-def oracle_pairs_all_cores(system, n_rows_sample: int):
-    """Pair distances/s of the oracle's histogram on every host core: the first n_rows_sample
-    rows of the pair scan dealt out in interleaved row blocks to one host thread per core (the
-    oracle's C routine releases the interpreter lock). Returns (pairs/s, threads)."""
+def oracle_full_step(system, moves_per_step: int = MOVES_PER_STEP, seed: int = 1):
+    """The FP64 oracle on one whole step of the workload, measured, not extrapolated: the
+    Monte Carlo chain of `moves_per_step` moves on one host core (a Markov chain is
+    sequential), then one full all-pair histogram on every host core (the oracle's OpenMP
+    pair scan), then S(Q). Returns a dict of the measured times and rates."""
     import oracle
-    from concurrent.futures import ThreadPoolExecutor
+    ob = oracle.Box(system)
     threads = os.cpu_count() or 1
-    ob = oracle.Box(system)
-    N = system.n_atoms
-    pairs = sum(N - 1 - i for i in range(n_rows_sample))
-    blk = 64
-    blocks = [(i, min(i + blk, n_rows_sample)) for i in range(0, n_rows_sample, blk)]
-
-    def work(t):
-        for i0, i1 in blocks[t::threads]:
-            ob.histogram(i0, i1)
-
     t0 = time.perf_counter()
-    with ThreadPoolExecutor(threads) as ex:
-        list(ex.map(work, range(threads)))
-    return pairs / (time.perf_counter() - t0), threads
-
-
-def oracle_step_estimate(system, n_moves_sample: int, n_rows_sample: int, seed: int = 1,
-                         moves_per_step: int = MOVES_PER_STEP):
-    """Time the FP64 oracle on a bounded sample of one step and scale to the full step.
-    Returns (seconds per full step, description, threads used)."""
-    import oracle
-    ob = oracle.Box(system)
+    ob.mc_sweep(moves_per_step, seed=seed, move0=0)
+    t_mc = time.perf_counter() - t0
     t0 = time.perf_counter()
-    ob.mc_sweep(n_moves_sample, seed=seed, move0=0)
-    t_move = (time.perf_counter() - t0) / n_moves_sample
-    N = system.n_atoms
-    t0 = time.perf_counter()
-    ob.histogram(0, n_rows_sample)
-    t_hist = time.perf_counter() - t0
-    pairs_sample = sum(N - 1 - i for i in range(n_rows_sample))
-    t_pair = t_hist / pairs_sample
-    pairs = N * (N - 1) // 2
-    g = ob.normalize_g(np.zeros((3, system.n_bins), np.uint64) + 1)
+    H = ob.histogram(threads=threads)
+    t_gr = time.perf_counter() - t0
+    g = ob.normalize_g(H)
     t0 = time.perf_counter()
     oracle.sq_of_box(ob, g)
     t_sq = time.perf_counter() - t0
-    t_step = moves_per_step * t_move + pairs * t_pair + t_sq
-    desc = (f"{n_moves_sample} moves + {pairs_sample:.3g} of {pairs:.3g} pair distances + 1 S(Q) "
-            f"timed, scaled to {moves_per_step} moves + all pairs; 1 thread")
-    return t_step, desc, 1, t_move, t_pair
+    N = system.n_atoms
+    pairs = N * (N - 1) // 2
+    # beside it: the pair scan on one core, over the first rows (about 10 s of work)
+    rows = max(1, min(N - 1, int(3.0e8 / N)))
+    t0 = time.perf_counter()
+    ob.histogram(0, rows)
+    t_rows = time.perf_counter() - t0
+    pairs_rows = rows * (N - 1) - rows * (rows - 1) // 2
+    return {"t_mc": t_mc, "t_gr": t_gr, "t_sq": t_sq, "threads": threads, "pairs": pairs,
+            "pairs_1core_per_s": pairs_rows / t_rows, "rows_1core": rows,
+            "pairs_1core_sample": pairs_rows}
+
+
+def oracle_sample_step(ob, system, frac: float, move0: int, seed: int = 1):
+    """One step of the reference arm: the fraction `frac` of the step's work done by the
+    oracle on one host core -- frac x 10,000 moves of the chain, the first rows of the pair
+    scan holding frac x N(N-1)/2 pair distances, and one S(Q). Returns (seconds, moves, pairs)."""
+    import oracle
+    N = system.n_atoms
+    moves = max(1, int(round(frac * MOVES_PER_STEP)))
+    target = frac * (N * (N - 1) // 2)
+    rows, pairs = 0, 0
+    while rows < N - 1 and pairs < target:
+        pairs += N - 1 - rows
+        rows += 1
+    t0 = time.perf_counter()
+    ob.mc_sweep(moves, seed=seed, move0=move0)
+    H = ob.histogram(0, rows)
+    oracle.sq_of_box(ob, ob.normalize_g(H))
+    return time.perf_counter() - t0, moves, pairs
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on one host core. Each step is the
+    fraction 1/100 of the benchmarked step (100 moves, 5.0e7 of the 5.0e9 pair distances, one
+    S(Q)), timed as it runs; the rate of that sample is the line's value and its measured
+    time the line's ms_per_step, so the steps printed are the steps that ran."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle
     from paper_1904_08756_gb300 import synth
     system = synth.paper_water()
-    times = []
+    ob = oracle.Box(system)
+    frac = 0.01
+    times, moves_done, pairs_done = [], 0, 0
     for i in range(args.warmup + args.steps):
-        t_step, desc, cores, _, _ = oracle_step_estimate(system, 20, 200, seed=1 + i)
+        t, m, p = oracle_sample_step(ob, system, frac, move0=i * 1000)
         if i >= args.warmup:
-            times.append(t_step)
-    t = sum(times) / len(times)
-    v = MOVES_PER_STEP / t
+            times.append(t)
+            moves_done += m
+            pairs_done += p
+    t = sum(times)
+    v = moves_done / t
+    N = system.n_atoms
+    desc = (f"each step 1/100 of the benchmarked step, measured: {moves_done // args.steps} moves of "
+            f"the chain + the first rows of the pair scan ({pairs_done / args.steps:.3g} of "
+            f"{N * (N - 1) // 2:.3g} pair distances) + one S(Q); value = moves done / time taken")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(system, MOVES_PER_STEP),
                        "n_atoms": system.n_atoms, "moves_per_step": MOVES_PER_STEP},
-            "cpu_baseline": {"value": v, "unit": "moves/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "moves/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
+            "sample_fraction_of_step": frac,
             "e2e": {"value": v, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -658,14 +673,19 @@ def main():
             "gpu_launches": launches,
         }
         if not args.no_cpu_baseline and ws == 1:
-            t_cpu, desc, cores, t_move, t_pair = oracle_step_estimate(system, 300, 3000, moves_per_step=moves)
-            pps_all, threads = oracle_pairs_all_cores(system, 10000)
-            line["cpu_baseline"] = {"value": moves / t_cpu, "unit": "moves/s",
-                                    "cores": cores, "kind": "oracle", "sample": desc,
-                                    "moves_per_s": 1.0 / t_move, "pair_distances_per_s": 1.0 / t_pair,
-                                    "pair_distances_per_s_all_cores": pps_all, "all_cores_threads": threads,
-                                    "all_cores_sample": "the first 10,000 rows of the pair scan (0.95e9 pair distances), "
-                                                        "one host thread per core"}
+            o = oracle_full_step(system, moves_per_step=moves)
+            t_cpu = o["t_mc"] + o["t_gr"] + o["t_sq"]
+            line["cpu_baseline"] = {
+                "value": moves / t_cpu, "unit": "moves/s", "cores": o["threads"], "kind": "oracle",
+                "sample": (f"full step, measured: {moves} moves of the chain on 1 core "
+                           f"({o['t_mc']:.1f} s) + the full pair scan ({o['pairs']:.4g} pair "
+                           f"distances) on {o['threads']} cores ({o['t_gr']:.1f} s) + S(Q) "
+                           f"({o['t_sq']:.2f} s)"),
+                "moves_per_s_1core": moves / o["t_mc"],
+                "pair_distances_per_s_all_cores": o["pairs"] / o["t_gr"],
+                "pair_distances_per_s_1core": o["pairs_1core_per_s"],
+                "pair_distances_1core_sample": (f"the first {o['rows_1core']} rows of the pair scan "
+                                                f"({o['pairs_1core_sample']:.3g} pair distances)")}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

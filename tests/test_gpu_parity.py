@@ -261,21 +261,43 @@ def test_mc_replay_silica_atom_moves_with_ep():
     assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
 
 
-@pytest.mark.parametrize("cells", [None, (0, 256), (0, 4), (0, 0)],
-                         ids=["default", "margin0", "escapee-overflow", "no-cells"])
-def test_mc_replay_paper_water_sampled(cells):
+@pytest.mark.parametrize("cells,check_every", [(None, 1), ((0, 256), 40), ((0, 4), 40), ((0, 0), 40)],
+                         ids=["default-every-move", "margin0", "escapee-overflow", "no-cells"])
+def test_mc_replay_paper_water_sampled(cells, check_every):
     """99,999-atom water on the full grid of CTAs: trial coordinates of every move
-    bit-exact, dU checked on a sample of moves, final coordinates bit-exact. With a zero
-    cell margin every partner that leaves its cell becomes an escapee; a list of 4 overflows
-    and the CTAs fall back to full scans; capacity 0 turns cell queries off."""
+    bit-exact, dU (and the decision) checked against the oracle on every move for the
+    default configuration and on every 40th for the cell-query variants, final coordinates
+    bit-exact. With a zero cell margin every partner that leaves its cell becomes an escapee;
+    a list of 4 overflows and the CTAs fall back to full scans; capacity 0 turns cell queries
+    off."""
     s = synth.paper_water()
     box = epsr.Box(s)
     if cells is not None:
         box.epsr_mc_set_cells(*cells)
     n = 4000
     stats, log = run_logged(box, n, seed=2024)
-    ob, checked, worst, flips = replay(s, s.xyz, log[0], 2024, check_every=40)
-    assert checked == n // 40
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 2024, check_every=check_every)
+    assert checked == n // check_every
+    assert flips <= 2
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
+def test_mc_replay_paper_silica_every_move():
+    """The 99,000-atom silica box as benchmarked (default CTAs, 64 moves per barrier,
+    single-atom moves, Lennard-Jones on every type pair) with a random empirical potential on
+    its 600 bins: dU and the decision of every one of 3,000 moves against the FP64 oracle,
+    final coordinates bit-exact."""
+    s = synth.paper_silica()
+    rng = np.random.default_rng(21)
+    ep = (rng.normal(size=(3, s.n_bins)) * 0.3).astype(np.float32)
+    box = epsr.Box(s)
+    box.epsr_box_set_ep(0, ep)
+    n = 3000
+    stats, log = run_logged(box, n, seed=606)
+    att, acc, nonfin, sdu = stats[0]
+    assert att == n and nonfin == 0 and 0 < acc < n
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 606, ep=ep.astype(np.float64))
+    assert checked == n and flips <= 2
     assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
 
 
@@ -310,6 +332,60 @@ def test_mc_batched_replicas_replay():
         _, a0 = box.epsr_box_offsets(b)
         ob, _, _, _ = replay(s, s.xyz, log[b], 5, box_index=b, check_every=5)
         assert np.array_equal(xyz[a0:a0 + s.n_atoms], ob.xyz)
+
+
+def test_replicas_64_boxes_graph_step_against_oracle():
+    """The 64-box replica handle at its real shape (atom counts log-uniform on 2k-60k from
+    seed 3, half water, half silica, 1.04 M atoms; boxes of 1-3 CTAs, so the small-batch and
+    one-CTA paths run): one step captured as a CUDA graph -- 256 logged moves per box, the
+    pair histograms with g, and S(Q) of all 192 columns in the BF16x3 tensor-core mode.
+    Every box's moves are replayed on the oracle (trial coordinates of every move, dU on
+    every fourth), final coordinates bit-exact; the histograms of eight boxes bit-exact; S(Q)
+    within 1e-4 barn of the oracle's Eq. (1) on the GPU's own g."""
+    systems = synth.replica_batch()
+    nb = len(systems)
+    n_moves, seed = 256, 3
+    box = epsr.Box(systems)
+    ws = np.concatenate([box.epsr_sq_weights(b)[0] for b in range(nb)])
+    flats = np.array([box.epsr_sq_weights(b)[1] for b in range(nb)])
+    Q = systems[0].Q
+    plan = epsr.SqPlan(Q, 600, 0.02, epsr.SQ_BF16X3, max_cols=3 * nb)
+    H = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    g = torch.zeros(box.hist_len, dtype=torch.float32, device=DEV)
+    S = torch.zeros((nb, len(Q)), dtype=torch.float32, device=DEV)
+    log = torch.zeros((nb * n_moves * 128,), dtype=torch.uint8, device=DEV)
+    st = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        cs = torch.cuda.current_stream().cuda_stream
+        box.epsr_mc_sweep_async(n_moves, seed, 0, log=log, stream=cs)
+        H.zero_()
+        box.epsr_partial_gr(H, g, 1, stream=cs)
+        plan.epsr_sq_exec(g.view(-1, 600), ws, 3, flats, None, S, stream=cs)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert box.epsr_mc_status() == epsr.EPSR_OK
+    assert plan.epsr_sq_plan_status() == epsr.EPSR_OK
+    lg = log.cpu().numpy().view(epsr.MOVE_LOG_DTYPE).reshape(nb, n_moves)
+    xyz = box.epsr_box_get_coords()
+    Hn = H.cpu().numpy().astype(np.uint64)
+    finals = []
+    for b, s in enumerate(systems):
+        h0, a0 = box.epsr_box_offsets(b)
+        ob, checked, _, flips = replay(s, s.xyz, lg[b], seed, box_index=b, check_every=4)
+        assert checked == n_moves // 4 and flips <= 2
+        assert np.array_equal(xyz[a0:a0 + s.n_atoms], ob.xyz), b
+        finals.append((ob, h0))
+    order = np.argsort([s.n_atoms for s in systems])
+    for b in list(order[:4]) + list(order[-4:]):
+        ob, h0 = finals[b]
+        ref = ob.histogram(threads=0)
+        assert np.array_equal(Hn[h0:h0 + ref.size].reshape(ref.shape), ref), b
+    gh = g.cpu().numpy().astype(np.float64).reshape(-1, 600)
+    _, St_ref = oracle.sq(gh, 0.02, Q.astype(np.float32).astype(np.float64), ws, 3, flats)
+    err = np.abs(S.cpu().numpy() - St_ref).max()
+    print(f"64 replicas: BF16x3 S(Q) max |dS| {err:.3e} barn")
+    assert err <= 1e-4
 
 
 def test_mc_energy_drift(small_water):
