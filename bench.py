@@ -235,6 +235,8 @@ def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
             flops = 2.0 * n_q * n_bins * n_cols
             rec = {"ms": ms, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
                    "max_abs_diff_vs_fp32": float((S - S_ref).abs().max())}
+            if mode != epsr.SQ_FP32:
+                rec["tiles"] = dict(zip(("cols_per_cta", "k_split"), plan.epsr_sq_plan_get_tiles(n_cols, 3)))
             if mode in products and peaks.get("bf16_tflops"):
                 issued = flops * products[mode] / (ms * 1e-3) / 1e12
                 peak = peaks["bf16_tflops"] * (0.5 if mode == epsr.SQ_TF32X3 else 1.0)

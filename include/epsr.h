@@ -393,6 +393,17 @@ int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, const doubl
 int epsr_sq(const float *g, int32_t n_cols, int32_t n_bins, double dr, const float *Q,
             int32_t nQ, const double *w, int32_t cols_per_set, const double *flat,
             float *S_partial, float *S_total, int32_t mode, epsr_stream_t stream);
+/* Tiling of the tensor-core modes (no counterpart in the paper; a performance setting that
+ * does not change which products are summed, only how the K sum is split): n_chunk columns
+ * of g per CTA (a multiple of 16, at most 256; when it is a multiple of cols_per_set the set
+ * totals are formed in the same launch) and k_split CTAs per output tile along the bins (one
+ * thread-block cluster, at most 8, at most the number of 128-byte K units), whose FP32
+ * partials are added in a fixed order. 0 selects the built-in rule. EPSR_EINVAL for the FP32
+ * mode (unless both are 0) or a tiling whose buffers do not fit in shared memory. Host only.
+ * epsr_sq_plan_get_tiles reports the tiling an epsr_sq_exec of n_cols columns would use. */
+int epsr_sq_plan_set_tiles(epsr_sq_plan *plan, int32_t n_chunk, int32_t k_split);
+int epsr_sq_plan_get_tiles(const epsr_sq_plan *plan, int32_t n_cols, int32_t cols_per_set,
+                           int32_t with_totals, int32_t *n_chunk, int32_t *k_split);
 
 #ifdef __cplusplus
 }

@@ -332,6 +332,56 @@ static void plan_mc_groups(epsr_box *h)
     h->cta_box_len = c0;
 }
 
+// Shared-memory layout of the sweep for the current CTA split: thresholds, EP table, cell
+// index [types][513] (uint32), correction items, and, when they fit, the partner slice (int4 per
+// slot) and the home cell of every slot (uint16); otherwise the slices and home cells live in
+// global memory and a chunk of partners is staged.
+struct McLayout {
+    int slice_cap = 0, types_cap = 1;
+    size_t smem = 0;
+    bool gslice = false;
+};
+
+static int mc_layout(const epsr_box *h, McLayout *L)
+{
+    for (auto &b : h->hb) L->slice_cap = std::max(L->slice_cap, b.chunk);
+    for (auto &b : h->hb) L->types_cap = std::max(L->types_cap, b.n_types);
+    const size_t tables = (size_t)h->tbl_cap * sizeof(long long) + (size_t)h->ep_cap * sizeof(float) +
+                          (size_t)L->types_cap * (kMcCells + 1) * sizeof(unsigned) +
+                          (size_t)kMcBatchMax * kMcBatchMax * sizeof(float) + (size_t)kMcCorrItems * sizeof(float);
+    const size_t per_slot = sizeof(int4) + sizeof(unsigned short);
+    L->smem = (((size_t)L->slice_cap * per_slot + tables) + 15) & ~(size_t)15;
+    L->gslice = L->smem > kMcMaxDynSmem;
+    if (L->gslice) {
+        L->smem = ((tables + 15) & ~(size_t)15) + (size_t)kMcStageChunk * sizeof(int4);
+        if (L->smem > kMcMaxDynSmem)
+            return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of tables per CTA (limit %zu)", L->smem, kMcMaxDynSmem);
+    }
+    return EPSR_OK;
+}
+
+// Global-memory slices of the partners when the layout needs them (allocated here, outside
+// any sweep, so that a sweep can be captured in a CUDA graph).
+static int alloc_mc_slices(epsr_box *h)
+{
+    McLayout L;
+    int rc = mc_layout(h, &L);
+    if (rc) return rc;
+    if (!L.gslice) return EPSR_OK;
+    const size_t slots = (size_t)h->cta_box_len * L.slice_cap;
+    if (h->slice_g_cap >= slots) return EPSR_OK;
+    if (h->slice_g) cudaFree(h->slice_g);
+    if (h->home_g) cudaFree(h->home_g);
+    h->slice_g = nullptr;
+    h->home_g = nullptr;
+    h->slice_g_cap = 0;
+    rc = dalloc(&h->slice_g, slots);
+    if (!rc) rc = dalloc(&h->home_g, slots);
+    if (rc) return rc;
+    h->slice_g_cap = slots;
+    return EPSR_OK;
+}
+
 static int upload_mc_groups(epsr_box *h)
 {
     std::vector<int> cb;
@@ -355,7 +405,7 @@ static int upload_mc_groups(epsr_box *h)
         return rc;
     CK(cudaMemcpy(h->cta_box, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->boxes, h->hb.data(), h->hb.size() * sizeof(BoxDev), cudaMemcpyHostToDevice));
-    return EPSR_OK;
+    return alloc_mc_slices(h);
 }
 
 static int create_impl(const epsr_box_desc *descs, int n_boxes, const int32_t *xyz,
@@ -736,44 +786,22 @@ extern "C" int epsr_mc_stats_get(epsr_box *box, epsr_mc_stats *stats, epsr_strea
     return EPSR_OK;
 }
 
-// Enqueues a sweep without synchronising (graph-capturable once the move table exists).
+// Enqueues a sweep without synchronising (graph-capturable: it allocates nothing; the global
+// slices a layout needs are allocated with the layout, at creation or by epsr_mc_set_ctas).
 static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint64_t move0,
                             epsr_move_log *log, cudaStream_t s)
 {
     if (!box || n_moves < 0) return set_error(EPSR_EINVAL, "bad argument");
     CK(cudaMemsetAsync(box->status, 0, sizeof(int), s));
     if (n_moves == 0) return EPSR_OK;
-    int slice_cap = 0;
-    for (auto &b : box->hb) slice_cap = std::max(slice_cap, b.chunk);
-    int types_cap = 1;
-    for (auto &b : box->hb) types_cap = std::max(types_cap, b.n_types);
-    // shared memory: thresholds, EP table, cell index [types][513] (uint32), correction items, and, when they
-    // fit, the partner slice (int4 per slot) and the home cell of every slot (uint16);
-    // otherwise the slices and home cells live in global memory
-    const size_t tables = (size_t)box->tbl_cap * sizeof(long long) + (size_t)box->ep_cap * sizeof(float) +
-                          (size_t)types_cap * (kMcCells + 1) * sizeof(unsigned) +
-                          (size_t)kMcBatchMax * kMcBatchMax * sizeof(float) + (size_t)kMcCorrItems * sizeof(float);
-    const size_t per_slot = sizeof(int4) + sizeof(unsigned short);
-    size_t smem = (((size_t)slice_cap * per_slot + tables) + 15) & ~(size_t)15;
-    const bool gslice = smem > kMcMaxDynSmem;
-    if (gslice) {
-        smem = (tables + 15) & ~(size_t)15;
-        smem += (size_t)kMcStageChunk * sizeof(int4);            // staged chunk of partners
-        if (smem > kMcMaxDynSmem)
-            return set_error(EPSR_EINVAL, "mc sweep: %zu bytes of tables per CTA (limit %zu)", smem, kMcMaxDynSmem);
-        const size_t slots = (size_t)box->cta_box_len * slice_cap;
-        if (box->slice_g_cap < slots) {
-            if (box->slice_g) cudaFree(box->slice_g);
-            if (box->home_g) cudaFree(box->home_g);
-            box->slice_g = nullptr;
-            box->home_g = nullptr;
-            box->slice_g_cap = 0;
-            int rc = dalloc(&box->slice_g, slots);
-            if (!rc) rc = dalloc(&box->home_g, slots);
-            if (rc) return rc;
-            box->slice_g_cap = slots;
-        }
-    }
+    McLayout lay;
+    int rcl = mc_layout(box, &lay);
+    if (rcl) return rcl;
+    const int slice_cap = lay.slice_cap, types_cap = lay.types_cap;
+    const size_t smem = lay.smem;
+    const bool gslice = lay.gslice;
+    if (gslice && box->slice_g_cap < (size_t)box->cta_box_len * slice_cap)
+        return set_error(EPSR_EINVAL, "mc sweep: global slices not allocated for this layout");
     // moves per launch: the table (allocated at creation) holds at most 2^22 moves over all boxes
     const long long chunk = std::min<long long>(n_moves, box->moves_cap / box->n_boxes);
     // type-major spatial partition of the partners for this sweep
@@ -992,17 +1020,85 @@ struct epsr_sq_plan {
     double *res = nullptr;      // chi^2 residuals [nQ]
     double *chiF = nullptr;     // chi^2 basis values [max basis][nQ] (allocated on first use)
     // tensor-core modes
-    unsigned char *a_packed = nullptr, *b_packed = nullptr;
+    unsigned char *a_packed = nullptr;
     int *tc_status = nullptr;
     int fmt_bf16 = 1, np = 2, kt = 64, stages = 0, m_tiles = 0, n_products = 0;
     int prod_a[8] = {0}, prod_b[8] = {0};
+    int tc_n_chunk = 0, tc_k_split = 0;   // tensor-core tiling set by epsr_sq_plan_set_tiles (0 = rule)
+    int sms = 0;
     ~epsr_sq_plan()
     {
-        void *ptrs[] = {Q, Kt, Sp_scratch, res, chiF, a_packed, b_packed, tc_status};
+        void *ptrs[] = {Q, Kt, Sp_scratch, res, chiF, a_packed, tc_status};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
 };
+
+static int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
+
+// Tiling of the tensor-core contraction: columns per CTA (a multiple of 16, and of the set size
+// when the set totals are fused into the epilogue) and the number of CTAs sharing one output
+// tile along K (one cluster). The rule aims at two CTAs per SM; a tiling set on the plan
+// (epsr_sq_plan_set_tiles, e.g. by the autotuner) takes precedence.
+static int tc_choose_tiles(const epsr_sq_plan *p, int n_cols, int cps, bool want_sets, int *n_chunk,
+                           int *k_split, bool *fused)
+{
+    const int L = 16 / gcd_i(16, cps) * cps;          // lcm(16, cols_per_set)
+    const int n_pad = (n_cols + 15) / 16 * 16;
+    if (p->tc_n_chunk > 0) {
+        *n_chunk = std::min(p->tc_n_chunk, std::max(16, n_pad));
+        *fused = want_sets && *n_chunk % cps == 0;
+    } else {
+        *fused = want_sets && L <= 256;
+        const int unit = *fused ? L : 16;
+        int nc = unit * std::max(1, 64 / unit);
+        nc = std::min(nc, (n_cols + unit - 1) / unit * unit);
+        while (nc > unit && tc_smem_bytes(nc, p->kt, p->np, p->np, p->fmt_bf16) == 0) nc -= unit;
+        if (tc_smem_bytes(nc, p->kt, p->np, p->np, p->fmt_bf16) == 0) {
+            nc = 16;
+            *fused = want_sets && cps == 1;
+        }
+        *n_chunk = nc;
+    }
+    if (tc_smem_bytes(*n_chunk, p->kt, p->np, p->np, p->fmt_bf16) == 0)
+        return set_error(EPSR_EINVAL, "sq exec: %d columns per CTA do not fit in shared memory", *n_chunk);
+    const int tiles = p->m_tiles * ((n_cols + *n_chunk - 1) / *n_chunk);
+    int ks = p->tc_k_split > 0 ? p->tc_k_split : (2 * std::max(1, p->sms) + tiles - 1) / tiles;
+    ks = std::max(1, std::min(ks, std::min(kTcMaxKSplit, p->stages)));
+    *k_split = ks;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_sq_plan_set_tiles(epsr_sq_plan *plan, int32_t n_chunk, int32_t k_split)
+{
+    if (!plan) return set_error(EPSR_EINVAL, "plan is NULL");
+    if (plan->mode == EPSR_SQ_FP32) return n_chunk == 0 && k_split == 0 ? EPSR_OK
+        : set_error(EPSR_EINVAL, "sq plan: the FP32 mode has no tensor-core tiling");
+    if (n_chunk < 0 || n_chunk > 256 || n_chunk % 16 || k_split < 0 || k_split > kTcMaxKSplit ||
+        k_split > plan->stages)
+        return set_error(EPSR_EINVAL, "sq plan: tiling (%d, %d) out of range", n_chunk, k_split);
+    if (n_chunk > 0 && tc_smem_bytes(n_chunk, plan->kt, plan->np, plan->np, plan->fmt_bf16) == 0)
+        return set_error(EPSR_EINVAL, "sq plan: %d columns per CTA do not fit in shared memory", n_chunk);
+    plan->tc_n_chunk = n_chunk;
+    plan->tc_k_split = k_split;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_sq_plan_get_tiles(const epsr_sq_plan *plan, int32_t n_cols, int32_t cols_per_set,
+                                      int32_t with_totals, int32_t *n_chunk, int32_t *k_split)
+{
+    if (!plan || !n_chunk || !k_split || n_cols < 1 || n_cols > plan->max_cols || cols_per_set < 1)
+        return set_error(EPSR_EINVAL, "sq plan: bad argument");
+    *n_chunk = *k_split = 0;
+    if (plan->mode == EPSR_SQ_FP32) return EPSR_OK;
+    int nc = 0, ks = 0;
+    bool fused = false;
+    int rc = tc_choose_tiles(plan, n_cols, cols_per_set, with_totals != 0, &nc, &ks, &fused);
+    if (rc) return rc;
+    *n_chunk = nc;
+    *k_split = ks;
+    return EPSR_OK;
+}
 
 extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, double dr, int32_t mode,
                                    int32_t max_cols, epsr_stream_t stream, epsr_sq_plan **out)
@@ -1040,11 +1136,11 @@ extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, d
             for (int j = 0; j < p->np; ++j)
                 if (i + j < p->np) { p->prod_a[np_] = i; p->prod_b[np_] = j; ++np_; }
         p->n_products = np_;
-        const int n_pad = std::min(256, ((max_cols + 15) / 16) * 16);
         const size_t a_bytes = (size_t)p->m_tiles * p->stages * p->np * 128 * p->kt * esize;
-        const size_t b_bytes = (size_t)p->stages * p->np * n_pad * p->kt * esize;
-        if ((rc = dalloc(&p->a_packed, a_bytes)) || (rc = dalloc(&p->b_packed, b_bytes)) ||
-            (rc = dalloc(&p->tc_status, 1))) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
+        if ((rc = dalloc(&p->a_packed, a_bytes)) || (rc = dalloc(&p->tc_status, 1))) {
             delete p;
             return rc;
         }
@@ -1088,38 +1184,47 @@ extern "C" int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, 
     a->n_cols = n_cols;
     for (int c = 0; c < n_cols; ++c) a->w[c] = w[c];
     int rc = EPSR_OK;
+    bool totals_done = false;
     if (plan->mode == EPSR_SQ_FP32) {
         rc = sq_exec_fp32(*a, (cudaStream_t)stream);
     } else {
-        // tensor cores: chunks of at most 256 columns (one N tile of M = 128 MMAs)
+        // tensor cores: one clustered launch over (M tiles, column chunks, K split)
         TcArgs *t = new (std::nothrow) TcArgs();
         if (!t) { delete a; return set_error(EPSR_ENOMEM, "host allocation failed"); }
-        for (int c0 = 0; c0 < n_cols && !rc; c0 += 256) {
-            const int nc = std::min(256, n_cols - c0);
+        int n_chunk = 0, k_split = 0;
+        bool fused = false;
+        rc = tc_choose_tiles(plan, n_cols, cols_per_set, S_total != nullptr, &n_chunk, &k_split, &fused);
+        if (!rc) {
             t->a_packed = plan->a_packed;
-            t->b_packed = plan->b_packed;
-            t->S_partial = a->S_partial + (size_t)c0 * plan->nQ;
+            t->g = g;
+            t->S_partial = (S_partial || !fused) ? a->S_partial : nullptr;
+            t->S_total = fused ? S_total : nullptr;
             t->status = plan->tc_status;
             t->nQ = plan->nQ;
             t->n_bins = plan->n_bins;
-            t->n_cols = nc;
-            t->n_pad = ((nc + 15) / 16) * 16;
-            int tc = 32;
-            while (tc < t->n_pad) tc <<= 1;
-            t->tmem_cols = tc;
+            t->n_cols = n_cols;
             t->m_tiles = plan->m_tiles;
-            t->stages = plan->stages;
-            t->kt = plan->kt;
+            t->units = plan->stages;
+            t->ku = plan->kt;
             t->np_a = t->np_b = plan->np;
             t->fmt_bf16 = plan->fmt_bf16;
             t->n_products = plan->n_products;
+            t->n_chunk = n_chunk;
+            t->k_split = k_split;
+            int tc = 32;
+            while (tc < n_chunk) tc <<= 1;
+            t->tmem_cols = tc;
+            t->cols_per_set = cols_per_set;
             for (int i = 0; i < 8; ++i) { t->prod_a[i] = plan->prod_a[i]; t->prod_b[i] = plan->prod_b[i]; }
-            for (int c = 0; c < nc; ++c) t->w[c] = w[c0 + c];
-            rc = tc_exec(*t, g + (size_t)c0 * plan->n_bins, (cudaStream_t)stream);
+            for (int c = 0; c < n_cols; ++c) t->w[c] = w[c];
+            if (fused)
+                for (int s_ = 0; s_ < n_cols / cols_per_set; ++s_) t->flat[s_] = flat[s_];
+            rc = tc_exec(*t, (cudaStream_t)stream);
+            totals_done = fused;
         }
         delete t;
     }
-    if (!rc && S_total) {
+    if (!rc && S_total && !totals_done) {
         SqWeights *W = new (std::nothrow) SqWeights();
         if (!W) { delete a; return set_error(EPSR_ENOMEM, "host allocation failed"); }
         for (int s = 0; s < n_cols / cols_per_set; ++s) W->flat[s] = flat[s];

@@ -20,19 +20,30 @@ struct SqWeights {
     double flat[EPSR_SQ_MAX_COLS];
 };
 
-// tcgen05 split-precision contraction (k_sq_tc.cu)
+// tcgen05 split-precision contraction (k_sq_tc.cu). Passed as a __grid_constant__ kernel
+// parameter (about 8 KB: the column weights and set backgrounds travel with the launch).
+constexpr int kTcMaxKSplit = 8;     // CTAs of one cluster sharing an output tile (portable size)
+constexpr int kTcSlots = 2;         // K-unit buffers per CTA (the copy of unit j+1 overlaps MMAs of j)
 struct TcArgs {
-    const unsigned char *a_packed;   // [m_tiles][stages][np_a] packed blocks of the sine matrix
-    unsigned char *b_packed;         // [stages][np_b] packed blocks of B = g - 1
-    float *S_partial;                // [n_cols][nQ]
-    int *status;                     // set to 1 if an MMA wait gave up
-    int nQ, n_bins, n_cols, n_pad, m_tiles, stages, kt, np_a, np_b, fmt_bf16, tmem_cols, n_products;
+    const unsigned char *a_packed;   // [m_tiles][units][np_a] packed blocks of the sine matrix
+    const float *g;                  // [n_cols][n_bins]; B = g - 1 is split and packed in the kernel
+    float *S_partial;                // [n_cols][nQ] or NULL
+    float *S_total;                  // [n_cols / cols_per_set][nQ] or NULL (fused sets only)
+    int *status;                     // set to 1 if a copy or MMA wait gave up
+    int nQ, n_bins, n_cols, m_tiles, units, ku, np_a, np_b, fmt_bf16, n_products;
+    int n_chunk;                     // columns per CTA: a multiple of 16, <= 256
+    int k_split;                     // CTAs per output tile (one cluster), <= kTcMaxKSplit
+    int tmem_cols;                   // power of two >= max(32, n_chunk)
+    int cols_per_set;                // S_total sets; n_chunk % cols_per_set == 0 when S_total != NULL
     int prod_a[8], prod_b[8];
-    double w[256];
+    double w[EPSR_SQ_MAX_COLS];
+    double flat[EPSR_SQ_MAX_COLS];
 };
 int tc_pack_a(const float *Kt, int nQ, int n_bins, int m_tiles, int stages, int kt, int np, int fmt_bf16,
               unsigned char *out, cudaStream_t stream);
-int tc_exec(const TcArgs &a, const float *g, cudaStream_t stream);
+// Bytes of dynamic shared memory one CTA of the contraction needs (0: does not fit).
+size_t tc_smem_bytes(int n_chunk, int ku, int np_a, int np_b, int fmt_bf16);
+int tc_exec(const TcArgs &a, cudaStream_t stream);
 
 int sq_build_kt(const float *Q_dev, int nQ, int n_bins, double dr, float *Kt, cudaStream_t stream);
 int sq_exec_fp32(const SqArgs &A, cudaStream_t stream);

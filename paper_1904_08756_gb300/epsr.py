@@ -36,7 +36,8 @@ EXPORTS = [
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
     "epsr_mc_set_cells", "epsr_sq_plan_status", "epsr_partial_gr_cells",
-    "epsr_bench_barrier_floor", "epsr_bench_alu_rate",
+    "epsr_bench_barrier_floor", "epsr_bench_alu_rate", "epsr_sq_plan_set_tiles",
+    "epsr_sq_plan_get_tiles",
 ]
 
 
@@ -129,6 +130,8 @@ def lib():
             "epsr_sq_exec_adjoint": ([vp, vp, i32, vp, i32, vp, vp], C.c_int),
             "epsr_chi2": ([vp, vp, vp, vp, i32, vp, i32, dbl, dbl, vp, vp, vp, vp], C.c_int),
             "epsr_partial_gr_noalloc": ([vp, vp, i64, i64, i32, i32, i32, i32, i32, vp, vp], C.c_int),
+            "epsr_sq_plan_set_tiles": ([vp, i32, i32], C.c_int),
+            "epsr_sq_plan_get_tiles": ([vp, i32, i32, i32, P(C.c_int32), P(C.c_int32)], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -447,6 +450,15 @@ class SqPlan:
         st = C.c_int32()
         _check(lib().epsr_sq_plan_status(self.h, C.byref(st), _stream(stream)), "epsr_sq_plan_status")
         return st.value
+
+    def epsr_sq_plan_set_tiles(self, n_chunk: int, k_split: int):
+        _check(lib().epsr_sq_plan_set_tiles(self.h, n_chunk, k_split), "epsr_sq_plan_set_tiles")
+
+    def epsr_sq_plan_get_tiles(self, n_cols: int, cols_per_set: int, with_totals: bool = True):
+        nc, ks = C.c_int32(), C.c_int32()
+        _check(lib().epsr_sq_plan_get_tiles(self.h, n_cols, cols_per_set, int(with_totals),
+                                            C.byref(nc), C.byref(ks)), "epsr_sq_plan_get_tiles")
+        return nc.value, ks.value
 
     def epsr_sq_exec(self, g, w: np.ndarray, cols_per_set: int, flat: np.ndarray,
                      S_partial=None, S_total=None, stream=None):

@@ -687,6 +687,46 @@ def test_sq_modes_against_oracle(mode, tol, n_cols):
     assert plan.epsr_sq_plan_status() == epsr.EPSR_OK
 
 
+@pytest.mark.parametrize("mode", [epsr.SQ_BF16X3, epsr.SQ_TF32X3, epsr.SQ_BF16X6])
+def test_sq_tensor_core_tilings_against_oracle(mode):
+    """Every tiling of the clustered tensor-core contraction -- columns per CTA with the set
+    totals in the same launch (48, 96) or in a separate pass (16, 64), and 1 to 8 CTAs per
+    output tile along the bins -- gives S(Q) within 1e-4 barn of the oracle, and repeated
+    calls are bit-identical (the K-split partials are added in a fixed order)."""
+    n_bins, dr, n_cols = 600, 0.02, 192
+    Q = 0.3 + np.arange(2000) * (39.7 / 1999)
+    g = _synthetic_g(n_cols, n_bins, dr, seed=5)
+    rng = np.random.default_rng(4)
+    w = rng.uniform(0.05, 0.4, n_cols)
+    flat = rng.uniform(0.2, 0.6, n_cols // 3)
+    Sp_ref, St_ref = oracle.sq(g.astype(np.float64), dr, Q.astype(np.float32).astype(np.float64), w, 3, flat)
+    plan = epsr.SqPlan(Q, n_bins, dr, mode, max_cols=n_cols)
+    gd = torch.from_numpy(g).to(DEV)
+    for n_chunk, k_split in ((48, 1), (48, 5), (96, 8), (16, 3), (64, 2), (0, 0)):
+        plan.epsr_sq_plan_set_tiles(n_chunk, k_split)
+        outs = []
+        for _ in range(2):
+            Sp = torch.zeros((n_cols, 2000), dtype=torch.float32, device=DEV)
+            St = torch.zeros((n_cols // 3, 2000), dtype=torch.float32, device=DEV)
+            plan.epsr_sq_exec(gd, w, 3, flat, Sp, St)
+            torch.cuda.synchronize()
+            outs.append((Sp.cpu().numpy(), St.cpu().numpy()))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+        err = max(np.abs(outs[0][0] - Sp_ref).max(), np.abs(outs[0][1] - St_ref).max())
+        print(f"mode {mode} tiling ({n_chunk}, {k_split}): max |dS| {err:.3e}")
+        assert err <= 1e-4, (n_chunk, k_split, err)
+        # totals alone (no partial output requested)
+        St2 = torch.zeros((n_cols // 3, 2000), dtype=torch.float32, device=DEV)
+        plan.epsr_sq_exec(gd, w, 3, flat, None, St2)
+        torch.cuda.synchronize()
+        assert np.array_equal(St2.cpu().numpy(), outs[0][1])
+    assert plan.epsr_sq_plan_status() == epsr.EPSR_OK
+    with pytest.raises(epsr.EpsrError):
+        plan.epsr_sq_plan_set_tiles(40, 1)          # not a multiple of 16
+    with pytest.raises(epsr.EpsrError):
+        plan.epsr_sq_plan_set_tiles(48, 9)          # more than one portable cluster
+
+
 def test_checkpoint_resume_is_bit_exact():
     s = synth.silica_box(800, seed=91)
     ep = (np.random.default_rng(2).normal(size=(3, s.n_bins)) * 0.2).astype(np.float32)
