@@ -207,7 +207,8 @@ def run_reference(args):
 
 def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
     """S(Q) of the same resident g(r) columns in every contraction mode: mean time of one
-    epsr_sq_exec (CUDA events on the launching stream, L2 flushed before each) and the largest
+    epsr_sq_exec (CUDA events on the launching stream, L2 flushed before each, the GPU kept
+    busy ahead of the events so that no host latency falls between them) and the largest
     difference from the FP32 mode's result."""
     import torch
     from paper_1904_08756_gb300 import epsr
@@ -226,6 +227,9 @@ def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(reps)]
             for a, b in evs:
+                # a device-side delay ahead of the flush keeps the GPU behind the host, so the
+                # events bracket the contraction alone and not the host's enqueue latency
+                torch.cuda._sleep(400_000)
                 flush.fill_(1.0)
                 a.record(stream)
                 plan.epsr_sq_exec(g, ws, 3, flats, None, S, stream=stream.cuda_stream)

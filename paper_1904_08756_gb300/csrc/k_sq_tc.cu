@@ -39,6 +39,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;
 constexpr unsigned long long kTcSpinLimit = 1ull << 26;
 constexpr int kTcMaxUnits = 64;     // K units of one CTA's range (n_bins <= 4096 at 64 per unit)
+constexpr int kTcLoadBatch = 32;    // g values per thread loaded before any is packed
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
     int u0, u1;
     tc_unit_range(A.units, A.k_split, z, &u0, &u1);
     const int nu = u1 - u0;
+    const int ku_shift = __ffs(A.ku) - 1;                   // ku is a power of two
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -295,22 +297,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
                 "l"(src), "r"(bytes), "r"(mb)
                 : "memory");
         }
-        // B = g - 1 for this CTA's columns and unit, split into pieces, packed K-major
+        // B = g - 1 for this CTA's columns and unit, split into pieces, packed K-major; the
+        // loads of a batch are all issued before the first is used
         const int k0 = u * A.ku;
-        for (int e = tid; e < A.n_chunk * A.ku; e += kTcThreads) {
-            const int row = e / A.ku, kin = e % A.ku;
-            const int c = c_base + row, k = k0 + kin;
-            const float v = (c < A.n_cols && k < A.n_bins) ? A.g[(size_t)c * A.n_bins + k] - 1.0f : 0.f;
-            const size_t off = tc_elem_offset(row, kin, esize, A.ku);
-            if (A.fmt_bf16) {
-                unsigned short pc[3];
-                split_bf16(v, A.np_b, pc);
-                for (int i = 0; i < A.np_b; ++i)
-                    *reinterpret_cast<unsigned short *>(sb_s + i * b_piece + off) = pc[i];
-            } else {
-                unsigned pc[3];
-                split_tf32(v, A.np_b, pc);
-                for (int i = 0; i < A.np_b; ++i) *reinterpret_cast<unsigned *>(sb_s + i * b_piece + off) = pc[i];
+        const int n_el = A.n_chunk * A.ku;
+        for (int e0 = 0; e0 < n_el; e0 += kTcThreads * kTcLoadBatch) {
+            float v[kTcLoadBatch];
+#pragma unroll
+            for (int i = 0; i < kTcLoadBatch; ++i) {
+                const int e = e0 + i * kTcThreads + tid;
+                const int row = e >> ku_shift, kin = e & (A.ku - 1);
+                const int c = c_base + row, k = k0 + kin;
+                v[i] = (e < n_el && c < A.n_cols && k < A.n_bins) ? __ldg(A.g + (size_t)c * A.n_bins + k) : 1.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < kTcLoadBatch; ++i) {
+                const int e = e0 + i * kTcThreads + tid;
+                if (e >= n_el) break;
+                const int row = e >> ku_shift, kin = e & (A.ku - 1);
+                const size_t off = tc_elem_offset(row, kin, esize, A.ku);
+                const float x = v[i] - 1.0f;
+                if (A.fmt_bf16) {
+                    float r = x;
+                    for (int pc = 0; pc < A.np_b; ++pc) {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(r);
+                        *reinterpret_cast<unsigned short *>(sb_s + pc * b_piece + off) = __bfloat16_as_ushort(h);
+                        r = r - __bfloat162float(h);
+                    }
+                } else {
+                    float r = x;
+                    for (int pc = 0; pc < A.np_b; ++pc) {
+                        const unsigned h = tf32_round(r);
+                        *reinterpret_cast<unsigned *>(sb_s + pc * b_piece + off) = h;
+                        r = r - __uint_as_float(h);
+                    }
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -381,17 +402,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
         const bool sets = A.S_total != nullptr;
         const int grp = sets ? A.cols_per_set : 1;
         const unsigned red_addr = smem_u32(red);
+        unsigned base[kTcMaxKSplit];
+#pragma unroll
+        for (int r = 0; r < kTcMaxKSplit; ++r)
+            base[r] = (A.k_split > 1 && r < A.k_split) ? map_rank(red_addr, (unsigned)r) : red_addr;
         for (int gi = (int)my_rank; gi * grp < A.n_chunk; gi += A.k_split) {
             const int cg = c_base + gi * grp;
             if (cg >= A.n_cols) break;
             double tot = 0.0;
             for (int t = 0; t < grp; ++t) {
                 const int cl = gi * grp + t, c = cg + t;
+                const unsigned off = (unsigned)((cl * kTcM + row) * sizeof(float));
+                // every CTA's partial of this element in flight at once, summed in rank order
+                float p[kTcMaxKSplit];
+#pragma unroll
+                for (int r = 0; r < kTcMaxKSplit; ++r)
+                    p[r] = r < A.k_split ? (A.k_split > 1 ? ld_cluster_f32(base[r] + off) : red[cl * kTcM + row]) : 0.f;
                 double acc = 0.0;
-                for (int r = 0; r < A.k_split; ++r) {
-                    const unsigned a = red_addr + (unsigned)((cl * kTcM + row) * sizeof(float));
-                    acc += (double)(A.k_split > 1 ? ld_cluster_f32(map_rank(a, (unsigned)r)) : red[cl * kTcM + row]);
-                }
+#pragma unroll
+                for (int r = 0; r < kTcMaxKSplit; ++r)
+                    if (r < A.k_split) acc += (double)p[r];
                 const float sp = (float)(acc * A.w[c]);
                 if (q < A.nQ && A.S_partial) A.S_partial[(size_t)c * A.nQ + q] = sp;
                 tot += (double)sp;
