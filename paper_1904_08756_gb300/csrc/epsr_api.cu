@@ -1023,7 +1023,6 @@ struct epsr_sq_plan {
     unsigned char *a_packed = nullptr;
     int *tc_status = nullptr;
     int fmt_bf16 = 1, np = 2, kt = 64, stages = 0, m_tiles = 0, n_products = 0;
-    int prod_a[8] = {0}, prod_b[8] = {0};
     int tc_n_chunk = 0, tc_k_split = 0;   // tensor-core tiling set by epsr_sq_plan_set_tiles (0 = rule)
     int sms = 0;
     ~epsr_sq_plan()
@@ -1038,33 +1037,41 @@ static int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
 
 // Tiling of the tensor-core contraction: columns per CTA (a multiple of 16, and of the set size
 // when the set totals are fused into the epilogue) and the number of CTAs sharing one output
-// tile along K (one cluster). The rule aims at two CTAs per SM; a tiling set on the plan
-// (epsr_sq_plan_set_tiles, e.g. by the autotuner) takes precedence.
+// tile along K (one cluster). The rule aims at about two CTAs per SM with power-of-two clusters;
+// a tiling set on the plan (epsr_sq_plan_set_tiles, e.g. by the autotuner) takes precedence.
 static int tc_choose_tiles(const epsr_sq_plan *p, int n_cols, int cps, bool want_sets, int *n_chunk,
                            int *k_split, bool *fused)
 {
     const int L = 16 / gcd_i(16, cps) * cps;          // lcm(16, cols_per_set)
-    const int n_pad = (n_cols + 15) / 16 * 16;
+    const bool user = p->tc_n_chunk > 0 || p->tc_k_split > 0;
+    int nc, unit;
     if (p->tc_n_chunk > 0) {
-        *n_chunk = std::min(p->tc_n_chunk, std::max(16, n_pad));
-        *fused = want_sets && *n_chunk % cps == 0;
+        nc = std::min(p->tc_n_chunk, std::max(16, (n_cols + 15) / 16 * 16));
+        *fused = want_sets && nc % cps == 0;
+        unit = 16;
     } else {
         *fused = want_sets && L <= 256;
-        const int unit = *fused ? L : 16;
-        int nc = unit * std::max(1, 64 / unit);
+        unit = *fused ? L : 16;
+        nc = unit * std::max(1, 64 / unit);
         nc = std::min(nc, (n_cols + unit - 1) / unit * unit);
-        while (nc > unit && tc_smem_bytes(nc, p->kt, p->np, p->np, p->fmt_bf16) == 0) nc -= unit;
-        if (tc_smem_bytes(nc, p->kt, p->np, p->np, p->fmt_bf16) == 0) {
-            nc = 16;
-            *fused = want_sets && cps == 1;
-        }
-        *n_chunk = nc;
     }
-    if (tc_smem_bytes(*n_chunk, p->kt, p->np, p->np, p->fmt_bf16) == 0)
-        return set_error(EPSR_EINVAL, "sq exec: %d columns per CTA do not fit in shared memory", *n_chunk);
-    const int tiles = p->m_tiles * ((n_cols + *n_chunk - 1) / *n_chunk);
-    int ks = p->tc_k_split > 0 ? p->tc_k_split : (2 * std::max(1, p->sms) + tiles - 1) / tiles;
+    const int tiles = p->m_tiles * ((n_cols + nc - 1) / nc);
+    int ks = p->tc_k_split;
+    if (ks <= 0) {
+        // about two CTAs per SM, in clusters of a power of two (they pack onto the GPCs better)
+        const int want = std::min((2 * std::max(1, p->sms) + tiles - 1) / tiles, std::min(kTcMaxKSplit, p->stages));
+        ks = 1;
+        while (ks * 2 <= want) ks *= 2;
+    }
     ks = std::max(1, std::min(ks, std::min(kTcMaxKSplit, p->stages)));
+    const int grp = *fused ? cps : 1;
+    while (tc_smem_bytes(nc, p->np, ks, grp) == 0) {
+        if (user) return set_error(EPSR_EINVAL, "sq exec: tiling (%d, %d) does not fit in shared memory", nc, ks);
+        if (nc > unit) nc -= unit;
+        else if (ks > 1) --ks;
+        else return set_error(EPSR_EINVAL, "sq exec: no tiling fits in shared memory");
+    }
+    *n_chunk = nc;
     *k_split = ks;
     return EPSR_OK;
 }
@@ -1077,7 +1084,7 @@ extern "C" int epsr_sq_plan_set_tiles(epsr_sq_plan *plan, int32_t n_chunk, int32
     if (n_chunk < 0 || n_chunk > 256 || n_chunk % 16 || k_split < 0 || k_split > kTcMaxKSplit ||
         k_split > plan->stages)
         return set_error(EPSR_EINVAL, "sq plan: tiling (%d, %d) out of range", n_chunk, k_split);
-    if (n_chunk > 0 && tc_smem_bytes(n_chunk, plan->kt, plan->np, plan->np, plan->fmt_bf16) == 0)
+    if (n_chunk > 0 && tc_smem_bytes(n_chunk, plan->np, std::max(1, k_split), 1) == 0)
         return set_error(EPSR_EINVAL, "sq plan: %d columns per CTA do not fit in shared memory", n_chunk);
     plan->tc_n_chunk = n_chunk;
     plan->tc_k_split = k_split;
@@ -1131,11 +1138,7 @@ extern "C" int epsr_sq_plan_create(const float *Q, int32_t nQ, int32_t n_bins, d
         p->kt = 128 / esize;                       // 128-byte rows per stage
         p->stages = (n_bins + p->kt - 1) / p->kt;
         p->m_tiles = (nQ + 127) / 128;
-        int np_ = 0;
-        for (int i = 0; i < p->np; ++i)
-            for (int j = 0; j < p->np; ++j)
-                if (i + j < p->np) { p->prod_a[np_] = i; p->prod_b[np_] = j; ++np_; }
-        p->n_products = np_;
+        p->n_products = p->np * (p->np + 1) / 2;      // split products with i + j < np
         const size_t a_bytes = (size_t)p->m_tiles * p->stages * p->np * 128 * p->kt * esize;
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1215,10 +1218,14 @@ extern "C" int epsr_sq_exec(epsr_sq_plan *plan, const float *g, int32_t n_cols, 
             while (tc < n_chunk) tc <<= 1;
             t->tmem_cols = tc;
             t->cols_per_set = cols_per_set;
-            for (int i = 0; i < 8; ++i) { t->prod_a[i] = plan->prod_a[i]; t->prod_b[i] = plan->prod_b[i]; }
-            for (int c = 0; c < n_cols; ++c) t->w[c] = w[c];
+            const int grp = fused ? cols_per_set : 1;
+            const long long ctas = (long long)plan->m_tiles * ((n_cols + n_chunk - 1) / n_chunk) * k_split;
+            t->slots = tc_slots_for(n_chunk, plan->np, (plan->stages + k_split - 1) / k_split, k_split, grp,
+                                    ctas <= plan->sms);
+            t->recv_cols = tc_recv_cols(n_chunk, grp, k_split);
+            for (int c = 0; c < n_cols; ++c) t->w[c] = (float)w[c];
             if (fused)
-                for (int s_ = 0; s_ < n_cols / cols_per_set; ++s_) t->flat[s_] = flat[s_];
+                for (int s_ = 0; s_ < n_cols / cols_per_set; ++s_) t->flat[s_] = (float)flat[s_];
             rc = tc_exec(*t, (cudaStream_t)stream);
             totals_done = fused;
         }

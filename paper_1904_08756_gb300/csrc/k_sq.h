@@ -21,9 +21,9 @@ struct SqWeights {
 };
 
 // tcgen05 split-precision contraction (k_sq_tc.cu). Passed as a __grid_constant__ kernel
-// parameter (about 8 KB: the column weights and set backgrounds travel with the launch).
+// parameter (about 4 KB: the column weights and set backgrounds travel with the launch).
 constexpr int kTcMaxKSplit = 8;     // CTAs of one cluster sharing an output tile (portable size)
-constexpr int kTcSlots = 2;         // K-unit buffers per CTA (the copy of unit j+1 overlaps MMAs of j)
+constexpr int kTcMaxSlots = 8;      // K-unit buffers per CTA (copies of later units overlap MMAs)
 struct TcArgs {
     const unsigned char *a_packed;   // [m_tiles][units][np_a] packed blocks of the sine matrix
     const float *g;                  // [n_cols][n_bins]; B = g - 1 is split and packed in the kernel
@@ -35,14 +35,20 @@ struct TcArgs {
     int k_split;                     // CTAs per output tile (one cluster), <= kTcMaxKSplit
     int tmem_cols;                   // power of two >= max(32, n_chunk)
     int cols_per_set;                // S_total sets; n_chunk % cols_per_set == 0 when S_total != NULL
-    int prod_a[8], prod_b[8];
-    double w[EPSR_SQ_MAX_COLS];
-    double flat[EPSR_SQ_MAX_COLS];
+    int slots;                       // K-unit buffers per CTA, 2 .. kTcMaxSlots
+    int recv_cols;                   // columns a cluster rank owns in the reduction, at most
+    float w[EPSR_SQ_MAX_COLS];
+    float flat[EPSR_SQ_MAX_COLS];
 };
 int tc_pack_a(const float *Kt, int nQ, int n_bins, int m_tiles, int stages, int kt, int np, int fmt_bf16,
               unsigned char *out, cudaStream_t stream);
-// Bytes of dynamic shared memory one CTA of the contraction needs (0: does not fit).
-size_t tc_smem_bytes(int n_chunk, int ku, int np_a, int np_b, int fmt_bf16);
+// Shared memory of one CTA of the contraction (tc_smem_bytes: with two unit buffers, 0 if it
+// does not fit), the unit buffers a CTA with units_per_cta units gets, and the columns one
+// cluster rank owns in the reduction (grp: set size when the set totals are fused, else 1).
+size_t tc_smem_need(int n_chunk, int np, int slots, int k_split, int grp);
+size_t tc_smem_bytes(int n_chunk, int np, int k_split, int grp);
+int tc_slots_for(int n_chunk, int np, int units_per_cta, int k_split, int grp, bool one_per_sm);
+int tc_recv_cols(int n_chunk, int grp, int k_split);
 int tc_exec(const TcArgs &a, cudaStream_t stream);
 
 int sq_build_kt(const float *Q_dev, int nQ, int n_bins, double dr, float *Kt, cudaStream_t stream);

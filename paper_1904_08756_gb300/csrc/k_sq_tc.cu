@@ -35,11 +35,12 @@ namespace epsr {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;     // 8 warps: warps w and w + 4 share TMEM lane quarter w
 constexpr int kTcM = 128;
 constexpr unsigned long long kTcSpinLimit = 1ull << 26;
 constexpr int kTcMaxUnits = 64;     // K units of one CTA's range (n_bins <= 4096 at 64 per unit)
-constexpr int kTcLoadBatch = 32;    // g values per thread loaded before any is packed
+constexpr size_t kTcSmemMax = 220 * 1024;        // dynamic shared memory of one CTA, at most
+constexpr size_t kTcSmemTwoPerSm = 110 * 1024;   // budget that leaves room for two CTAs per SM
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
@@ -190,7 +191,7 @@ __device__ __forceinline__ unsigned map_rank(unsigned addr, unsigned rank)
 __device__ __forceinline__ float ld_cluster_f32(unsigned addr)
 {
     float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
     return v;
 }
 
@@ -201,23 +202,60 @@ __device__ __forceinline__ int ld_cluster_s32(unsigned addr)
     return v;
 }
 
-__host__ __device__ __forceinline__ size_t tc_a_unit_bytes(int ku, int np, int esize)
+__host__ __device__ __forceinline__ size_t tc_a_unit_bytes(int np)
 {
-    return (size_t)np * kTcM * ku * esize;
+    return (size_t)np * kTcM * 128;                     // 128 bytes of K per row and piece
 }
 
-__host__ __device__ __forceinline__ size_t tc_b_unit_bytes(int n_chunk, int ku, int np, int esize)
+__host__ __device__ __forceinline__ size_t tc_b_unit_bytes(int n_chunk, int np)
 {
-    return (size_t)np * n_chunk * ku * esize;
+    return (size_t)np * n_chunk * 128;
 }
 
-size_t tc_smem_bytes(int n_chunk, int ku, int np_a, int np_b, int fmt_bf16)
+// Dynamic shared memory of one CTA: `slots` (A, B) unit buffers; the FP32 partial
+// accumulator [n_chunk][128] reuses the A buffers once the MMAs are done.
+// Columns of a chunk owned by cluster rank r for the reduction: the chunk's column groups
+// (sets, or single columns) split into k_split contiguous ranges.
+__host__ __device__ __forceinline__ void tc_owned_cols(int ncol, int grp, int k_split, int r, int *c_lo, int *c_hi)
 {
-    const int esize = fmt_bf16 ? 2 : 4;
-    const size_t a = kTcSlots * tc_a_unit_bytes(ku, np_a, esize);
+    const int ng = (ncol + grp - 1) / grp;
+    const int g_lo = (int)((long long)ng * r / k_split), g_hi = (int)((long long)ng * (r + 1) / k_split);
+    *c_lo = g_lo * grp;
+    *c_hi = min(ncol, g_hi * grp);
+}
+
+int tc_recv_cols(int n_chunk, int grp, int k_split)
+{
+    const int ng = (n_chunk + grp - 1) / grp;
+    return (ng + k_split - 1) / k_split * grp;
+}
+
+// Dynamic shared memory of one CTA: `slots` (A, B) unit buffers; once the MMAs are done the A
+// buffers hold this CTA's FP32 partial [n_chunk][128] and the B buffers the partials the other
+// CTAs of the cluster push for the columns this CTA owns ([k_split][recv_cols][128]).
+size_t tc_smem_need(int n_chunk, int np, int slots, int k_split, int grp)
+{
+    const size_t a = (size_t)slots * tc_a_unit_bytes(np);
     const size_t red = (size_t)n_chunk * kTcM * sizeof(float);
-    const size_t total = (a > red ? a : red) + kTcSlots * tc_b_unit_bytes(n_chunk, ku, np_b, esize);
-    return total <= 220 * 1024 ? total : 0;
+    const size_t b = (size_t)slots * tc_b_unit_bytes(n_chunk, np);
+    const size_t recv = k_split > 1 ? (size_t)k_split * tc_recv_cols(n_chunk, grp, k_split) * kTcM * sizeof(float) : 0;
+    return (a > red ? a : red) + (b > recv ? b : recv);
+}
+
+size_t tc_smem_bytes(int n_chunk, int np, int k_split, int grp)
+{
+    const size_t total = tc_smem_need(n_chunk, np, 2, k_split, grp);
+    return total <= kTcSmemMax ? total : 0;
+}
+
+int tc_slots_for(int n_chunk, int np, int units_per_cta, int k_split, int grp, bool one_per_sm)
+{
+    // as many unit buffers as the CTA has units, within a budget that leaves room for two CTAs
+    // per SM (unless the grid has at most one CTA per SM), at least two
+    const size_t budget = one_per_sm ? kTcSmemMax : kTcSmemTwoPerSm;
+    int s = 2;
+    while (s < units_per_cta && s < kTcMaxSlots && tc_smem_need(n_chunk, np, s + 1, k_split, grp) <= budget) ++s;
+    return s;
 }
 
 // K unit range [u0, u1) of split z out of k_split over `units` units (balanced).
@@ -227,30 +265,105 @@ __host__ __device__ __forceinline__ void tc_unit_range(int units, int k_split, i
     *u1 = (int)((long long)units * (z + 1) / k_split);
 }
 
+// Packs units u and u + 1 (n_units = 1 or 2) of B = g - 1 for this CTA's columns into slots
+// sb0 and sb1: every thread takes 16-byte core-matrix rows (8 BF16 or 4 TF32 values), threads
+// 8k..8k+7 the 8 rows of one core matrix (contiguous in shared memory), and the loads of both
+// units are issued before any is used.
+template <bool BF16, int NP>
+__device__ __forceinline__ void tc_stage_b(const TcArgs &A, unsigned char *sb0, unsigned char *sb1, size_t b_piece,
+                                           int u, int n_units, int c_base, int tid)
+{
+    constexpr int EPV = BF16 ? 8 : 4;              // values per 16-byte vector
+    constexpr int KU = 8 * EPV;                    // K values per unit (128 bytes per row)
+    constexpr int BATCH = 2;
+    const int nvec = A.n_chunk * 8;
+    for (int v0 = 0; v0 < nvec; v0 += kTcThreads * BATCH) {
+        float x[2][BATCH][EPV];
+#pragma unroll
+        for (int uu = 0; uu < 2; ++uu)
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int v = v0 + i * kTcThreads + tid;
+                const int r = v & 7, h = (v >> 3) & 7, g8 = v >> 6;
+                const int c = c_base + g8 * 8 + r, k = (u + uu) * KU + h * EPV;
+                const bool ok = uu < n_units && v < nvec && c < A.n_cols;
+                const float *src = A.g + (size_t)(ok ? c : 0) * A.n_bins + k;
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) x[uu][i][e] = (ok && k + e < A.n_bins) ? __ldg(src + e) : 1.0f;
+            }
+#pragma unroll
+        for (int uu = 0; uu < 2; ++uu) {
+            if (uu >= n_units) break;
+            unsigned char *sb_s = uu ? sb1 : sb0;
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int v = v0 + i * kTcThreads + tid;
+                if (v >= nvec) break;
+                const int r = v & 7, h = (v >> 3) & 7, g8 = v >> 6;
+                const size_t off = (size_t)(g8 * 8 + h) * 128 + r * 16;
+                float res[EPV];
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) res[e] = x[uu][i][e] - 1.0f;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    unsigned wv[4];
+                    if (BF16) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __nv_bfloat16 lo = __float2bfloat16_rn(res[2 * e]);
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(res[2 * e + 1]);
+                            wv[e] = (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+                            res[2 * e] -= __bfloat162float(lo);
+                            res[2 * e + 1] -= __bfloat162float(hi);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            wv[e] = tf32_round(res[e]);
+                            res[e] -= __uint_as_float(wv[e]);
+                        }
+                    }
+                    *reinterpret_cast<uint4 *>(sb_s + p * b_piece + off) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                }
+            }
+        }
+    }
+}
+
+template <bool BF16, int NP>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_constant__ TcArgs A)
 {
+    constexpr int ES = BF16 ? 2 : 4;
+    constexpr int KU = 128 / ES;                            // K values per unit
+    constexpr int KMMA = 32 / ES;                           // K per instruction: 16 BF16, 8 TF32
+    constexpr size_t A_PIECE = (size_t)kTcM * 128;
+    constexpr unsigned SBO = 8u * 128u;                     // stride between 8-row groups
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long mbar_full[kTcSlots];
-    __shared__ __align__(8) unsigned long long mbar_empty[kTcSlots];
+    __shared__ __align__(8) unsigned long long mbar_full[kTcMaxSlots];
+    __shared__ __align__(8) unsigned long long mbar_empty[kTcMaxSlots];
+    __shared__ __align__(8) unsigned long long mbar_red;
     __shared__ unsigned tmem_base_sh;
     __shared__ int err_sh;
+    __shared__ float w_sh[256], flat_sh[256];              // this chunk's column weights, set backgrounds
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mt = blockIdx.x, chunk = blockIdx.y, z = blockIdx.z;
-    const int esize = A.fmt_bf16 ? 2 : 4;
-    const int kmma = 32 / esize;                            // K per instruction: 16 BF16, 8 TF32
-    const size_t a_piece = (size_t)kTcM * A.ku * esize;
-    const size_t b_piece = (size_t)A.n_chunk * A.ku * esize;
-    const size_t a_slot = A.np_a * a_piece, b_slot = A.np_b * b_piece;
+    const int S = A.slots;
+    const size_t b_piece = (size_t)A.n_chunk * 128;
+    const size_t a_slot = NP * A_PIECE, b_slot = NP * b_piece;
     const size_t red_bytes = (size_t)A.n_chunk * kTcM * sizeof(float);
     unsigned char *sa = smem;                               // [slot][piece] A blocks
-    unsigned char *sb = smem + (kTcSlots * a_slot > red_bytes ? kTcSlots * a_slot : red_bytes);
+    unsigned char *sb = smem + (S * a_slot > red_bytes ? S * a_slot : red_bytes);
     float *red = reinterpret_cast<float *>(smem);           // [n_chunk][128] partial, after the MMAs
-    const unsigned sbo = (unsigned)(A.ku * esize / 16) * 128u;   // stride between 8-row groups
+    float *recv = reinterpret_cast<float *>(sb);            // [k_split][recv_cols][128], pushed partials
     const int c_base = chunk * A.n_chunk;
     int u0, u1;
     tc_unit_range(A.units, A.k_split, z, &u0, &u1);
     const int nu = u1 - u0;
-    const int ku_shift = __ffs(A.ku) - 1;                   // ku is a power of two
+    for (int c = tid; c < A.n_chunk; c += kTcThreads) {
+        const int cc = min(c_base + c, A.n_cols - 1);
+        w_sh[c] = A.w[cc];
+        flat_sh[c] = A.S_total ? A.flat[cc / A.cols_per_set] : 0.f;
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -260,99 +373,81 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
     }
     if (tid == 0) {
         err_sh = 0;
-        for (int i = 0; i < kTcSlots; ++i) {
+        for (int i = 0; i < S; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_full[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_empty[i])));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_red)));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        // prologue: the copies of the first min(nu, S) units, all in flight at once
+        for (int j = 0; j < nu && j < S; ++j) {
+            const unsigned mb = smem_u32(&mbar_full[j]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"((unsigned)a_slot) : "memory");
+            const unsigned char *src = A.a_packed + ((size_t)mt * A.units + u0 + j) * a_slot;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(sa + j * a_slot)),
+                "l"(src), "r"((unsigned)a_slot), "r"(mb)
+                : "memory");
+        }
     }
+    for (int j = 0; j < nu && j < S; j += 2)
+        tc_stage_b<BF16, NP>(A, sb + j * b_slot, sb + (j + 1) * b_slot, b_piece, u0 + j, min(2, min(nu, S) - j),
+                             c_base, tid);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const unsigned tmem_d = tmem_base_sh;
-    const unsigned idesc = make_idesc(A.fmt_bf16 ? 1u : 2u, kTcM, (unsigned)A.n_chunk);
+    const unsigned idesc = make_idesc(BF16 ? 1u : 2u, kTcM, (unsigned)A.n_chunk);
     int pending_slot = -1;                                  // thread 0: a copy whose wait gave up
     unsigned pending_parity = 0;
 
     for (int j = 0; j < nu; ++j) {
-        const int slot = j % kTcSlots;
-        if (j >= kTcSlots) {
-            // the MMAs that last read this slot (unit j - kTcSlots) must be complete
-            if (!mbar_wait_bounded(smem_u32(&mbar_empty[slot]), (unsigned)((j / kTcSlots - 1) & 1)))
-                atomicOr(&err_sh, 1);
-        }
-        __syncthreads();
-        if (err_sh) break;
-        const int u = u0 + j;
+        const int slot = j % S;
         unsigned char *sa_s = sa + slot * a_slot;
         unsigned char *sb_s = sb + slot * b_slot;
-        if (tid == 0) {
-            const unsigned bytes = (unsigned)a_slot;
-            const unsigned mb = smem_u32(&mbar_full[slot]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-            const unsigned char *src = A.a_packed + ((size_t)mt * A.units + u) * a_slot;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(sa_s)),
-                "l"(src), "r"(bytes), "r"(mb)
-                : "memory");
-        }
-        // B = g - 1 for this CTA's columns and unit, split into pieces, packed K-major; the
-        // loads of a batch are all issued before the first is used
-        const int k0 = u * A.ku;
-        const int n_el = A.n_chunk * A.ku;
-        for (int e0 = 0; e0 < n_el; e0 += kTcThreads * kTcLoadBatch) {
-            float v[kTcLoadBatch];
-#pragma unroll
-            for (int i = 0; i < kTcLoadBatch; ++i) {
-                const int e = e0 + i * kTcThreads + tid;
-                const int row = e >> ku_shift, kin = e & (A.ku - 1);
-                const int c = c_base + row, k = k0 + kin;
-                v[i] = (e < n_el && c < A.n_cols && k < A.n_bins) ? __ldg(A.g + (size_t)c * A.n_bins + k) : 1.0f;
+        if (j >= S) {
+            // refill: the MMAs that last read this slot (unit j - S) must be complete
+            if (!mbar_wait_bounded(smem_u32(&mbar_empty[slot]), (unsigned)((j / S - 1) & 1)))
+                atomicOr(&err_sh, 1);
+            __syncthreads();
+            if (err_sh) break;
+            if (tid == 0) {
+                const unsigned mb = smem_u32(&mbar_full[slot]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"((unsigned)a_slot) : "memory");
+                const unsigned char *src = A.a_packed + ((size_t)mt * A.units + u0 + j) * a_slot;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(sa_s)),
+                    "l"(src), "r"((unsigned)a_slot), "r"(mb)
+                    : "memory");
             }
-#pragma unroll
-            for (int i = 0; i < kTcLoadBatch; ++i) {
-                const int e = e0 + i * kTcThreads + tid;
-                if (e >= n_el) break;
-                const int row = e >> ku_shift, kin = e & (A.ku - 1);
-                const size_t off = tc_elem_offset(row, kin, esize, A.ku);
-                const float x = v[i] - 1.0f;
-                if (A.fmt_bf16) {
-                    float r = x;
-                    for (int pc = 0; pc < A.np_b; ++pc) {
-                        const __nv_bfloat16 h = __float2bfloat16_rn(r);
-                        *reinterpret_cast<unsigned short *>(sb_s + pc * b_piece + off) = __bfloat16_as_ushort(h);
-                        r = r - __bfloat162float(h);
-                    }
-                } else {
-                    float r = x;
-                    for (int pc = 0; pc < A.np_b; ++pc) {
-                        const unsigned h = tf32_round(r);
-                        *reinterpret_cast<unsigned *>(sb_s + pc * b_piece + off) = h;
-                        r = r - __uint_as_float(h);
-                    }
-                }
-            }
+            tc_stage_b<BF16, NP>(A, sb_s, sb_s, b_piece, u0 + j, 1, c_base, tid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            if (!mbar_wait_bounded(smem_u32(&mbar_full[slot]), (unsigned)((j / kTcSlots) & 1))) {
+        if (tid == 0 && !err_sh) {
+            if (!mbar_wait_bounded(smem_u32(&mbar_full[slot]), (unsigned)((j / S) & 1))) {
                 err_sh = 1;
                 pending_slot = slot;
-                pending_parity = (unsigned)((j / kTcSlots) & 1);
+                pending_parity = (unsigned)((j / S) & 1);
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                for (int kk = 0; kk < A.ku / kmma; ++kk) {
+#pragma unroll
+                for (int kk = 0; kk < KU / KMMA; ++kk) {
                     const unsigned koff = (unsigned)kk * 256u;    // two 16-byte k-groups per MMA
-                    for (int pr = 0; pr < A.n_products; ++pr) {
-                        const int pa = A.prod_a[pr], pb = A.prod_b[pr];
-                        const unsigned long long da = make_desc(smem_u32(sa_s + pa * a_piece) + koff, 128u, sbo);
-                        const unsigned long long db = make_desc(smem_u32(sb_s + pb * b_piece) + koff, 128u, sbo);
-                        const unsigned acc = (j > 0 || kk > 0 || pr > 0) ? 1u : 0u;
-                        if (A.fmt_bf16) mma_bf16(tmem_d, da, db, idesc, acc);
-                        else mma_tf32(tmem_d, da, db, idesc, acc);
-                    }
+#pragma unroll
+                    for (int pa = 0; pa < NP; ++pa)
+#pragma unroll
+                        for (int pb = 0; pb < NP; ++pb) {
+                            if (pa + pb >= NP) continue;        // products down to the split order
+                            const unsigned long long da = make_desc(smem_u32(sa_s + pa * A_PIECE) + koff, 128u, SBO);
+                            const unsigned long long db = make_desc(smem_u32(sb_s + pb * b_piece) + koff, 128u, SBO);
+                            const unsigned acc = (j > 0 || kk > 0 || pa > 0 || pb > 0) ? 1u : 0u;
+                            if (BF16) mma_bf16(tmem_d, da, db, idesc, acc);
+                            else mma_tf32(tmem_d, da, db, idesc, acc);
+                        }
                 }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -364,8 +459,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
     if (!err_sh && nu > 0) {
         // the last commit covers every MMA this thread issued
         const int j = nu - 1;
-        if (!mbar_wait_bounded(smem_u32(&mbar_empty[j % kTcSlots]), (unsigned)((j / kTcSlots) & 1)))
-            atomicOr(&err_sh, 1);
+        if (!mbar_wait_bounded(smem_u32(&mbar_empty[j % S]), (unsigned)((j / S) & 1))) atomicOr(&err_sh, 1);
     }
     if (tid == 0 && pending_slot >= 0) {
         // a copy wait gave up: let that copy land (bounded again) before the buffers go
@@ -374,11 +468,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!err_sh) {
-        // partial accumulator -> shared memory, red[c][row] (row = this thread's TMEM lane)
-        const int row = warp * 32 + lane;
-        for (int c0 = 0; c0 < A.n_chunk; c0 += 16) {
+        // partial accumulator -> shared memory, red[c][row]: warp w reads TMEM lanes
+        // 32 (w % 4) .. +31 (its lane quarter) for the 16-column blocks b = w / 4, w / 4 + 2, ...
+        const int row = (warp & 3) * 32 + lane;
+        for (int c0 = (warp >> 2) * 16; c0 < A.n_chunk; c0 += 32) {
             unsigned v[16];
-            const unsigned taddr = tmem_d + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+            const unsigned taddr = tmem_d + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -386,53 +481,77 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sq_kernel(const __grid_const
                   "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
             for (int t = 0; t < 16; ++t) red[(c0 + t) * kTcM + row] = __uint_as_float(v[t]);
         }
     }
-    if (A.k_split > 1) cluster_sync();
+    const int ks = A.k_split;
+    const bool sets = A.S_total != nullptr;
+    const int grp = sets ? A.cols_per_set : 1;
+    const int ncol = min(A.n_chunk, A.n_cols - c_base);
+    const unsigned my_rank = ks > 1 ? cluster_rank() : 0u;
+    int c_lo, c_hi;
+    tc_owned_cols(ncol, grp, ks, (int)my_rank, &c_lo, &c_hi);
+    const unsigned recv_bytes = ks > 1 ? (unsigned)((ks - 1) * (c_hi - c_lo) * kTcM * sizeof(float)) : 0u;
+    if (tid == 0 && recv_bytes > 0)      // before the barrier, so no pushed byte can come first
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_red)), "r"(recv_bytes) : "memory");
+    if (ks > 1) cluster_sync();
     else __syncthreads();
     // every CTA of the cluster must have a valid partial
-    const unsigned my_rank = A.k_split > 1 ? cluster_rank() : 0u;
     int any_err = 0;
-    for (int r = 0; r < A.k_split; ++r)
-        any_err |= A.k_split > 1 ? ld_cluster_s32(map_rank(smem_u32(&err_sh), (unsigned)r)) : err_sh;
-    if (!any_err) {
-        const int row = warp * 32 + lane;
-        const int q = mt * kTcM + row;
-        const bool sets = A.S_total != nullptr;
-        const int grp = sets ? A.cols_per_set : 1;
-        const unsigned red_addr = smem_u32(red);
-        unsigned base[kTcMaxKSplit];
-#pragma unroll
-        for (int r = 0; r < kTcMaxKSplit; ++r)
-            base[r] = (A.k_split > 1 && r < A.k_split) ? map_rank(red_addr, (unsigned)r) : red_addr;
-        for (int gi = (int)my_rank; gi * grp < A.n_chunk; gi += A.k_split) {
-            const int cg = c_base + gi * grp;
-            if (cg >= A.n_cols) break;
-            double tot = 0.0;
-            for (int t = 0; t < grp; ++t) {
-                const int cl = gi * grp + t, c = cg + t;
-                const unsigned off = (unsigned)((cl * kTcM + row) * sizeof(float));
-                // every CTA's partial of this element in flight at once, summed in rank order
-                float p[kTcMaxKSplit];
-#pragma unroll
-                for (int r = 0; r < kTcMaxKSplit; ++r)
-                    p[r] = r < A.k_split ? (A.k_split > 1 ? ld_cluster_f32(base[r] + off) : red[cl * kTcM + row]) : 0.f;
-                double acc = 0.0;
-#pragma unroll
-                for (int r = 0; r < kTcMaxKSplit; ++r)
-                    if (r < A.k_split) acc += (double)p[r];
-                const float sp = (float)(acc * A.w[c]);
+    for (int r = 0; r < ks; ++r) any_err |= ks > 1 ? ld_cluster_s32(map_rank(smem_u32(&err_sh), (unsigned)r)) : err_sh;
+    if (!any_err && ks > 1 && tid == 0) {
+        // push this CTA's partial of every other CTA's owned columns into that CTA's receive
+        // buffer (slot = this rank), one bulk copy over distributed shared memory each
+        for (int d = 0; d < ks; ++d) {
+            if (d == (int)my_rank) continue;
+            int d_lo, d_hi;
+            tc_owned_cols(ncol, grp, ks, d, &d_lo, &d_hi);
+            if (d_hi <= d_lo) continue;
+            const unsigned bytes = (unsigned)((d_hi - d_lo) * kTcM * sizeof(float));
+            const unsigned src = smem_u32(red) + (unsigned)(d_lo * kTcM * sizeof(float));
+            const unsigned dst = map_rank(smem_u32(recv) + (unsigned)(my_rank * A.recv_cols * kTcM * sizeof(float)), (unsigned)d);
+            const unsigned mb = map_rank(smem_u32(&mbar_red), (unsigned)d);
+            asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                         "r"(src), "r"(bytes), "r"(mb)
+                         : "memory");
+        }
+    }
+    int red_ok = !any_err;
+    if (red_ok && recv_bytes > 0 && !mbar_wait_bounded(smem_u32(&mbar_red), 0u)) {
+        red_ok = 0;
+        atomicOr(A.status, 1);
+    }
+    if (red_ok) {
+        // items (owned column group, row): each sums the k_split partials of its columns in rank
+        // order (FP32, own partial from `red`, the others from `recv`), scales by w_c and, for
+        // sets, adds the set's columns to its flat background
+        const int items = (c_hi - c_lo + grp - 1) / grp * kTcM;
+        for (int it = tid; it < items; it += kTcThreads) {
+            const int gl = it / kTcM, row = it % kTcM;
+            const int q = mt * kTcM + row;
+            const int cl0 = c_lo + gl * grp;
+            float tot = 0.f;
+            for (int t = 0; t < grp && cl0 + t < ncol; ++t) {
+                const int cl = cl0 + t, c = c_base + cl;
+                float acc = 0.f;
+                for (int r = 0; r < ks; ++r)
+                    acc += r == (int)my_rank ? red[cl * kTcM + row]
+                                             : recv[((size_t)r * A.recv_cols + (cl - c_lo)) * kTcM + row];
+                const float sp = acc * w_sh[cl];
                 if (q < A.nQ && A.S_partial) A.S_partial[(size_t)c * A.nQ + q] = sp;
-                tot += (double)sp;
+                tot += sp;
             }
-            if (sets && q < A.nQ) A.S_total[(size_t)(cg / grp) * A.nQ + q] = (float)(A.flat[cg / grp] + tot);
+            if (sets && q < A.nQ) {
+                const int set = (c_base + cl0) / grp;
+                A.S_total[(size_t)set * A.nQ + q] = flat_sh[cl0] + tot;
+            }
         }
     } else if (tid == 0 && err_sh) {
         atomicOr(A.status, 1);
     }
     // no CTA leaves while another may still read its shared memory
-    if (A.k_split > 1) cluster_sync();
+    if (ks > 1) cluster_sync();
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0)
@@ -453,15 +572,23 @@ int tc_pack_a(const float *Kt, int nQ, int n_bins, int m_tiles, int stages, int 
 
 int tc_exec(const TcArgs &a, cudaStream_t stream)
 {
-    const size_t smem = tc_smem_bytes(a.n_chunk, a.ku, a.np_a, a.np_b, a.fmt_bf16);
-    if (smem == 0 || a.n_chunk % 16 || a.n_chunk < 16 || a.n_chunk > 256 || a.k_split < 1 ||
-        a.k_split > kTcMaxKSplit || a.k_split > a.units || (a.units + a.k_split - 1) / a.k_split > kTcMaxUnits)
+    const int np = a.np_a;
+    const int grp = a.S_total ? a.cols_per_set : 1;
+    const size_t smem = tc_smem_need(a.n_chunk, np, a.slots, a.k_split, grp);
+    if (a.np_a != a.np_b || (np != 2 && np != 3) || (!a.fmt_bf16 && np != 2) || a.ku != (a.fmt_bf16 ? 64 : 32) ||
+        smem > kTcSmemMax || a.n_chunk % 16 || a.n_chunk < 16 || a.n_chunk > 256 || a.k_split < 1 ||
+        a.k_split > kTcMaxKSplit || a.k_split > a.units || a.slots < 2 || a.slots > kTcMaxSlots ||
+        (a.k_split > 1 && a.recv_cols < tc_recv_cols(a.n_chunk, grp, a.k_split)) ||
+        (a.S_total && (a.cols_per_set < 1 || a.n_chunk % a.cols_per_set)))
         return set_error(EPSR_EINVAL, "tc sq: tile configuration out of range");
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_sq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    void (*kern)(const TcArgs) = a.fmt_bf16 ? (np == 3 ? tc_sq_kernel<true, 3> : tc_sq_kernel<true, 2>)
+                                            : tc_sq_kernel<false, 2>;
+    static bool attr[3] = {false, false, false};
+    const int ki = a.fmt_bf16 ? (np == 3 ? 2 : 1) : 0;
+    if (!attr[ki]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
         if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(tc_sq)");
-        attr = true;
+        attr[ki] = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)a.m_tiles, (unsigned)((a.n_cols + a.n_chunk - 1) / a.n_chunk), (unsigned)a.k_split);
@@ -475,7 +602,7 @@ int tc_exec(const TcArgs &a, cudaStream_t stream)
     attr_cl[0].val.clusterDim.z = (unsigned)a.k_split;
     cfg.attrs = attr_cl;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, tc_sq_kernel, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
     note_launch();
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? EPSR_OK : set_cuda_error(e, "tc_sq launch");
