@@ -205,7 +205,7 @@ def run_reference(args):
 # Replicas: 64 boxes of uneven size advanced together, each step captured as a CUDA graph
 # ------------------------------------------------------------------------------------------
 
-def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
+def time_sq_modes(Q, g, ws, flats, S_like, nb, stream, flush, reps: int = 20):
     """S(Q) of the same resident g(r) columns in every contraction mode: mean time of one
     epsr_sq_exec (CUDA events on the launching stream, L2 flushed before each, the GPU kept
     busy ahead of the events so that no host latency falls between them) and the largest
@@ -218,10 +218,12 @@ def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
     products = {epsr.SQ_TF32X3: 3, epsr.SQ_BF16X3: 3, epsr.SQ_BF16X6: 6}
     n_q, n_bins, n_cols = len(Q), g.shape[1], g.shape[0]
     out = {}
+    S_fp32 = None
     with torch.cuda.stream(stream):
         for mode, name in names.items():
             plan = epsr.SqPlan(Q, n_bins, 0.02, mode, max_cols=n_cols)
-            S = torch.zeros_like(S_ref)
+            S = torch.zeros_like(S_like)
+            plan.epsr_sq_plan_autotune(g, ws, 3, flats, None, S)
             for _ in range(3):
                 plan.epsr_sq_exec(g, ws, 3, flats, None, S, stream=stream.cuda_stream)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -237,8 +239,10 @@ def time_sq_modes(Q, g, ws, flats, S_ref, nb, stream, flush, reps: int = 20):
             stream.synchronize()
             ms = sum(a.elapsed_time(b) for a, b in evs) / reps
             flops = 2.0 * n_q * n_bins * n_cols
+            if mode == epsr.SQ_FP32:
+                S_fp32 = S.clone()
             rec = {"ms": ms, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
-                   "max_abs_diff_vs_fp32": float((S - S_ref).abs().max())}
+                   "max_abs_diff_vs_fp32": float((S - S_fp32).abs().max())}
             if mode != epsr.SQ_FP32:
                 rec["tiles"] = dict(zip(("cols_per_cta", "k_split"), plan.epsr_sq_plan_get_tiles(n_cols, 3)))
             if mode in products and peaks.get("bf16_tflops"):
@@ -416,12 +420,17 @@ def run_replicas(args):
     systems = synth.replica_batch()
     nb = len(systems)
     box = epsr.Box(systems)
+    tuning = box.epsr_autotune()
     ws = np.concatenate([box.epsr_sq_weights(b)[0] for b in range(nb)])
     flats = np.array([box.epsr_sq_weights(b)[1] for b in range(nb)])
-    plan = epsr.SqPlan(systems[0].Q, 600, 0.02, epsr.SQ_FP32, max_cols=3 * nb)
+    # the batched S(Q): all 3 x 64 columns in one BF16 split-precision tensor-core contraction
+    plan = epsr.SqPlan(systems[0].Q, 600, 0.02, epsr.SQ_BF16X3, max_cols=3 * nb)
     H = torch.zeros(box.hist_len, dtype=torch.int64, device=dev)
     g = torch.zeros(box.hist_len, dtype=torch.float32, device=dev)
     S = torch.zeros((nb, len(systems[0].Q)), dtype=torch.float32, device=dev)
+    box.epsr_partial_gr(H, g, 1)
+    sq_tuning = plan.epsr_sq_plan_autotune(g.view(-1, 600), ws, 3, flats, None, S)
+    H.zero_()
     stream = torch.cuda.Stream()
     moves = args.moves
 
@@ -464,10 +473,12 @@ def run_replicas(args):
             "dtype": "fp32+int64", "data": "synthetic",
             "config": {"workload": f"{nb} replica boxes (log-uniform 2k-60k atoms, half water, half "
                                    f"silica, {sum(n_atoms)} atoms), {moves} moves per box + g(r) + "
-                                   f"S(Q) [2000 x 600] x [600 x {3 * nb}] per step, one CUDA graph per step",
+                                   f"S(Q) [2000 x 600] x [600 x {3 * nb}] in BF16x3 per step, one CUDA graph per step",
                        "l2": "flushed before every step outside the timed events"},
             "pair_distances_per_step": sum(n * (n - 1) // 2 for n in n_atoms),
             "status": status, "clocks": clk.summary(), "gpu_launches": launches,
+            "tuning": {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
+            "sq_step_mode": "bf16x3", "sq_tuning": sq_tuning,
             "sq_modes": sq_modes}
     print(json.dumps(line), flush=True)
     box.close()
@@ -530,6 +541,7 @@ def main():
     moves = args.moves
     stream = torch.cuda.current_stream(dev)
     box = epsr.Box(system)
+    tuning = box.epsr_autotune()          # launch shapes timed on this handle, state restored
     P = 3
     H = torch.zeros(box.hist_len, dtype=torch.int64, device=dev)
     g = torch.zeros(box.hist_len, dtype=torch.float32, device=dev)
@@ -677,6 +689,7 @@ def main():
             "e2e": {"value": ws * moves / (t_e2e * 1e-3), "unit": "moves/s",
                     "h2d_bytes_per_step": N * 3 * 4, "d2h_bytes_per_step": len(system.Q) * 4},
             "gpu_launches": launches,
+            "tuning": {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
         }
         if not args.no_cpu_baseline and ws == 1:
             o = oracle_full_step(system, moves_per_step=moves)

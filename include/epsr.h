@@ -223,6 +223,47 @@ int epsr_mc_set_ctas(epsr_box *box, int32_t ctas);
  * launch. Defaults: 2^20 (1 A), -1. EPSR_EINVAL for margin_fx < 0, margin_fx >= L_fx / 4
  * of a box, or escapee_cap outside [-1, 256]. Host only; takes effect at the next sweep. */
 int epsr_mc_set_cells(epsr_box *box, int32_t margin_fx, int32_t escapee_cap);
+/* Persistent CTAs per SM of the all-pair histogram kernel (1 .. 4; 0 restores the default, 4).
+ * A performance setting: the integer counts do not depend on it. Host only. */
+int epsr_gr_set_ctas_per_sm(epsr_box *box, int32_t ctas_per_sm);
+/* The current launch settings: moves per barrier and CTA budget of the sweep (0 = automatic),
+ * CTAs per SM of the histogram. Any pointer may be NULL. Host only. */
+int epsr_box_get_launch(const epsr_box *box, int32_t *mc_batch, int32_t *mc_ctas, int32_t *gr_ctas_per_sm);
+
+/* ---- autotuner (no counterpart in the paper, whose GPU and MPI versions fix their own
+ * decomposition; here the launch shapes are chosen by timing) ------------------------------
+ * epsr_autotune times, on this handle, the sweep at CTA budgets {SMs, 3/4, 1/2 of the SMs}
+ * x {16, 32, 64} moves per barrier (probe_moves moves each, 0 = 2048, after a warm-up run)
+ * and the all-pair histogram at {2, 3, 4} CTAs per SM, and applies the fastest. The
+ * handle's coordinates, empirical potentials and running statistics are saved to a host
+ * checkpoint before and restored after, so the handle continues from the state it had; every
+ * candidate computes the same chain and the same counts. The choice is cached per shape
+ * (every box's atoms, molecules, types, move kind and bins, and the SM count) for the life of
+ * the process: a later call on a handle of the same shape applies it without timing
+ * (out->from_cache = 1). Synchronises; allocates a scratch histogram while timing.
+ * Errors: those of the calls it makes (a probe sweep that times out returns ETIMEOUT and
+ * leaves the handle's previous settings).
+ *
+ * epsr_sq_plan_autotune times the tensor-core tilings (n_chunk in {16, 32, 64} and, with
+ * S_total, the least multiple of 16 and cols_per_set and its double; k_split in
+ * {1, 2, 4, 8}) of epsr_sq_exec with these arguments (which it writes, three times per
+ * candidate), sets the fastest on the plan (epsr_sq_plan_set_tiles) and caches it per (Q
+ * grid size, bins, mode, columns, set size, totals or not, SM count). Reports the tiling and
+ * its time per call in microseconds (pointers may be NULL). An FP32 plan has nothing to tune
+ * (zeros, EPSR_OK). Synchronises. */
+typedef struct {
+    int32_t mc_batch;        /* moves per grid barrier chosen for the sweep */
+    int32_t mc_ctas;         /* CTA budget of the sweep over the handle */
+    int32_t gr_ctas_per_sm;  /* persistent CTAs per SM of the all-pair histogram */
+    int32_t from_cache;      /* 1: applied from the process's cache, nothing timed */
+    double mc_us_per_move;   /* measured at the chosen setting (per move of every box) */
+    double gr_ms;            /* measured at the chosen setting, one full histogram */
+} epsr_tuning;
+int epsr_autotune(epsr_box *box, uint64_t seed, int32_t probe_moves, epsr_tuning *out, epsr_stream_t stream);
+int epsr_sq_plan_autotune(epsr_sq_plan *plan, const float *g, int32_t n_cols, const double *w,
+                          int32_t cols_per_set, const double *flat, float *S_partial, float *S_total,
+                          int32_t *n_chunk, int32_t *k_split, double *us, epsr_stream_t stream);
+
 /* Test hook: CTA `cta` of the following sweeps skips its barrier arrival and every
  * barrier wait is limited to timeout_ms, so the bounded wait expires and the sweep
  * returns EPSR_ETIMEOUT with the GPU context intact. cta = -1 restores normal operation

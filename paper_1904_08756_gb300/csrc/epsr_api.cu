@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "epsr.h"
@@ -118,6 +119,7 @@ struct epsr_box {
     int cell_margin = 1 << 20;                // 1 A on the 2^20 grid
     int esc_cap = -1;                         // -1: the kernel's maximum
     int mc_ctas = 0;
+    int gr_ctas_per_sm = 4;                   // persistent CTAs per SM of the all-pairs histogram
     int fault_cta = -1;
     double timeout_ms = 2000.0;
     // device
@@ -748,6 +750,42 @@ extern "C" int epsr_mc_set_batch(epsr_box *box, int32_t batch_k)
     return EPSR_OK;
 }
 
+extern "C" int epsr_gr_set_ctas_per_sm(epsr_box *box, int32_t ctas_per_sm)
+{
+    if (!box || ctas_per_sm < 0 || ctas_per_sm > 4)
+        return set_error(EPSR_EINVAL, "gr: CTAs per SM %d outside [0, 4]", ctas_per_sm);
+    box->gr_ctas_per_sm = ctas_per_sm == 0 ? 4 : ctas_per_sm;
+    return EPSR_OK;
+}
+
+extern "C" int epsr_box_get_launch(const epsr_box *box, int32_t *mc_batch, int32_t *mc_ctas,
+                                   int32_t *gr_ctas_per_sm)
+{
+    if (!box) return set_error(EPSR_EINVAL, "NULL argument");
+    if (mc_batch) *mc_batch = box->mc_batch;
+    if (mc_ctas) *mc_ctas = box->mc_ctas;
+    if (gr_ctas_per_sm) *gr_ctas_per_sm = box->gr_ctas_per_sm;
+    return EPSR_OK;
+}
+
+namespace epsr {
+// The shape a tuning applies to: every box's atoms, types, move kind and bins, and the SM count.
+std::string box_shape_key(const epsr_box *box)
+{
+    std::string k = "box:" + std::to_string(box->sms);
+    for (int b = 0; b < box->n_boxes; ++b) {
+        const epsr_box_desc &d = box->desc[b];
+        k += "|" + std::to_string(d.n_atoms) + "," + std::to_string(d.n_mol) + "," + std::to_string(d.n_types) +
+             "," + std::to_string(d.move_kind) + "," + std::to_string(d.n_bins);
+    }
+    return k;
+}
+
+int box_sms(const epsr_box *box) { return box->sms; }
+
+std::string sq_plan_key(const epsr_sq_plan *p, int n_cols, int cols_per_set, bool totals);
+}  // namespace epsr
+
 extern "C" int epsr_mc_set_cells(epsr_box *box, int32_t margin_fx, int32_t escapee_cap)
 {
     if (!box) return set_error(EPSR_EINVAL, "NULL argument");
@@ -919,7 +957,7 @@ static int gr_range(epsr_box *box, long long t0, long long t1, uint64_t *hist, c
     a.hist = (unsigned long long *)hist;
     a.max_pairs_bins = box->ep_cap;
     a.max_bins1 = box->tbl_cap;
-    const int grid = (int)std::min<long long>(t1 - t0, (long long)box->sms * 4);   // 4 CTAs per SM
+    const int grid = (int)std::min<long long>(t1 - t0, (long long)box->sms * box->gr_ctas_per_sm);
     return launch_partial_gr(a, std::max(grid, 1), s);
 }
 
@@ -1075,6 +1113,17 @@ static int tc_choose_tiles(const epsr_sq_plan *p, int n_cols, int cps, bool want
     *k_split = ks;
     return EPSR_OK;
 }
+
+namespace epsr {
+std::string sq_plan_key(const epsr_sq_plan *p, int n_cols, int cols_per_set, bool totals)
+{
+    return "sq:" + std::to_string(p->sms) + "|" + std::to_string(p->nQ) + "," + std::to_string(p->n_bins) + "," +
+           std::to_string(p->mode) + "," + std::to_string(n_cols) + "," + std::to_string(cols_per_set) + "," +
+           std::to_string((int)totals);
+}
+int sq_plan_mode(const epsr_sq_plan *p) { return p->mode; }
+int sq_plan_stages(const epsr_sq_plan *p) { return p->stages; }
+}  // namespace epsr
 
 extern "C" int epsr_sq_plan_set_tiles(epsr_sq_plan *plan, int32_t n_chunk, int32_t k_split)
 {

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "epsr.h"
 
 namespace epsr {
@@ -18,6 +20,13 @@ int set_cuda_error(cudaError_t e, const char *what);
 
 // ---- launch accounting (epsr_launch_count): called once after every kernel enqueue ----------
 void note_launch();
+
+// ---- autotuner support (epsr_tune.cu): the shape a tuning is cached under --------------------
+std::string box_shape_key(const epsr_box *box);
+int box_sms(const epsr_box *box);
+std::string sq_plan_key(const epsr_sq_plan *p, int n_cols, int cols_per_set, bool totals);
+int sq_plan_mode(const epsr_sq_plan *p);
+int sq_plan_stages(const epsr_sq_plan *p);
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------
 constexpr size_t kMcMaxDynSmem = 176 * 1024;   // with about 44 KB of static shared memory, under the 227 KB per CTA

@@ -38,7 +38,6 @@ namespace {
 constexpr int kTcThreads = 256;     // 8 warps: warps w and w + 4 share TMEM lane quarter w
 constexpr int kTcM = 128;
 constexpr unsigned long long kTcSpinLimit = 1ull << 26;
-constexpr int kTcMaxUnits = 64;     // K units of one CTA's range (n_bins <= 4096 at 64 per unit)
 constexpr size_t kTcSmemMax = 220 * 1024;        // dynamic shared memory of one CTA, at most
 constexpr size_t kTcSmemTwoPerSm = 110 * 1024;   // budget that leaves room for two CTAs per SM
 

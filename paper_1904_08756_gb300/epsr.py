@@ -37,7 +37,8 @@ EXPORTS = [
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
     "epsr_mc_set_cells", "epsr_sq_plan_status", "epsr_partial_gr_cells",
     "epsr_bench_barrier_floor", "epsr_bench_alu_rate", "epsr_sq_plan_set_tiles",
-    "epsr_sq_plan_get_tiles",
+    "epsr_sq_plan_get_tiles", "epsr_gr_set_ctas_per_sm", "epsr_box_get_launch", "epsr_autotune",
+    "epsr_sq_plan_autotune",
 ]
 
 
@@ -51,6 +52,11 @@ class BoxDesc(C.Structure):
                 ("max_translation", C.c_double), ("max_rotation_deg", C.c_double),
                 ("bond_k", C.c_double * (MAX_TYPES * MAX_TYPES)),
                 ("bond_d", C.c_double * (MAX_TYPES * MAX_TYPES))]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("mc_batch", C.c_int32), ("mc_ctas", C.c_int32), ("gr_ctas_per_sm", C.c_int32),
+                ("from_cache", C.c_int32), ("mc_us_per_move", C.c_double), ("gr_ms", C.c_double)]
 
 
 class McStats(C.Structure):
@@ -131,6 +137,11 @@ def lib():
             "epsr_chi2": ([vp, vp, vp, vp, i32, vp, i32, dbl, dbl, vp, vp, vp, vp], C.c_int),
             "epsr_partial_gr_noalloc": ([vp, vp, i64, i64, i32, i32, i32, i32, i32, vp, vp], C.c_int),
             "epsr_sq_plan_set_tiles": ([vp, i32, i32], C.c_int),
+            "epsr_gr_set_ctas_per_sm": ([vp, i32], C.c_int),
+            "epsr_box_get_launch": ([vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)], C.c_int),
+            "epsr_autotune": ([vp, C.c_uint64, i32, P(Tuning), vp], C.c_int),
+            "epsr_sq_plan_autotune": ([vp, vp, i32, vp, i32, vp, vp, vp, P(C.c_int32), P(C.c_int32),
+                                       P(C.c_double), vp], C.c_int),
             "epsr_sq_plan_get_tiles": ([vp, i32, i32, i32, P(C.c_int32), P(C.c_int32)], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -356,6 +367,21 @@ class Box:
     def epsr_mc_set_ctas(self, n: int):
         _check(lib().epsr_mc_set_ctas(self.h, n), "epsr_mc_set_ctas")
 
+    def epsr_gr_set_ctas_per_sm(self, n: int):
+        _check(lib().epsr_gr_set_ctas_per_sm(self.h, n), "epsr_gr_set_ctas_per_sm")
+
+    def epsr_box_get_launch(self):
+        b, c, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().epsr_box_get_launch(self.h, C.byref(b), C.byref(c), C.byref(g)), "epsr_box_get_launch")
+        return {"mc_batch": b.value, "mc_ctas": c.value, "gr_ctas_per_sm": g.value}
+
+    def epsr_autotune(self, seed: int = 12345, probe_moves: int = 0, stream=None) -> dict:
+        """Times the sweep and histogram launch shapes on this handle and applies the fastest
+        (state saved and restored around the probes); returns the chosen settings."""
+        t = Tuning()
+        _check(lib().epsr_autotune(self.h, seed, probe_moves, C.byref(t), _stream(stream)), "epsr_autotune")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
     def epsr_debug_barrier_fault(self, cta: int, timeout_ms: float):
         _check(lib().epsr_debug_barrier_fault(self.h, cta, timeout_ms), "epsr_debug_barrier_fault")
 
@@ -453,6 +479,18 @@ class SqPlan:
 
     def epsr_sq_plan_set_tiles(self, n_chunk: int, k_split: int):
         _check(lib().epsr_sq_plan_set_tiles(self.h, n_chunk, k_split), "epsr_sq_plan_set_tiles")
+
+    def epsr_sq_plan_autotune(self, g, w: np.ndarray, cols_per_set: int, flat: np.ndarray,
+                              S_partial=None, S_total=None, stream=None) -> dict:
+        """Times the tensor-core tilings of this exec and sets the fastest on the plan."""
+        w = np.ascontiguousarray(w, np.float64)
+        flat = np.ascontiguousarray(np.atleast_1d(flat), np.float64)
+        nc, ks, us = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib().epsr_sq_plan_autotune(self.h, _dev_ptr(g), g.shape[0], _np_ptr(w), cols_per_set,
+                                           _np_ptr(flat), _dev_ptr(S_partial), _dev_ptr(S_total),
+                                           C.byref(nc), C.byref(ks), C.byref(us), _stream(stream)),
+               "epsr_sq_plan_autotune")
+        return {"cols_per_cta": nc.value, "k_split": ks.value, "us": us.value}
 
     def epsr_sq_plan_get_tiles(self, n_cols: int, cols_per_set: int, with_totals: bool = True):
         nc, ks = C.c_int32(), C.c_int32()

@@ -388,6 +388,41 @@ def test_replicas_64_boxes_graph_step_against_oracle():
     assert err <= 1e-4
 
 
+def test_autotune_keeps_state_and_results():
+    """The autotuner times launch shapes on the handle itself and restores its state: the
+    coordinates and running statistics are unchanged by tuning, the chain run with the tuned
+    settings replays against the oracle, the tuned histogram equals the oracle's bit for bit,
+    and a second handle of the same shape takes the cached choice without timing."""
+    systems = [synth.water_box(700, seed=91), synth.silica_box(600, seed=92),
+               synth.water_box(1500, seed=93)]
+    box = epsr.Box(systems)
+    box.epsr_mc_sweep(300, seed=40)
+    xyz0 = box.epsr_box_get_coords()
+    st0 = box.epsr_mc_stats_get()
+    t = box.epsr_autotune(probe_moves=512)
+    print("tuning:", t)
+    assert t["from_cache"] == 0 and t["mc_batch"] in (16, 32, 64) and t["gr_ctas_per_sm"] in (2, 3, 4)
+    assert box.epsr_box_get_launch() == {"mc_batch": t["mc_batch"], "mc_ctas": t["mc_ctas"],
+                                         "gr_ctas_per_sm": t["gr_ctas_per_sm"]}
+    assert np.array_equal(box.epsr_box_get_coords(), xyz0)
+    assert box.epsr_mc_stats_get() == st0
+    stats, log = run_logged(box, 1000, seed=41, move0=300)
+    xyz = box.epsr_box_get_coords()
+    Hg = gpu_hist(box)
+    for b, s in enumerate(systems):
+        h0, a0 = box.epsr_box_offsets(b)
+        ob, checked, _, flips = replay(s, xyz0[a0:a0 + s.n_atoms], log[b], 41, move0=300, box_index=b,
+                                       check_every=2)
+        assert flips <= 2
+        assert np.array_equal(xyz[a0:a0 + s.n_atoms], ob.xyz), b
+        ref = ob.histogram()
+        assert np.array_equal(Hg[h0:h0 + ref.size].reshape(ref.shape), ref), b
+    second = epsr.Box(systems)
+    t2 = second.epsr_autotune()
+    assert t2["from_cache"] == 1
+    assert (t2["mc_batch"], t2["mc_ctas"], t2["gr_ctas_per_sm"]) == (t["mc_batch"], t["mc_ctas"], t["gr_ctas_per_sm"])
+
+
 def test_mc_energy_drift(small_water):
     box = epsr.Box(small_water)
     U0 = box.epsr_box_total_energy()[0]
@@ -725,6 +760,29 @@ def test_sq_tensor_core_tilings_against_oracle(mode):
         plan.epsr_sq_plan_set_tiles(40, 1)          # not a multiple of 16
     with pytest.raises(epsr.EpsrError):
         plan.epsr_sq_plan_set_tiles(48, 9)          # more than one portable cluster
+
+
+def test_sq_autotune_picks_a_tiling_that_matches_the_oracle():
+    n_bins, dr, n_cols = 600, 0.02, 192
+    Q = 0.3 + np.arange(2000) * (39.7 / 1999)
+    g = _synthetic_g(n_cols, n_bins, dr, seed=7)
+    rng = np.random.default_rng(8)
+    w = rng.uniform(0.05, 0.4, n_cols)
+    flat = rng.uniform(0.2, 0.6, n_cols // 3)
+    _, St_ref = oracle.sq(g.astype(np.float64), dr, Q.astype(np.float32).astype(np.float64), w, 3, flat)
+    plan = epsr.SqPlan(Q, n_bins, dr, epsr.SQ_BF16X3, max_cols=n_cols)
+    gd = torch.from_numpy(g).to(DEV)
+    St = torch.zeros((n_cols // 3, 2000), dtype=torch.float32, device=DEV)
+    r = plan.epsr_sq_plan_autotune(gd, w, 3, flat, None, St)
+    print("sq tuning:", r)
+    assert r["cols_per_cta"] in (16, 32, 48, 64, 96) and r["k_split"] in (1, 2, 4, 8) and r["us"] > 0
+    assert plan.epsr_sq_plan_get_tiles(n_cols, 3) == (r["cols_per_cta"], r["k_split"])
+    St.zero_()
+    plan.epsr_sq_exec(gd, w, 3, flat, None, St)
+    torch.cuda.synchronize()
+    assert np.abs(St.cpu().numpy() - St_ref).max() <= 1e-4
+    plan2 = epsr.SqPlan(Q, n_bins, dr, epsr.SQ_BF16X3, max_cols=n_cols)
+    assert plan2.epsr_sq_plan_autotune(gd, w, 3, flat, None, St)["cols_per_cta"] == r["cols_per_cta"]
 
 
 def test_checkpoint_resume_is_bit_exact():
