@@ -379,6 +379,55 @@ int epsr_ep_update(epsr_box *box, int32_t b, const float *dS, int32_t n_data, co
                    const float *Q, int32_t nQ, int32_t n_basis, double s_basis, double gamma,
                    double alpha, double *C_out, epsr_stream_t stream);
 
+/* ---- the refinement loop (Sec. 2.2 items III-VI; Sec. 2.1; Eq. 2) ------------------------
+ * A refiner drives the loop of the method on a one-box handle: each epsr_refine_step runs
+ *   III  moves_per_pass Metropolis moves (epsr_mc_sweep; moves continue from move0 on),
+ *   VI   the pair histograms, accumulated over the passes (accumulate = 1, Sec. 2.2 item VI)
+ *        or of this configuration alone (0), and g_ab(r),
+ *   IV   S_d(Q) of every dataset d by Eq. (1): flat_d + sum_p 4 pi rho w[d][p] sum_k K (g_p - 1),
+ *        then Delta S_d = target_d - S_d and chi^2 = sum_d sum_Q Delta S_d^2,
+ *   V    epsr_ep_update(Delta S, w, n_basis, s_basis, gamma, alpha): the Poisson fit of the
+ *        pair-resolved Delta S added to the empirical potential.
+ * The loop is repeated by the caller until ep_change_max (the largest change the pass made to
+ * the table, kJ/mol) or chi^2 is small enough (Sec. 2.1).
+ *   plan    an S(Q) plan on the datasets' Q grid (nQ points, the box's bins, at least
+ *           n_data * n_pairs columns), any mode
+ *   target  device float [n_data][nQ], the measured S(Q) (barn/sr/atom); caller-owned, read at
+ *           every step
+ *   w       host double [n_data][n_pairs], Eq. (1) weights (2 - delta) c_a c_b b_a b_b of each
+ *           dataset (barn), copied; flat host double [n_data], sum_a c_a b_a^2; Q host float [nQ]
+ *   n_data  1 .. 16; fewer datasets than pairs need gamma > 0
+ * epsr_refiner_get copies the accumulated histogram (device uint64 [n_pairs][n_bins]), g, S and
+ * Delta S of the last step (device float) and its fitted coefficients (host double
+ * [n_pairs][n_basis]); any pointer may be NULL. Steps synchronise; create and destroy
+ * allocate and free the refiner's device buffers. */
+typedef struct epsr_refiner epsr_refiner;
+typedef struct {
+    int64_t moves_per_pass;   /* Metropolis moves per step (0: no moves) */
+    uint64_t seed;            /* Philox key of the moves */
+    uint64_t move0;           /* index of the first move of the first step */
+    int32_t accumulate;       /* 1: histograms accumulate over steps; 0: each step alone */
+    int32_t n_basis;          /* Poisson functions per pair, 1 .. 40 */
+    double s_basis;           /* Poisson width s (A) */
+    double gamma;             /* pair-resolution regulariser */
+    double alpha;             /* feedback factor of the update */
+} epsr_refine_params;
+typedef struct {
+    int64_t iteration;        /* steps done */
+    int64_t attempted, accepted;  /* running Monte Carlo totals of the box */
+    int64_t n_configs;        /* configurations in the histogram */
+    uint64_t next_move;       /* move index the next step starts at */
+    double chi2;              /* sum over datasets and Q of Delta S^2 before this step's update */
+    double ep_change_max;     /* largest |change| of the empirical-potential table (kJ/mol) */
+} epsr_refine_result;
+int epsr_refiner_create(epsr_box *box, epsr_sq_plan *plan, const float *target, int32_t n_data,
+                        const double *w, const double *flat, const float *Q, int32_t nQ,
+                        const epsr_refine_params *params, epsr_stream_t stream, epsr_refiner **out);
+int epsr_refine_step(epsr_refiner *r, epsr_move_log *log, epsr_refine_result *res, epsr_stream_t stream);
+int epsr_refiner_get(const epsr_refiner *r, uint64_t *hist, float *g, float *S, float *dS, double *C,
+                     epsr_stream_t stream);
+int epsr_refiner_destroy(epsr_refiner *r);
+
 /* ---- pair histogram without device allocation -----------------------------------------
  * The paper has no counterpart: this entry point exists for callers that must not
  * allocate device memory when they need the counts -- plug-ins whose host framework's

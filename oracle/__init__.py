@@ -188,6 +188,11 @@ class Box:
         lib().orc_mc_sweep(self.ref(), n_moves, seed, move0, box_index, C.byref(st))
         return st.attempted, st.accepted, st.sum_dU
 
+    def set_ep(self, ep):
+        """Replaces the empirical-potential table (FP64 [n_pairs][n_bins], or None for zero)."""
+        self.ep = None if ep is None else np.ascontiguousarray(ep, np.float64)
+        self.st.ep = _ptr(self.ep, C.c_double) if self.ep is not None else C.POINTER(C.c_double)()
+
     # --- histograms and g(r) --------------------------------------------------------
     def histogram(self, i0: int = 0, i1: int | None = None, threads: int = 1) -> np.ndarray:
         H = np.zeros((self.n_pairs, self.sys.n_bins), np.uint64)
@@ -422,3 +427,45 @@ def chi2_and_grads(box: Box, sigma: float, Q: np.ndarray, target: np.ndarray,
     else:
         gx = box.smeared_grad(sigma, lam, grad_atoms)
     return chi2, dC, gx, S_t, lam
+
+
+# ------------------------------------------------------------------------------------
+# The refinement loop (Sec. 2.2 items III-VI; Sec. 2.1; Eq. 2)
+# ------------------------------------------------------------------------------------
+
+def refine_pass(ob: Box, target: np.ndarray, w: np.ndarray, flat: np.ndarray, Q: np.ndarray,
+                n_basis: int, s_basis: float, gamma: float, alpha: float,
+                H_acc: np.ndarray | None = None, n_cfg: int = 0,
+                moves: int = 0, seed: int = 0, move0: int = 0):
+    """One pass of the loop, in the paper's order:
+      III  `moves` Metropolis moves of the oracle's chain (none when the caller has already
+           moved the box, e.g. by replaying another implementation's decisions);
+      VI   the pair histogram of this configuration added to H_acc (n_cfg configurations so
+           far; H_acc None starts afresh) and g_ab from the accumulated counts;
+      IV   S_d(Q) of every dataset d by Eq. (1) with the dataset's weights w[d] (barn,
+           without 4 pi rho) and background flat[d]; Delta S_d = target_d - S_d, chi^2;
+      V    the pair-resolved Delta S_p (pseudo-inverse of the weights, reading c16), its
+           least-squares Poisson coefficients C (Sec. 2.1) and the table update
+           -alpha kT sum_n C_pn p_n(r_k) (reading c13) added to the box's EP table.
+    Returns a dict with H, n_cfg, g, S, dS, chi2, C and the new table."""
+    s = ob.sys
+    if moves:
+        ob.mc_sweep(moves, seed, move0)
+    H = ob.histogram()
+    H = H if H_acc is None else H_acc + H
+    n_cfg = 1 if H_acc is None else n_cfg + 1
+    g = ob.normalize_g(H, n_cfg)
+    w = np.asarray(w, np.float64)
+    n_data, P = w.shape
+    rho = number_density(s)
+    _, S = sq(np.tile(g, (n_data, 1)), s.dr, Q, (4.0 * math.pi * rho * w).ravel(), P,
+              np.asarray(flat, np.float64))
+    dS = np.asarray(target, np.float64) - S
+    chi2 = float((dS * dS).sum())
+    dSp = pair_resolve(dS, w, gamma)
+    C_ = ep_fit(dSp, ep_basis_matrix(n_basis, s_basis, Q, rho))
+    kT = gas_constant() * s.temperature
+    table = ep_table(C_, s_basis, s.n_bins, s.dr, alpha, kT)
+    ep = table if ob.ep is None else ob.ep + table
+    ob.set_ep(ep)
+    return {"H": H, "n_cfg": n_cfg, "g": g, "S": S, "dS": dS, "chi2": chi2, "C": C_, "ep": ep}

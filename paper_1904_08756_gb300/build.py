@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libepsr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["epsr_api.cu", "k_mc.cu", "k_gr.cu", "k_sq.cu", "k_sq_tc.cu", "k_ep.cu", "k_smear.cu", "epsr_noalloc.cu", "k_micro.cu", "epsr_tune.cu"]
+SOURCES = ["epsr_api.cu", "k_mc.cu", "k_gr.cu", "k_sq.cu", "k_sq_tc.cu", "k_ep.cu", "k_smear.cu", "epsr_noalloc.cu", "k_micro.cu", "epsr_tune.cu", "epsr_refine.cu"]
 # The Monte Carlo kernel's FP32 energies never come near the denormal range (|r| >= grid
 # spacing, r <= box diagonal), so denormal support is dropped there (single-instruction rsqrt).
 PER_FILE_FLAGS = {"k_mc.cu": ["-ftz=true"]}

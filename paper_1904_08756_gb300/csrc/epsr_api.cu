@@ -783,6 +783,19 @@ std::string box_shape_key(const epsr_box *box)
 
 int box_sms(const epsr_box *box) { return box->sms; }
 
+int box_summary(const epsr_box *box, int b, BoxSummary *out)
+{
+    if (!box || !out || b < 0 || b >= box->n_boxes) return set_error(EPSR_EINVAL, "bad box index");
+    const BoxDev &bx = box->hb[b];
+    out->n_boxes = box->n_boxes;
+    out->n_pairs = bx.n_pairs;
+    out->n_bins = bx.n_bins;
+    out->kT = bx.kT;
+    out->rho = (double)bx.n_atoms / bx.volume;
+    out->dr = bx.dr_A;
+    return EPSR_OK;
+}
+
 std::string sq_plan_key(const epsr_sq_plan *p, int n_cols, int cols_per_set, bool totals);
 }  // namespace epsr
 
@@ -1122,6 +1135,12 @@ std::string sq_plan_key(const epsr_sq_plan *p, int n_cols, int cols_per_set, boo
            std::to_string((int)totals);
 }
 int sq_plan_mode(const epsr_sq_plan *p) { return p->mode; }
+void sq_plan_dims(const epsr_sq_plan *p, int *nQ, int *n_bins, int *max_cols)
+{
+    *nQ = p->nQ;
+    *n_bins = p->n_bins;
+    *max_cols = p->max_cols;
+}
 int sq_plan_stages(const epsr_sq_plan *p) { return p->stages; }
 }  // namespace epsr
 

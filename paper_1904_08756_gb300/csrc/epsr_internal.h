@@ -23,9 +23,15 @@ void note_launch();
 
 // ---- autotuner support (epsr_tune.cu): the shape a tuning is cached under --------------------
 std::string box_shape_key(const epsr_box *box);
+struct BoxSummary {
+    int n_boxes, n_pairs, n_bins;
+    double kT, rho, dr;     // kJ/mol, atoms per A^3, A
+};
+int box_summary(const epsr_box *box, int b, BoxSummary *out);
 int box_sms(const epsr_box *box);
 std::string sq_plan_key(const epsr_sq_plan *p, int n_cols, int cols_per_set, bool totals);
 int sq_plan_mode(const epsr_sq_plan *p);
+void sq_plan_dims(const epsr_sq_plan *p, int *nQ, int *n_bins, int *max_cols);
 int sq_plan_stages(const epsr_sq_plan *p);
 
 // ---- Monte Carlo kernel ----------------------------------------------------------------------

@@ -38,7 +38,8 @@ EXPORTS = [
     "epsr_mc_set_cells", "epsr_sq_plan_status", "epsr_partial_gr_cells",
     "epsr_bench_barrier_floor", "epsr_bench_alu_rate", "epsr_sq_plan_set_tiles",
     "epsr_sq_plan_get_tiles", "epsr_gr_set_ctas_per_sm", "epsr_box_get_launch", "epsr_autotune",
-    "epsr_sq_plan_autotune",
+    "epsr_sq_plan_autotune", "epsr_refiner_create", "epsr_refine_step", "epsr_refiner_get",
+    "epsr_refiner_destroy",
 ]
 
 
@@ -57,6 +58,18 @@ class BoxDesc(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("mc_batch", C.c_int32), ("mc_ctas", C.c_int32), ("gr_ctas_per_sm", C.c_int32),
                 ("from_cache", C.c_int32), ("mc_us_per_move", C.c_double), ("gr_ms", C.c_double)]
+
+
+class RefineParams(C.Structure):
+    _fields_ = [("moves_per_pass", C.c_int64), ("seed", C.c_uint64), ("move0", C.c_uint64),
+                ("accumulate", C.c_int32), ("n_basis", C.c_int32), ("s_basis", C.c_double),
+                ("gamma", C.c_double), ("alpha", C.c_double)]
+
+
+class RefineResult(C.Structure):
+    _fields_ = [("iteration", C.c_int64), ("attempted", C.c_int64), ("accepted", C.c_int64),
+                ("n_configs", C.c_int64), ("next_move", C.c_uint64), ("chi2", C.c_double),
+                ("ep_change_max", C.c_double)]
 
 
 class McStats(C.Structure):
@@ -138,6 +151,10 @@ def lib():
             "epsr_partial_gr_noalloc": ([vp, vp, i64, i64, i32, i32, i32, i32, i32, vp, vp], C.c_int),
             "epsr_sq_plan_set_tiles": ([vp, i32, i32], C.c_int),
             "epsr_gr_set_ctas_per_sm": ([vp, i32], C.c_int),
+            "epsr_refiner_create": ([vp, vp, vp, i32, vp, vp, vp, i32, P(RefineParams), vp, P(vp)], C.c_int),
+            "epsr_refine_step": ([vp, vp, P(RefineResult), vp], C.c_int),
+            "epsr_refiner_get": ([vp, vp, vp, vp, vp, vp, vp], C.c_int),
+            "epsr_refiner_destroy": ([vp], C.c_int),
             "epsr_box_get_launch": ([vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)], C.c_int),
             "epsr_autotune": ([vp, C.c_uint64, i32, P(Tuning), vp], C.c_int),
             "epsr_sq_plan_autotune": ([vp, vp, i32, vp, i32, vp, vp, vp, P(C.c_int32), P(C.c_int32),
@@ -596,3 +613,52 @@ def epsr_partial_gr_noalloc(system, hist, stream=None):
     _check(lib().epsr_partial_gr_noalloc(_np_ptr(xyz), _np_ptr(typ), xyz.shape[0], system.L_fx, 20,
                                          system.n_types, system.bin_p, system.bin_q, system.n_bins,
                                          hp, _stream(stream)), "epsr_partial_gr_noalloc")
+
+
+class Refiner:
+    """Owner of an epsr_refiner: the refinement loop (Sec. 2.2 items III-VI) on a one-box
+    handle against measured S(Q) of n_data datasets (target device float [n_data][nQ])."""
+
+    def __init__(self, box: Box, plan: SqPlan, target, w: np.ndarray, flat: np.ndarray, Q: np.ndarray,
+                 moves_per_pass: int, seed: int = 1, move0: int = 0, accumulate: bool = False,
+                 n_basis: int = 20, s_basis: float = 0.5, gamma: float = 0.0, alpha: float = 1.0,
+                 stream=None):
+        self.w = np.ascontiguousarray(np.atleast_2d(w), np.float64)
+        self.flat = np.ascontiguousarray(np.atleast_1d(flat), np.float64)
+        q = np.ascontiguousarray(Q, np.float32)
+        self.n_data = self.w.shape[0]
+        if target.numel() < self.n_data * len(q):
+            raise ValueError("target: n_data x nQ elements needed")
+        self.target, self.box, self.plan = target, box, plan
+        self.n_basis = n_basis
+        p = RefineParams(moves_per_pass, seed, move0, int(accumulate), n_basis, s_basis, gamma, alpha)
+        h = C.c_void_p()
+        _check(lib().epsr_refiner_create(box.h, plan.h, _dev_ptr(target), self.n_data, _np_ptr(self.w),
+                                         _np_ptr(self.flat), _np_ptr(q), len(q), C.byref(p), _stream(stream),
+                                         C.byref(h)), "epsr_refiner_create")
+        self.h = h
+
+    def step(self, log=None, stream=None) -> dict:
+        r = RefineResult()
+        _check(lib().epsr_refine_step(self.h, _dev_ptr(log), C.byref(r), _stream(stream)), "epsr_refine_step")
+        return {f: getattr(r, f) for f, _ in RefineResult._fields_}
+
+    def get(self, hist=None, g=None, S=None, dS=None, stream=None):
+        """Copies the accumulated histogram, g, and S and Delta S of the last step into the given
+        device tensors; returns the last fitted coefficients [n_pairs][n_basis]."""
+        P = self.w.shape[1]
+        Cb = np.zeros((P, self.n_basis), np.float64)
+        _check(lib().epsr_refiner_get(self.h, _dev_ptr(hist), _dev_ptr(g), _dev_ptr(S), _dev_ptr(dS),
+                                      _np_ptr(Cb), _stream(stream)), "epsr_refiner_get")
+        return Cb
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().epsr_refiner_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -356,6 +356,27 @@ def uniform_gas(n_atoms: int, L_A: float, seed: int, n_types: int = 2) -> System
                   Q=0.5 + np.arange(200) * 0.1, seed=seed)
 
 
+def lj_fluid(n_side: int, seed: int, density: float = 0.021, sigma: float = 3.4, eps: float = 1.0,
+             temperature: float = 120.0, max_translation: float = 0.3, n_bins: int = 333) -> System:
+    """A one-type Lennard-Jones liquid (argon-like by default): n_side^3 atoms on a simple cubic
+    lattice of the given density, each displaced uniformly by up to 1/4 of the spacing, no
+    charges; single-atom moves; 0.03 A bins and Q on 0.3-20 1/A. The refinement loop's test
+    system: it equilibrates in a few sweeps, and one pair means one dataset fixes it."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = n_side ** 3
+    L_fx = box_side_fx(n, density)
+    a = L_fx / n_side
+    g = np.stack(np.meshgrid(np.arange(n_side), np.arange(n_side), np.arange(n_side), indexing="ij"),
+                 axis=-1).reshape(-1, 3).astype(np.float64)
+    jit = rng.uniform(-0.25, 0.25, size=(n, 3))
+    xyz = (np.floor((g + 0.5 + jit) * a).astype(np.int64) % L_fx).astype(np.int32)
+    return System(name="lj-fluid", L_fx=L_fx, xyz=xyz, type=np.zeros(n, np.int32),
+                  mol_start=np.arange(0, n + 1, dtype=np.int64), type_names=["Ar"], q=[0.0],
+                  sigma=[sigma], eps=[eps], b=[1.909], r_coul=9.0, bin_p=3, bin_q=100, n_bins=n_bins,
+                  temperature=temperature, rigid_molecules=False, max_translation=max_translation,
+                  max_rotation_deg=0.0, Q=0.3 + np.arange(400) * (19.7 / 399.0), seed=seed)
+
+
 # ----------------------------------------------------------------------------------------
 # Named workloads (the paper-shaped test systems)
 # ----------------------------------------------------------------------------------------
