@@ -630,6 +630,20 @@ def main():
     t_gc = sum(a_ev.elapsed_time(b_ev) for a_ev, b_ev in gc_ev) / len(gc_ev)
     in_range = int(Hc.sum().item())
 
+    # ---- the cutoff form of dU (LJ truncated at 9 A, partners by cell queries), beside --------
+    cut_sys = synth.System(**{**system.__dict__, "r_lj": 9.0})
+    cbox = epsr.Box(cut_sys)
+    cbox.epsr_mc_sweep(moves, 77, 0)
+    c_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for k, (a_ev, b_ev) in enumerate(c_ev):
+        flush.fill_(4.0)
+        a_ev.record(stream)
+        cbox.epsr_mc_sweep(moves, 77, moves * (k + 1))
+        b_ev.record(stream)
+    torch.cuda.synchronize()
+    t_cut = sum(a_ev.elapsed_time(b_ev) for a_ev, b_ev in c_ev) / len(c_ev)
+    cbox.close()
+
     # ---- bounds of the sweep measured on this GPU: grid-barrier floor, issue rates ------------
     sms_dev = torch.cuda.get_device_properties(dev).multi_processor_count
     barrier_ns = epsr.epsr_bench_barrier_floor(sms_dev, 4000)
@@ -680,6 +694,10 @@ def main():
                 "note": "epsr_bench_barrier_floor (152 CTAs, the sweep's exchange alone) and "
                         "epsr_bench_alu_rate (independent xor+add / FMA chains); the roofline peak stays "
                         "the unit-count figure"},
+            "mc_lj_cutoff": {"r_lj_A": 9.0, "ms_per_sweep": t_cut, "moves_per_s": moves / (t_cut * 1e-3),
+                             "speedup_vs_all_pairs": t_mc / t_cut,
+                             "note": "dU with Lennard-Jones truncated at 9 A (epsr_box_desc.r_lj), every "
+                                     "partner row by cell queries; not the paper's all-pairs dU, not in the step"},
             "gr_cell_list": {"ms": t_gc, "pairs_in_range": in_range,
                              "pairs_in_range_per_s": in_range / (t_gc * 1e-3),
                              "speedup_vs_all_pairs": t_gr / t_gc,

@@ -94,6 +94,12 @@ typedef struct {
      * + b] (symmetric; k = 0: no spring). Non-bonded terms inside a molecule are left out. */
     double bond_k[EPSR_MAX_TYPES * EPSR_MAX_TYPES];
     double bond_d[EPSR_MAX_TYPES * EPSR_MAX_TYPES];
+    /* Lennard-Jones cutoff (A). 0, the form the paper's dU takes (every atom of the box):
+     * LJ over every minimum-image pair. > 0: LJ plainly truncated at r_lj (the exact integer
+     * test d^2 < llround(r_lj S)^2, no shift), so every partner beyond max(r_lj, r_coul, the
+     * EP table) contributes nothing and the sweep finds the others by cell queries: the cost
+     * of a move is O(neighbours) instead of O(N) (Sec. 2.3's cost statement). */
+    double r_lj;
 } epsr_box_desc;
 
 typedef struct epsr_box epsr_box;   /* opaque: one box or a batch of boxes */

@@ -51,7 +51,7 @@ class OrcSystem(C.Structure):
                 ("bond_k", C.c_double * (MAX_TYPES * MAX_TYPES)),
                 ("bond_d", C.c_double * (MAX_TYPES * MAX_TYPES)), ("temperature", C.c_double),
                 ("max_translation", C.c_double), ("max_rotation_deg", C.c_double),
-                ("ep", C.POINTER(C.c_double))]
+                ("ep", C.POINTER(C.c_double)), ("r_lj", C.c_double)]
 
 
 class OrcStats(C.Structure):
@@ -147,6 +147,7 @@ class Box:
         st.max_translation = system.max_translation
         st.max_rotation_deg = system.max_rotation_deg
         st.ep = _ptr(self.ep, C.c_double) if self.ep is not None else C.POINTER(C.c_double)()
+        st.r_lj = float(getattr(system, "r_lj", 0.0))
         self.st = st
 
     @property

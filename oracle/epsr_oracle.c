@@ -123,7 +123,8 @@ double orc_pair_energy(const orc_system *s, int32_t ta, int32_t tb, int64_t d2)
     const double r = sqrt((double)d2) / S;
     double u = 0.0;
     const double eps = sqrt(s->eps[ta] * s->eps[tb]);
-    if (eps > 0.0) {
+    const int64_t rl_fx = llround(s->r_lj * S);
+    if (eps > 0.0 && (s->r_lj <= 0.0 || d2 < rl_fx * rl_fx)) {
         const double sig = 0.5 * (s->sigma[ta] + s->sigma[tb]);
         const double x = sig / r;
         const double x6 = x * x * x * x * x * x;

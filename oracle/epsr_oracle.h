@@ -45,6 +45,8 @@ typedef struct {
     double max_translation;    /* A */
     double max_rotation_deg;
     const double *ep;          /* [n_pairs][n_bins] empirical potential (kJ/mol) or NULL */
+    double r_lj;               /* Lennard-Jones cutoff (A): 0 = every pair (reading c1), > 0 =
+                                  plainly truncated at r_lj (d^2 < llround(r_lj S)^2) */
 } orc_system;
 
 typedef struct {

@@ -211,7 +211,7 @@ static int validate_desc(const epsr_box_desc &d, int b)
                     return set_error(EPSR_EINVAL, "box %d: spring of types %d-%d invalid or not symmetric", b, a, c);
             }
     if (!(d.temperature > 0) || !(d.max_translation >= 0) || !(d.max_rotation_deg >= 0) ||
-        !(d.max_rotation_deg < 180) || !(d.r_coul >= 0))
+        !(d.max_rotation_deg < 180) || !(d.r_coul >= 0) || !(d.r_lj >= 0) || !(d.r_lj < 1e6))
         return set_error(EPSR_EINVAL, "box %d: temperature/move/cutoff parameters invalid", b);
     const double S = std::ldexp(1.0, d.scale_log2);
     if (d.max_translation * S > 0.25 * (double)d.L_fx)
@@ -252,6 +252,11 @@ static void fill_boxdev(const epsr_box_desc &d, const int *type, BoxDev &b)
     b.max_shift = (int)std::llround(d.max_translation * S);
     const long long rc = std::llround(d.r_coul * S);
     b.rc2 = rc * rc;
+    b.lj_cut = d.r_lj > 0.0 ? 1 : 0;
+    const long long rl = b.lj_cut ? std::llround(d.r_lj * S) : 0;
+    b.lj2 = rl * rl;
+    b.lj2_lo = (float)((double)b.lj2 * (1.0 - 0x1p-20));
+    b.lj2_hi = (float)((double)b.lj2 * (1.0 + 0x1p-20));
     const double pi = 3.14159265358979323846;
     b.h_rot = std::tan(0.5 * d.max_rotation_deg * pi / 180.0) / std::sqrt(3.0);
     if (d.move_kind == EPSR_MOVE_FLEXIBLE_MOLECULE)
@@ -285,10 +290,12 @@ static void fill_boxdev(const epsr_box_desc &d, const int *type, BoxDev &b)
         }
 }
 
-// Radius (grid units) beyond which a pair has no Coulomb and no empirical-potential term.
+// Radius (grid units) beyond which a pair has no Coulomb, no empirical-potential and, when the
+// Lennard-Jones term is cut, no Lennard-Jones term.
 static void set_near(BoxDev &bx)
 {
-    const long long lim = std::max<long long>(bx.rc2, bx.has_ep ? bx.tmax : 0LL);
+    const long long lim = std::max<long long>(std::max<long long>(bx.rc2, bx.has_ep ? bx.tmax : 0LL),
+                                              bx.lj_cut ? bx.lj2 : 0LL);
     bx.near_fx = (int)std::ceil(std::sqrt((double)lim)) + 1;
 }
 

@@ -58,7 +58,10 @@ struct BoxDev {
     int32_t cell0;        // first global cell of this box (spatial sort)
     int32_t cells_p3;     // cells per box in the sort key space (power of two cubed)
     int32_t mc_cell0;     // first key of this box in the type-major sort
-    int32_t near_fx;      // ceil(sqrt(max(rc2, tmax if an EP is set))), grid units
+    int32_t near_fx;      // ceil(sqrt(max(rc2, tmax if an EP is set, lj2 if LJ is cut))), grid units
+    int32_t lj_cut;       // 1: Lennard-Jones truncated at d2 < lj2; 0: over every pair
+    int64_t lj2;          // (llround(r_lj * S))^2, grid units^2
+    float lj2_lo, lj2_hi; // lj2 * (1 -/+ 2^-20)
     int32_t gc_n;         // cell-list histogram: cells per side (>= 3, each at least the
                           // histogram range wide), or 0 when the box is too small for it
     int32_t gc0;          // first key of this box in the cell-list sort
@@ -134,6 +137,19 @@ __device__ __forceinline__ int bin_of(long long d2, float g2, const long long *T
     return k;
 }
 
+// A pair row whose Lennard-Jones term reaches every partner (LJ not cut): evaluated against
+// the whole slice. Any other row with a term is "near": non-zero only within near_fx of the
+// moved atom, so its partners can come from cell queries.
+__device__ __forceinline__ bool lj_full_row(const PairRow &r, const BoxDev &bx)
+{
+    return (r.c12 != 0.f || r.c6 != 0.f) && !bx.lj_cut;
+}
+
+__device__ __forceinline__ bool near_row(const PairRow &r, const BoxDev &bx)
+{
+    return !lj_full_row(r, bx) && (r.c12 != 0.f || r.c6 != 0.f || r.kqq != 0.f || bx.has_ep);
+}
+
 // Pair energy of a separation (FP32; Sec. 2.1: reference potential + empirical
 // potential). Coincident points have +inf energy.
 __device__ __forceinline__ float pair_u(Sep s, const PairRow &pr, const BoxDev &bx,
@@ -144,7 +160,7 @@ __device__ __forceinline__ float pair_u(Sep s, const PairRow &pr, const BoxDev &
     const float r2 = g2 * bx.inv_s2;
     const float a = rsqrtf(r2);
     float u = 0.f;
-    if (pr.c12 != 0.f || pr.c6 != 0.f) {
+    if ((pr.c12 != 0.f || pr.c6 != 0.f) && (!bx.lj_cut || below(g2, s, bx.lj2, bx.lj2_lo, bx.lj2_hi))) {
         const float i2 = a * a;
         const float s6 = i2 * i2 * i2;
         u = fmaf(pr.c12, s6, -pr.c6) * s6;
@@ -201,7 +217,23 @@ __device__ __forceinline__ float pair_du(Sep sn, Sep so, const PairRow &pr, cons
     const float g2n = c.g2n, g2o = c.g2o, an = c.an, ao = c.ao, dr2 = c.dr2;
     if (g2n == 0.f) return __int_as_float(0x7f800000);
     float du = 0.f;
-    if (pr.c12 != 0.f || pr.c6 != 0.f) du = lj_du(c, pr.c12, pr.c6);
+    if (pr.c12 != 0.f || pr.c6 != 0.f) {
+        if (!bx.lj_cut) {
+            du = lj_du(c, pr.c12, pr.c6);
+        } else {
+            // truncated LJ: the difference where both sides are inside, else the one term
+            const bool ln = below(g2n, sn, bx.lj2, bx.lj2_lo, bx.lj2_hi);
+            const bool lo = below(g2o, so, bx.lj2, bx.lj2_lo, bx.lj2_hi);
+            if (ln && lo) {
+                du = lj_du(c, pr.c12, pr.c6);
+            } else if (ln || lo) {
+                const float a2 = ln ? an * an : ao * ao;
+                const float s6 = a2 * a2 * a2;
+                const float u = fmaf(pr.c12, s6, -pr.c6) * s6;
+                du = ln ? u : -u;
+            }
+        }
+    }
     const bool cn = below(g2n, sn, bx.rc2, bx.rc2_lo, bx.rc2_hi);
     const bool co = below(g2o, so, bx.rc2, bx.rc2_lo, bx.rc2_hi);
     if (cn && co) {

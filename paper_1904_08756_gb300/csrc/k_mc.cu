@@ -355,8 +355,8 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
         for (int a = 0; a < M; ++a) {
             pr[a] = &bx.row[pn[a].w * kMaxTypes + t];
             if (a >= m) continue;
-            if (pr[a]->c12 != 0.f || pr[a]->c6 != 0.f) lj |= 1u << a;
-            else if (pr[a]->kqq != 0.f || bx.has_ep) nr |= 1u << a;
+            if (lj_full_row(*pr[a], bx)) lj |= 1u << a;
+            else if (near_row(*pr[a], bx)) nr |= 1u << a;
         }
         if (SKIP_LJ) lj = 0u;                            // Lennard-Jones rows done by the caller
         if (!(lj | nr)) continue;
@@ -435,7 +435,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
                 continue;
             for (int a = 0; a < m; ++a) {
                 const PairRow &r = bx.row[np[a].w * kMaxTypes + t];
-                if (r.c12 == 0.f && r.c6 == 0.f && (r.kqq != 0.f || bx.has_ep))
+                if (near_row(r, bx))
                     acc += pair_du_cold(sep(np[a], pj, L), sep(op[a], pj, L), r, bx, T, ep);
             }
         }
@@ -457,7 +457,7 @@ __device__ __forceinline__ float lj_chunk(const int4 *np, const int4 *op, int m,
         po[a] = a < m ? op[a] : make_int4(0, 0, 0, 0);
         if (a < m) {
             const PairRow &r = bx.row[pn[a].w * kMaxTypes + t];
-            if (r.c12 != 0.f || r.c6 != 0.f) lj |= 1u << a;
+            if (lj_full_row(r, bx)) lj |= 1u << a;
         }
     }
     if (!lj) return 0.f;
@@ -476,8 +476,8 @@ __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, in
         unsigned lj = 0u, nr = 0u;
         for (int a = 0; a < m; ++a) {
             const PairRow &pr = bx.row[np[a].w * kMaxTypes + t];
-            if (pr.c12 != 0.f || pr.c6 != 0.f) lj |= 1u << a;
-            else if (pr.kqq != 0.f || bx.has_ep) nr |= 1u << a;
+            if (lj_full_row(pr, bx)) lj |= 1u << a;
+            else if (near_row(pr, bx)) nr |= 1u << a;
         }
         if (!(lj | nr)) continue;
         for (int j = blk[t] + lane; j < blk[t + 1]; j += 32) {
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         for (int a = 0; a < nt; ++a)
             for (int b = 0; b < nt; ++b) {
                 const PairRow &r = bx.row[a * kMaxTypes + b];
-                near_rows |= r.c12 == 0.f && r.c6 == 0.f && (r.kqq != 0.f || bx.has_ep);
+                near_rows |= near_row(r, bx);
             }
         sh.n_esc = 0;
         sh.cells_on = near_rows && A.esc_cap > 0 ? 1 : 0;

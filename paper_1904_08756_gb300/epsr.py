@@ -52,7 +52,7 @@ class BoxDesc(C.Structure):
                 ("n_bins", C.c_int32), ("move_kind", C.c_int32), ("temperature", C.c_double),
                 ("max_translation", C.c_double), ("max_rotation_deg", C.c_double),
                 ("bond_k", C.c_double * (MAX_TYPES * MAX_TYPES)),
-                ("bond_d", C.c_double * (MAX_TYPES * MAX_TYPES))]
+                ("bond_d", C.c_double * (MAX_TYPES * MAX_TYPES)), ("r_lj", C.c_double)]
 
 
 class Tuning(C.Structure):
@@ -249,6 +249,7 @@ def box_desc(system) -> BoxDesc:
     d.temperature = system.temperature
     d.max_translation = system.max_translation
     d.max_rotation_deg = system.max_rotation_deg
+    d.r_lj = float(getattr(system, "r_lj", 0.0))
     return d
 
 

