@@ -890,6 +890,8 @@ static int mc_sweep_enqueue(epsr_box *box, int64_t n_moves, uint64_t seed, uint6
     a.max_spin = 1LL << 40;
     a.timeout_ns = (unsigned long long)(box->timeout_ms * 1e6);
     a.grid = box->cta_box_len;
+    a.lj_cut = 0;
+    for (const auto &b : box->hb) a.lj_cut |= b.lj_cut;
     a.batch_k = box->mc_batch;
     a.slice_cap = slice_cap;
     a.tbl_cap = box->tbl_cap;

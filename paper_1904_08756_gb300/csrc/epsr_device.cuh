@@ -139,15 +139,18 @@ __device__ __forceinline__ int bin_of(long long d2, float g2, const long long *T
 
 // A pair row whose Lennard-Jones term reaches every partner (LJ not cut): evaluated against
 // the whole slice. Any other row with a term is "near": non-zero only within near_fx of the
-// moved atom, so its partners can come from cell queries.
+// moved atom, so its partners can come from cell queries. CUT = false compiles the form
+// without a cutoff (boxes with r_lj = 0); CUT = true reads the box's setting.
+template <bool CUT = true>
 __device__ __forceinline__ bool lj_full_row(const PairRow &r, const BoxDev &bx)
 {
-    return (r.c12 != 0.f || r.c6 != 0.f) && !bx.lj_cut;
+    return (r.c12 != 0.f || r.c6 != 0.f) && !(CUT && bx.lj_cut);
 }
 
+template <bool CUT = true>
 __device__ __forceinline__ bool near_row(const PairRow &r, const BoxDev &bx)
 {
-    return !lj_full_row(r, bx) && (r.c12 != 0.f || r.c6 != 0.f || r.kqq != 0.f || bx.has_ep);
+    return !lj_full_row<CUT>(r, bx) && (r.c12 != 0.f || r.c6 != 0.f || r.kqq != 0.f || bx.has_ep);
 }
 
 // Pair energy of a separation (FP32; Sec. 2.1: reference potential + empirical
@@ -209,7 +212,9 @@ __device__ __forceinline__ float lj_du(const DuCore &c, float c12, float c6)
 //   Coulomb: 1/r' - 1/r = (r^2 - r'^2) (a a')^2 / (a + a'),        a = 1/r, a' = 1/r'
 //   LJ:      s' - s = (r^2 - r'^2)(r^4 + r^2 r'^2 + r'^4) s s',      s = r^-6, s' = r'^-6
 //            c12 (s'^2 - s^2) - c6 (s' - s) = (s' - s)(c12 (s' + s) - c6)
-// so the FP32 error is a few ulp of |u(r') - u(r)|, not of |u|.
+// so the FP32 error is a few ulp of |u(r') - u(r)|, not of |u|. With CUT, a box whose LJ is
+// truncated (lj_cut) takes the LJ term only where r' or r is inside r_lj.
+template <bool CUT = false>
 __device__ __forceinline__ float pair_du(Sep sn, Sep so, const PairRow &pr, const BoxDev &bx,
                                          const long long *T, const float *ep)
 {
@@ -218,7 +223,7 @@ __device__ __forceinline__ float pair_du(Sep sn, Sep so, const PairRow &pr, cons
     if (g2n == 0.f) return __int_as_float(0x7f800000);
     float du = 0.f;
     if (pr.c12 != 0.f || pr.c6 != 0.f) {
-        if (!bx.lj_cut) {
+        if (!CUT || !bx.lj_cut) {
             du = lj_du(c, pr.c12, pr.c6);
         } else {
             // truncated LJ: the difference where both sides are inside, else the one term

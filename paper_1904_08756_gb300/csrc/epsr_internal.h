@@ -73,6 +73,7 @@ struct McArgs {
     long long max_spin;           // iteration limit of one barrier wait
     unsigned long long timeout_ns;// time limit of one barrier wait
     int grid;
+    int lj_cut;                   // 1: some box truncates Lennard-Jones (the cut instantiation runs)
     int batch_k;
     int slice_cap;                // int4 capacity of the shared partner slice
     int tbl_cap;                  // capacity (entries) of the shared threshold table

@@ -270,10 +270,11 @@ __device__ __forceinline__ bool near_cell(int x, int k, const int *cb, int L, in
 }
 
 // Out-of-line copy of pair_du for code that runs once per batch (keeps the kernel small).
+template <bool CUT>
 __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, const BoxDev &bx,
                                            const long long *T, const float *ep)
 {
-    return pair_du(sn, so, pr, bx, T, ep);
+    return pair_du<CUT>(sn, so, pr, bx, T, ep);
 }
 
 // Lennard-Jones rows (bit a of lj: atom a of the move) against partners [j0, j1) of type t,
@@ -281,7 +282,7 @@ __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, co
 // per step. A pair whose squared distances both exceed far2 has no Coulomb and no EP term,
 // so its dU is the Lennard-Jones change alone, computed as straight-line code for both
 // partners at once; a pair that is not that far takes the full pair_du (same value).
-template <int M>
+template <int M, bool CUT>
 __device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const int4 (&po)[M], unsigned lj, int a0,
                                          int m, const int4 *part, int j0, int j1, int t, const BoxDev &bx,
                                          const long long *T, const float *ep, int lane)
@@ -306,8 +307,8 @@ __device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const i
             const bool s0 = v0 && !(c0.g2n > far2 && c0.g2o > far2);
             const bool s1 = v1 && !(c1.g2n > far2 && c1.g2o > far2);
             if (s0 || s1) {
-                if (s0) d0 = pair_du(n0, o0, r, bx, T, ep);
-                if (s1) d1 = pair_du(n1, o1, r, bx, T, ep);
+                if (s0) d0 = pair_du<CUT>(n0, o0, r, bx, T, ep);
+                if (s1) d1 = pair_du<CUT>(n1, o1, r, bx, T, ep);
             }
             if (v0) acc += d0;
             if (v1) acc += d1;
@@ -323,7 +324,7 @@ __device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const i
 // around old atom 0 (half width hw), so its partners come from a cell query when the cube
 // meets at most 32 cells, else from the full scan with the cube test. M is a compile-time
 // bound so the atom loop unrolls into independent dependency chains.
-template <int M, bool CELLS, bool SKIP_LJ = false>
+template <int M, bool CELLS, bool CUT, bool SKIP_LJ = false>
 __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int m, int a0, int hw,
                                              const int4 *slice, const int *blk, const CellIndex &ci,
                                              const BoxDev &bx, const long long *T, const float *ep,
@@ -355,15 +356,15 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
         for (int a = 0; a < M; ++a) {
             pr[a] = &bx.row[pn[a].w * kMaxTypes + t];
             if (a >= m) continue;
-            if (lj_full_row(*pr[a], bx)) lj |= 1u << a;
-            else if (near_row(*pr[a], bx)) nr |= 1u << a;
+            if (lj_full_row<CUT>(*pr[a], bx)) lj |= 1u << a;
+            else if (near_row<CUT>(*pr[a], bx)) nr |= 1u << a;
         }
         if (SKIP_LJ) lj = 0u;                            // Lennard-Jones rows done by the caller
         if (!(lj | nr)) continue;
         const bool cells = nr && use_cells;
         const unsigned scan_nr = cells ? 0u : nr;
         if (lj && !scan_nr) {
-            acc = lj_rows<M>(acc, pn, po, lj, a0, m, slice, blk[t], blk[t + 1], t, bx, T, ep, lane);
+            acc = lj_rows<M, CUT>(acc, pn, po, lj, a0, m, slice, blk[t], blk[t + 1], t, bx, T, ep, lane);
         } else if (lj | scan_nr) {
             const int jb = blk[t + 1];
 #pragma unroll 2
@@ -376,7 +377,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
 #pragma unroll
                 for (int a = 0; a < M; ++a) {
                     if (a < m && !self && (((lj >> a) & 1u) || (((scan_nr >> a) & 1u) && near)))
-                        acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
+                        acc += pair_du<CUT>(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
                 }
             }
         }
@@ -418,7 +419,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
 #pragma unroll
                         for (int a = 0; a < M; ++a)
                             if (a < m && ((nr >> a) & 1u))
-                                acc += pair_du(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
+                                acc += pair_du<CUT>(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
                     }
                 }
             }
@@ -435,8 +436,8 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
                 continue;
             for (int a = 0; a < m; ++a) {
                 const PairRow &r = bx.row[np[a].w * kMaxTypes + t];
-                if (near_row(r, bx))
-                    acc += pair_du_cold(sep(np[a], pj, L), sep(op[a], pj, L), r, bx, T, ep);
+                if (near_row<CUT>(r, bx))
+                    acc += pair_du_cold<CUT>(sep(np[a], pj, L), sep(op[a], pj, L), r, bx, T, ep);
             }
         }
     return acc;
@@ -444,7 +445,7 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
 
 // Lennard-Jones rows of one move against a staged chunk of partners of type t (the chunk
 // is shared by all warps of the CTA; used when the slices live in global memory).
-template <int M>
+template <int M, bool CUT>
 __device__ __forceinline__ float lj_chunk(const int4 *np, const int4 *op, int m, int a0, const int4 *stage,
                                           int nc, int t, const BoxDev &bx, const long long *T, const float *ep,
                                           int lane)
@@ -457,14 +458,15 @@ __device__ __forceinline__ float lj_chunk(const int4 *np, const int4 *op, int m,
         po[a] = a < m ? op[a] : make_int4(0, 0, 0, 0);
         if (a < m) {
             const PairRow &r = bx.row[pn[a].w * kMaxTypes + t];
-            if (lj_full_row(r, bx)) lj |= 1u << a;
+            if (lj_full_row<CUT>(r, bx)) lj |= 1u << a;
         }
     }
     if (!lj) return 0.f;
-    return lj_rows<M>(0.f, pn, po, lj, a0, m, stage, 0, nc, t, bx, T, ep, lane);
+    return lj_rows<M, CUT>(0.f, pn, po, lj, a0, m, stage, 0, nc, t, bx, T, ep, lane);
 }
 
 // The same for any molecule size (atoms read from shared memory; out-of-line pair function).
+template <bool CUT>
 __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, int m, int a0, int hw,
                                               const int4 *slice, const int *blk, const BoxDev &bx,
                                               const long long *T, const float *ep, int lane)
@@ -476,8 +478,8 @@ __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, in
         unsigned lj = 0u, nr = 0u;
         for (int a = 0; a < m; ++a) {
             const PairRow &pr = bx.row[np[a].w * kMaxTypes + t];
-            if (lj_full_row(pr, bx)) lj |= 1u << a;
-            else if (near_row(pr, bx)) nr |= 1u << a;
+            if (lj_full_row<CUT>(pr, bx)) lj |= 1u << a;
+            else if (near_row<CUT>(pr, bx)) nr |= 1u << a;
         }
         if (!(lj | nr)) continue;
         for (int j = blk[t] + lane; j < blk[t + 1]; j += 32) {
@@ -491,7 +493,7 @@ __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, in
             for (int a = 0; a < m; ++a) {
                 if ((todo >> a) & 1u) {
                     const int4 pn = np[a], po = op[a];
-                    acc += pair_du_cold(sep(pn, pj, L), sep(po, pj, L), bx.row[pn.w * kMaxTypes + t], bx, T, ep);
+                    acc += pair_du_cold<CUT>(sep(pn, pj, L), sep(po, pj, L), bx.row[pn.w * kMaxTypes + t], bx, T, ep);
                 }
             }
         }
@@ -502,7 +504,7 @@ __device__ __noinline__ float partner_sum_any(const int4 *np, const int4 *op, in
 // GSLICE: the partner slices live in global memory ([grid][slice_cap], read through L1/L2)
 // because they do not fit in shared memory; the thresholds, EP table and cell index stay
 // in shared memory either way.
-template <bool GSLICE>
+template <bool GSLICE, bool CUT>
 __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         for (int a = 0; a < nt; ++a)
             for (int b = 0; b < nt; ++b) {
                 const PairRow &r = bx.row[a * kMaxTypes + b];
-                near_rows |= near_row(r, bx);
+                near_rows |= near_row<CUT>(r, bx);
             }
         sh.n_esc = 0;
         sh.cells_on = near_rows && A.esc_cap > 0 ? 1 : 0;
@@ -778,7 +780,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 if (a < sh.natoms[k] && b < sh.natoms[k1]) {
                     const int4 na = sh.newp[par][k][a], oa = sh.oldp[k][a];
                     const int4 p1 = side ? sh.oldp[k1][b] : sh.newp[par][k1][b];
-                    v = pair_du(sep(na, p1, L), sep(oa, p1, L), bx.row[na.w * kMaxTypes + p1.w], bx, T, ep);
+                    v = pair_du<CUT>(sep(na, p1, L), sep(oa, p1, L), bx.row[na.w * kMaxTypes + p1.w], bx, T, ep);
                 }
                 corr_part[it] = v;
             }
@@ -793,8 +795,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     for (int b = 0; b < sh.natoms[k1]; ++b) {
                         const int4 nb1 = sh.newp[par][k1][b], ob1 = sh.oldp[k1][b];
                         const PairRow &pr = bx.row[na.w * kMaxTypes + nb1.w];
-                        ca += pair_du_cold(sep(na, nb1, L), sep(oa, nb1, L), pr, bx, T, ep) -
-                              pair_du_cold(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
+                        ca += pair_du_cold<CUT>(sep(na, nb1, L), sep(oa, nb1, L), pr, bx, T, ep) -
+                              pair_du_cold<CUT>(sep(na, ob1, L), sep(oa, ob1, L), pr, bx, T, ep);
                     }
                 }
                 corr_part[it] = ca;
@@ -820,8 +822,8 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                         const int k = warp + q * kMcWarps;
                         if (k >= nb) continue;
                         const int m = sh.natoms[k];
-                        accL[q] += m == 1 ? lj_chunk<1>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], stage, nc, t, bx, T, ep, lane)
-                                          : lj_chunk<3>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], stage, nc, t, bx, T, ep, lane);
+                        accL[q] += m == 1 ? lj_chunk<1, CUT>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], stage, nc, t, bx, T, ep, lane)
+                                          : lj_chunk<3, CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], stage, nc, t, bx, T, ep, lane);
                     }
                 }
             }
@@ -839,14 +841,14 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 const int m = sh.natoms[k];
                 float acc = accL[q];
                 if (m == 1)
-                    acc += ci.on ? partner_sum<1, true, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
+                    acc += ci.on ? partner_sum<1, true, CUT, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
                                                               slice, sh.blk, ci, bx, T, ep, lane)
-                                 : partner_sum<1, false, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
+                                 : partner_sum<1, false, CUT, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
                                                                slice, sh.blk, ci, bx, T, ep, lane);
                 else
-                    acc += ci.on ? partner_sum<3, true, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                    acc += ci.on ? partner_sum<3, true, CUT, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                                               slice, sh.blk, ci, bx, T, ep, lane)
-                                 : partner_sum<3, false, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                                 : partner_sum<3, false, CUT, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                                                slice, sh.blk, ci, bx, T, ep, lane);
                 acc = warp_sum(acc);
                 if (lane == 0) sh.part[k] = acc;
@@ -863,17 +865,17 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             ci.margin = A.cell_margin;
             ci.on = sh.cells_on != 0;
             if (m == 1)
-                acc = ci.on ? partner_sum<1, true>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
+                acc = ci.on ? partner_sum<1, true, CUT>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
                                                    slice, sh.blk, ci, bx, T, ep, lane)
-                            : partner_sum<1, false>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
+                            : partner_sum<1, false, CUT>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
                                                     slice, sh.blk, ci, bx, T, ep, lane);
             else if (m <= 3)
-                acc = ci.on ? partner_sum<3, true>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                acc = ci.on ? partner_sum<3, true, CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                                    slice, sh.blk, ci, bx, T, ep, lane)
-                            : partner_sum<3, false>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                            : partner_sum<3, false, CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                                     slice, sh.blk, ci, bx, T, ep, lane);
             else
-                acc = partner_sum_any(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
+                acc = partner_sum_any<CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                       slice, sh.blk, bx, T, ep, lane);
             acc = warp_sum(acc);
             if (lane == 0) sh.part[k] = acc;
@@ -1108,17 +1110,20 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
 
 int launch_mc_sweep(const McArgs &args, int grid, size_t smem, cudaStream_t stream)
 {
+    // instantiations: partner slices in shared or global memory x Lennard-Jones uncut or cut
+    const void *fns[2][2] = {{(const void *)mc_sweep_kernel<false, false>, (const void *)mc_sweep_kernel<false, true>},
+                             {(const void *)mc_sweep_kernel<true, false>, (const void *)mc_sweep_kernel<true, true>}};
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(mc_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMcMaxDynSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mc_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kMcMaxDynSmem);
-        if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(mc)");
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                cudaError_t e = cudaFuncSetAttribute(fns[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kMcMaxDynSmem);
+                if (e != cudaSuccess) return set_cuda_error(e, "cudaFuncSetAttribute(mc)");
+            }
         attr_set = true;
     }
-    const void *fn = args.slice_g ? (const void *)mc_sweep_kernel<true> : (const void *)mc_sweep_kernel<false>;
+    const void *fn = fns[args.slice_g ? 1 : 0][args.lj_cut ? 1 : 0];
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMcThreads, smem);
     if (e != cudaSuccess) return set_cuda_error(e, "occupancy(mc)");
