@@ -205,7 +205,7 @@ def run_reference(args):
 # Replicas: 64 boxes of uneven size advanced together, each step captured as a CUDA graph
 # ------------------------------------------------------------------------------------------
 
-def time_sq_modes(Q, g, ws, flats, S_like, nb, stream, flush, reps: int = 20):
+def time_sq_modes(Q, g, ws, flats, S_like, nb, stream, flush, reps: int = 20, autotune: bool = True):
     """S(Q) of the same resident g(r) columns in every contraction mode: mean time of one
     epsr_sq_exec (CUDA events on the launching stream, L2 flushed before each, the GPU kept
     busy ahead of the events so that no host latency falls between them) and the largest
@@ -223,7 +223,8 @@ def time_sq_modes(Q, g, ws, flats, S_like, nb, stream, flush, reps: int = 20):
         for mode, name in names.items():
             plan = epsr.SqPlan(Q, n_bins, 0.02, mode, max_cols=n_cols)
             S = torch.zeros_like(S_like)
-            plan.epsr_sq_plan_autotune(g, ws, 3, flats, None, S)
+            if autotune:
+                plan.epsr_sq_plan_autotune(g, ws, 3, flats, None, S)
             for _ in range(3):
                 plan.epsr_sq_exec(g, ws, 3, flats, None, S, stream=stream.cuda_stream)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -409,6 +410,45 @@ def run_smeared(args):
     return 0
 
 
+def run_sq(args):
+    """The batched S(Q) of the 64-replica workload alone: [2000 Q x 600 r] x [600 r x 192]
+    (3 partial g(r) of 64 boxes, g-like synthetic columns: an excluded core, a first shell,
+    decaying oscillations), every contraction mode, L2 flushed before each call."""
+    import torch
+    from paper_1904_08756_gb300 import build, epsr
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if not os.path.exists(epsr.LIB_PATH):
+        build.build()
+    nb, n_bins, dr = 64, 600, 0.02
+    Q = 0.3 + np.arange(2000) * (39.7 / 1999.0)
+    rng = np.random.default_rng(3)
+    r = (np.arange(n_bins) + 0.5) * dr
+    r0 = rng.uniform(2.4, 3.2, (3 * nb, 1))
+    g = (1 + 1.5 * np.exp(-((r - r0) / 0.25) ** 2) - np.exp(-(r / 1.8) ** 8)
+         + 0.3 * np.sin(2 * np.pi * r / r0) * np.exp(-r / 4)).astype(np.float32)
+    gd = torch.from_numpy(g).to(dev)
+    ws = rng.uniform(0.05, 0.4, 3 * nb)
+    flats = rng.uniform(0.2, 0.6, nb)
+    S = torch.zeros((nb, len(Q)), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with ClockSampler(0) as clk:
+        modes = time_sq_modes(Q, gd, ws, flats, S, nb, stream, flush, reps=max(args.steps, 5),
+                              autotune=not args.no_autotune)
+    b = modes["bf16x3"]
+    line = {"metric": "batched S(Q) contraction time (Eq. (1), 64 replicas)", "value": b["ms"] * 1e3,
+            "unit": "us", "n_gpus": 1, "steps": max(args.steps, 5), "warmup": 3, "ms_per_step": b["ms"],
+            "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": "[2000 Q x 600 r] x [600 r x 192 columns] (cfg-3 batched S(Q))",
+                       "l2": "flushed before every call outside the timed events"},
+            "sq_modes": modes, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_replicas(args):
     import torch
     from paper_1904_08756_gb300 import build, epsr, synth
@@ -420,7 +460,7 @@ def run_replicas(args):
     systems = synth.replica_batch()
     nb = len(systems)
     box = epsr.Box(systems)
-    tuning = box.epsr_autotune()
+    tuning = None if args.no_autotune else box.epsr_autotune()
     ws = np.concatenate([box.epsr_sq_weights(b)[0] for b in range(nb)])
     flats = np.array([box.epsr_sq_weights(b)[1] for b in range(nb)])
     # the batched S(Q): all 3 x 64 columns in one BF16 split-precision tensor-core contraction
@@ -429,7 +469,7 @@ def run_replicas(args):
     g = torch.zeros(box.hist_len, dtype=torch.float32, device=dev)
     S = torch.zeros((nb, len(systems[0].Q)), dtype=torch.float32, device=dev)
     box.epsr_partial_gr(H, g, 1)
-    sq_tuning = plan.epsr_sq_plan_autotune(g.view(-1, 600), ws, 3, flats, None, S)
+    sq_tuning = None if args.no_autotune else plan.epsr_sq_plan_autotune(g.view(-1, 600), ws, 3, flats, None, S)
     H.zero_()
     stream = torch.cuda.Stream()
     moves = args.moves
@@ -465,7 +505,8 @@ def run_replicas(args):
         torch.cuda.synchronize()
     status = box.epsr_mc_status()
     t = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    sq_modes = time_sq_modes(systems[0].Q, g.view(-1, 600), ws, flats, S, nb, stream, flush)
+    sq_modes = time_sq_modes(systems[0].Q, g.view(-1, 600), ws, flats, S, nb, stream, flush,
+                             autotune=not args.no_autotune)
     n_atoms = [s.n_atoms for s in systems]
     line = {"metric": METRIC + " (replica batch)", "value": nb * moves / (t * 1e-3),
             "unit": "moves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -477,7 +518,7 @@ def run_replicas(args):
                        "l2": "flushed before every step outside the timed events"},
             "pair_distances_per_step": sum(n * (n - 1) // 2 for n in n_atoms),
             "status": status, "clocks": clk.summary(), "gpu_launches": launches,
-            "tuning": {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
+            "tuning": tuning and {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
             "sq_step_mode": "bf16x3", "sq_tuning": sq_tuning,
             "sq_modes": sq_modes}
     print(json.dumps(line), flush=True)
@@ -497,12 +538,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water", choices=["water", "silica", "flexible", "replicas", "sweep", "smeared"],
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="profiling runs only: keep the built-in launch rules (no tuning launches)")
+    ap.add_argument("--workload", default="water", choices=["water", "silica", "flexible", "replicas", "sweep", "smeared", "sq"],
                     help="water: the paper-scale water box (default line); silica: the paper-scale "
                          "SiO2 box with single-atom moves; flexible: the water box with flexible "
                          "molecules (springs, three kinds of moves); replicas: 64 uneven boxes; sweep: MC "
                          "moves/s at the paper's Table 1 atom counts; smeared: chi^2 and gradients of "
-                         "the differentiable form")
+                         "the differentiable form; sq: the batched S(Q) contraction alone")
     ap.add_argument("--max-atoms", type=int, default=0, help="sweep: largest atom count (0: all)")
     ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
                     help="moves per step (profiling runs only; the benchmark uses 10,000)")
@@ -517,6 +560,8 @@ def main():
         return run_sweep(args)
     if args.workload == "smeared":
         return run_smeared(args)
+    if args.workload == "sq":
+        return run_sq(args)
 
     import torch
     from paper_1904_08756_gb300 import build, epsr, shard, synth
@@ -541,7 +586,7 @@ def main():
     moves = args.moves
     stream = torch.cuda.current_stream(dev)
     box = epsr.Box(system)
-    tuning = box.epsr_autotune()          # launch shapes timed on this handle, state restored
+    tuning = None if args.no_autotune else box.epsr_autotune()   # launch shapes timed on this handle
     P = 3
     H = torch.zeros(box.hist_len, dtype=torch.int64, device=dev)
     g = torch.zeros(box.hist_len, dtype=torch.float32, device=dev)
@@ -596,20 +641,22 @@ def main():
     gr_pairs_per_s = pairs / (t_gr * 1e-3)
 
     # ---- end to end through the public API with host buffers --------------------------------
-    xyz_host = torch.from_numpy(np.ascontiguousarray(box.epsr_box_get_coords())).pin_memory()
-    xyz_dev = torch.empty((N, 3), dtype=torch.int32, device=dev)
+    # host wall clock around: coordinates from (pinned) host memory into the box by the
+    # library's host entry, the step, S(Q) back to host memory, synchronise
+    xyz_pin = torch.from_numpy(np.ascontiguousarray(box.epsr_box_get_coords())).pin_memory()
+    xyz_host = xyz_pin.numpy()
     S_host = torch.empty((1, len(system.Q)), dtype=torch.float32).pin_memory()
-    e2e_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    t_e2e_s = []
     for k in range(args.steps):
         flush.fill_(float(k))
-        e2e_ev[k][0].record(stream)
-        xyz_dev.copy_(xyz_host, non_blocking=True)
-        box.epsr_box_set_coords_device(xyz_dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        box.epsr_box_set_coords(xyz_host)
         step()
         S_host.copy_(S_t, non_blocking=True)
-        e2e_ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    t_e2e = sum(e[0].elapsed_time(e[1]) for e in e2e_ev) / args.steps
+        torch.cuda.synchronize()
+        t_e2e_s.append(time.perf_counter() - t0)
+    t_e2e = 1e3 * sum(t_e2e_s) / args.steps
     if ws > 1:
         tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -705,9 +752,11 @@ def main():
             "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                        "reasons": clock["reasons"]},
             "e2e": {"value": ws * moves / (t_e2e * 1e-3), "unit": "moves/s",
-                    "h2d_bytes_per_step": N * 3 * 4, "d2h_bytes_per_step": len(system.Q) * 4},
+                    "h2d_bytes_per_step": N * 3 * 4, "d2h_bytes_per_step": len(system.Q) * 4,
+                    "timing": "host wall clock: epsr_box_set_coords from pinned host memory, the step, "
+                              "S(Q) to host, synchronise"},
             "gpu_launches": launches,
-            "tuning": {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
+            "tuning": tuning and {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
         }
         if not args.no_cpu_baseline and ws == 1:
             o = oracle_full_step(system, moves_per_step=moves)
