@@ -529,6 +529,42 @@ def run_replicas(args):
 
 
 # ------------------------------------------------------------------------------------------
+# Side workloads of the default line (each its own process and JSON line, summarised)
+# ------------------------------------------------------------------------------------------
+
+SIDE_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "ms_breakdown", "roofline", "roofline_gr",
+             "gr_pair_distances_per_s", "mc_moves_per_s_kernel", "mc_pair_evals_per_s_kernel", "mc_lj_cutoff",
+             "tuning", "sq_tuning", "sq_modes", "clocks", "gpu_launches", "status", "sweep", "e2e", "config")
+
+
+def run_side_workloads():
+    """The other paper-shaped workloads, run in child processes on the same GPU after the main
+    measurement (so that the default run records them too): the silica step, the 64-replica
+    step under CUDA graphs, the batched S(Q) alone, the differentiable form, and the atom-count
+    sweep up to 2.5e5 atoms. Each entry is the child's own JSON line (selected keys) and its
+    wall time; a child that fails is recorded with its exit status."""
+    side = {}
+    runs = {"silica": ["--workload", "silica", "--steps", "10", "--no-cpu-baseline"],
+            "replicas": ["--workload", "replicas", "--steps", "5"],
+            "sq": ["--workload", "sq", "--steps", "10"],
+            "smeared": ["--workload", "smeared", "--steps", "5"],
+            "sweep": ["--workload", "sweep", "--max-atoms", "250000"]}
+    for name, extra in runs.items():
+        t0 = time.perf_counter()
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), *extra], capture_output=True, text=True,
+                           cwd=ROOT, timeout=900)
+        rec = {"wall_s": time.perf_counter() - t0, "args": " ".join(extra)}
+        lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+        if r.returncode != 0 or not lines:
+            rec.update({"status": "failed", "returncode": r.returncode, "stderr_tail": r.stderr[-400:]})
+        else:
+            d = json.loads(lines[-1])
+            rec.update({k: d[k] for k in SIDE_KEYS if k in d})
+        side[name] = rec
+    return side
+
+
+# ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
@@ -539,6 +575,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="water line: skip the side workloads (silica step, 64 replicas, batched S(Q), "
+                         "differentiable form, atom-count sweep to 2.5e5 atoms) run as subprocesses")
     ap.add_argument("--no-autotune", action="store_true",
                     help="profiling runs only: keep the built-in launch rules (no tuning launches)")
     ap.add_argument("--workload", default="water", choices=["water", "silica", "flexible", "replicas", "sweep", "smeared", "sq"],
@@ -764,6 +803,8 @@ def main():
             "gpu_launches": launches,
             "tuning": tuning and {k: tuning[k] for k in ("mc_batch", "mc_ctas", "gr_ctas_per_sm", "from_cache")},
         }
+        if args.workload == "water" and ws == 1 and not args.no_side and moves == MOVES_PER_STEP:
+            line["side_workloads"] = run_side_workloads()
         if not args.no_cpu_baseline and ws == 1:
             o = oracle_full_step(system, moves_per_step=moves)
             t_cpu = o["t_mc"] + o["t_gr"] + o["t_sq"]
