@@ -282,18 +282,6 @@ int epsr_debug_barrier_fault(epsr_box *box, int32_t cta, double timeout_ms);
  * lets a caller state how many of the library's kernels ran inside a timed region. */
 int epsr_launch_count(uint64_t *count);
 
-/* ---- measurements of this GPU (no counterpart in the paper) ------------------------------
- * epsr_bench_barrier_floor: the least time of one batch exchange of the Monte Carlo sweep:
- * `ctas` co-resident CTAs of 512 threads repeat, `iters` times, nothing but the sweep's grid
- * barrier (64 partials and the batch-pair corrections to the exchange buffer, release add,
- * acquire poll, fixed-order gather). Returns ns per barrier; EPSR_EINVAL if the CTAs cannot be co-resident,
- * EPSR_ETIMEOUT if a wait exceeded 2 s. Synchronises.
- * epsr_bench_alu_rate: lane-operations per second of independent chains in every lane on
- * every SM; kind 0 = 32-bit integer exclusive-or/add pairs, 1 = FP32 fused multiply-adds.
- * Synchronises. */
-int epsr_bench_barrier_floor(int32_t ctas, int32_t iters, double *ns_per_barrier, epsr_stream_t stream);
-int epsr_bench_alu_rate(int32_t kind, double *lane_ops_per_s, epsr_stream_t stream);
-
 /* ---- checkpoint / resume ----------------------------------------------------------------
  * A checkpoint is the coordinates, the empirical-potential tables and the running MC
  * statistics of every box, in a host buffer of epsr_checkpoint_size() bytes. The move

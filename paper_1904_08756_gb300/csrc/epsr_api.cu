@@ -1552,19 +1552,6 @@ extern "C" int epsr_chi2(epsr_sq_plan *plan, const float *S, const float *target
                        (cudaStream_t)stream);
 }
 
-// ---- measurements of this GPU -------------------------------------------------------------------
-extern "C" int epsr_bench_barrier_floor(int32_t ctas, int32_t iters, double *ns_per_barrier, epsr_stream_t stream)
-{
-    if (!ns_per_barrier || iters < 1) return set_error(EPSR_EINVAL, "bad argument");
-    return micro_barrier_floor(ctas, iters, 2000.0, ns_per_barrier, (cudaStream_t)stream);
-}
-
-extern "C" int epsr_bench_alu_rate(int32_t kind, double *lane_ops_per_s, epsr_stream_t stream)
-{
-    if (!lane_ops_per_s) return set_error(EPSR_EINVAL, "NULL argument");
-    return micro_alu_rate(kind, lane_ops_per_s, (cudaStream_t)stream);
-}
-
 // ---- checkpoint / resume ------------------------------------------------------------------------
 // Layout: magic, version, n_boxes, n_atoms, ep_len; then int32 [n_atoms][3] coordinates,
 // float [ep_len] empirical-potential tables, epsr_mc_stats [n_boxes], int32 [n_boxes] has_ep.

@@ -93,8 +93,6 @@ int launch_mc_moves(const BoxDev *boxes, const int *mol_start, int n_boxes, long
 int launch_intra_energy(const BoxDev *boxes, int n_boxes, const int4 *coords, const int *mol_start, double *U,
                         cudaStream_t stream);
 int mc_threads();
-int micro_barrier_floor(int ctas, int iters, double timeout_ms, double *ns_per_barrier, cudaStream_t stream);
-int micro_alu_rate(int kind, double *lane_ops_per_s, cudaStream_t stream);
 int mc_escapee_max();
 int mc_batch_max();
 

@@ -7,6 +7,7 @@
 //    fused multiply-adds in every lane, counted as lane-operations per second.
 #include "epsr_device.cuh"
 #include "epsr_internal.h"
+#include "epsr_probe.h"
 
 namespace epsr {
 
@@ -199,3 +200,16 @@ int micro_alu_rate(int kind, double *lane_ops_per_s, cudaStream_t stream)
 }
 
 }  // namespace epsr
+
+extern "C" int epsr_bench_barrier_floor(int32_t ctas, int32_t iters, double *ns_per_barrier, epsr_stream_t stream)
+{
+    if (!ns_per_barrier || iters < 1) return epsr::set_error(EPSR_EINVAL, "bad argument");
+    return epsr::micro_barrier_floor(ctas, iters, 2000.0, ns_per_barrier, (cudaStream_t)stream);
+}
+
+extern "C" int epsr_bench_alu_rate(int32_t kind, double *lane_ops_per_s, epsr_stream_t stream)
+{
+    if (!lane_ops_per_s) return epsr::set_error(EPSR_EINVAL, "NULL argument");
+    return epsr::micro_alu_rate(kind, lane_ops_per_s, (cudaStream_t)stream);
+}
+

@@ -14,6 +14,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libepsr.so")
+PROBE_LIB_PATH = os.path.join(_HERE, "libepsr_probe.so")
+# Every symbol include/epsr_probe.h declares (the measurement library of the benchmark).
+PROBE_EXPORTS = ["epsr_bench_barrier_floor", "epsr_bench_alu_rate"]
 
 EPSR_OK, EPSR_EINVAL, EPSR_ENOMEM, EPSR_ECUDA, EPSR_ELAUNCH, EPSR_ETIMEOUT, EPSR_ENUMERIC = range(7)
 MAX_TYPES = 8
@@ -36,7 +39,7 @@ EXPORTS = [
     "epsr_gr_smeared_fwd", "epsr_gr_smeared_bwd", "epsr_sq_exec_adjoint", "epsr_chi2",
     "epsr_checkpoint_size", "epsr_checkpoint_save", "epsr_checkpoint_load", "epsr_launch_count",
     "epsr_mc_set_cells", "epsr_sq_plan_status", "epsr_partial_gr_cells",
-    "epsr_bench_barrier_floor", "epsr_bench_alu_rate", "epsr_sq_plan_set_tiles",
+    "epsr_sq_plan_set_tiles",
     "epsr_sq_plan_get_tiles", "epsr_gr_set_ctas_per_sm", "epsr_box_get_launch", "epsr_autotune",
     "epsr_sq_plan_autotune", "epsr_refiner_create", "epsr_refine_step", "epsr_refiner_get",
     "epsr_refiner_destroy",
@@ -140,8 +143,6 @@ def lib():
             "epsr_checkpoint_size": ([vp, P(C.c_size_t)], C.c_int),
             "epsr_launch_count": ([P(C.c_uint64)], C.c_int),
             "epsr_mc_set_cells": ([vp, C.c_int32, C.c_int32], C.c_int),
-            "epsr_bench_barrier_floor": ([C.c_int32, C.c_int32, P(C.c_double), vp], C.c_int),
-            "epsr_bench_alu_rate": ([C.c_int32, P(C.c_double), vp], C.c_int),
             "epsr_sq_plan_status": ([vp, P(C.c_int32), vp], C.c_int),
             "epsr_checkpoint_save": ([vp, vp, C.c_size_t, vp], C.c_int),
             "epsr_checkpoint_load": ([vp, vp, C.c_size_t, vp], C.c_int),
@@ -261,17 +262,37 @@ def epsr_version() -> int:
     return lib().epsr_version()
 
 
+_probe = None
+
+
+def probe_lib():
+    """libepsr_probe.so: the GPU measurements of the benchmark (grid-barrier floor, issue rates),
+    kept out of the product library; it links against libepsr.so, loaded first."""
+    global _probe
+    if _probe is None:
+        lib()
+        if not os.path.exists(PROBE_LIB_PATH):
+            raise RuntimeError(f"libepsr_probe.so not built ({PROBE_LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(PROBE_LIB_PATH)
+        L.epsr_bench_barrier_floor.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+        L.epsr_bench_barrier_floor.restype = C.c_int
+        L.epsr_bench_alu_rate.argtypes = [C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+        L.epsr_bench_alu_rate.restype = C.c_int
+        _probe = L
+    return _probe
+
+
 def epsr_bench_barrier_floor(ctas: int, iters: int = 2000, stream=None) -> float:
     """ns per grid barrier of the sweep's exchange with `ctas` co-resident CTAs."""
     v = C.c_double()
-    _check(lib().epsr_bench_barrier_floor(ctas, iters, C.byref(v), _stream(stream)), "epsr_bench_barrier_floor")
+    _check(probe_lib().epsr_bench_barrier_floor(ctas, iters, C.byref(v), _stream(stream)), "epsr_bench_barrier_floor")
     return v.value
 
 
 def epsr_bench_alu_rate(kind: int, stream=None) -> float:
     """Lane-operations/s: kind 0 = int32 adds, 1 = FP32 FMAs."""
     v = C.c_double()
-    _check(lib().epsr_bench_alu_rate(kind, C.byref(v), _stream(stream)), "epsr_bench_alu_rate")
+    _check(probe_lib().epsr_bench_alu_rate(kind, C.byref(v), _stream(stream)), "epsr_bench_alu_rate")
     return v.value
 
 

@@ -12,8 +12,8 @@ from paper_1904_08756_gb300 import epsr, synth
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def header_functions():
-    src = open(os.path.join(ROOT, "include", "epsr.h")).read()
+def header_functions(name="epsr.h"):
+    src = open(os.path.join(ROOT, "include", name)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(epsr_[a-z0-9_]+)\s*\(", src)))
 
@@ -31,6 +31,13 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(epsr.EXPORTS) == names
+    # the measurement probes live in their own library, not in the product one
+    probe = header_functions("epsr_probe.h")
+    assert sorted(epsr.PROBE_EXPORTS) == probe
+    pl = epsr.probe_lib()
+    for n in probe:
+        assert hasattr(pl, n), n
+        assert n not in names
 
 
 def test_status_strings(lib):

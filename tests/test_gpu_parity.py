@@ -667,6 +667,51 @@ def test_refine_pass_against_oracle():
         ob.set_ep(ep_gpu)
 
 
+def test_refine_pass_three_isotopic_datasets():
+    """The paper's water case: three datasets of the same box that differ only in the hydrogen
+    scattering length (H2O, D2O and an HDO-like 50:50 mixture), so the 3 x 3 weight matrix is
+    square and Eq. (2) inverts it (gamma = 0). One pass of 1,000 logged moves: the oracle replays
+    the moves and computes the pass; histograms bit-exact, S(Q) of every dataset and Delta S
+    within 1e-4 barn, fitted pair-resolved Delta S and table increment within the FP32 tolerance."""
+    s = synth.water_box(300, seed=18, L_A=20.8)
+    b_H, b_D = -3.739, 6.671
+    ws, flats = [], []
+    for bh in (b_H, b_D, 0.5 * (b_H + b_D)):
+        sd = synth.System(**{**s.__dict__, "b": [s.b[0], bh]})
+        W, fl = oracle.eq1_weights(sd)
+        ws.append(W)
+        flats.append(fl)
+    w = np.array(ws)
+    flat = np.array(flats)
+    assert abs(np.linalg.det(w)) > 1e-6            # three independent datasets
+    Q = s.Q.astype(np.float32).astype(np.float64)
+    tgt64 = flat[:, None] + 0.03 * np.sin(np.outer([1.0, 1.3, 0.8], Q)) * np.exp(-Q / 6)
+    target = torch.tensor(tgt64, dtype=torch.float32, device=DEV)
+    box = epsr.Box(s)
+    plan = epsr.SqPlan(s.Q, s.n_bins, s.dr, epsr.SQ_FP32, max_cols=9)
+    ref = epsr.Refiner(box, plan, target, w, flat, s.Q, moves_per_pass=1000, seed=23, accumulate=True,
+                       n_basis=20, s_basis=0.5, gamma=0.0, alpha=1.0)
+    log = torch.zeros((1000 * 128,), dtype=torch.uint8, device=DEV)
+    res = ref.step(log=log)
+    lg = log.cpu().numpy().view(epsr.MOVE_LOG_DTYPE)
+    ob, _, _, flips = replay(s, s.xyz, lg, 23)
+    assert flips <= 2
+    r = oracle.refine_pass(ob, target.cpu().numpy().astype(np.float64), w, flat, Q, 20, 0.5, 0.0, 1.0)
+    Hg = torch.zeros(box.hist_len, dtype=torch.int64, device=DEV)
+    Sg = torch.zeros((3, len(Q)), dtype=torch.float32, device=DEV)
+    dSg = torch.zeros((3, len(Q)), dtype=torch.float32, device=DEV)
+    C_gpu = ref.get(hist=Hg, S=Sg, dS=dSg)
+    assert np.array_equal(Hg.cpu().numpy().astype(np.uint64).reshape(3, -1), r["H"])
+    assert np.abs(Sg.cpu().numpy() - r["S"]).max() <= 1e-4
+    assert np.abs(dSg.cpu().numpy() - r["dS"]).max() <= 1e-4
+    assert abs(res["chi2"] - r["chi2"]) <= 1e-3 * r["chi2"]
+    F = oracle.ep_basis_matrix(20, 0.5, Q, s.n_atoms / s.L ** 3)
+    fit_gpu, fit_ref = C_gpu @ F.T, r["C"] @ F.T
+    assert np.abs(fit_gpu - fit_ref).max() <= 1e-3 * np.abs(fit_ref).max() + 1e-4
+    ep_gpu = box.epsr_box_get_ep(0, (3, s.n_bins)).astype(np.float64)
+    assert np.abs(ep_gpu - r["ep"]).max() <= 1e-3 * np.abs(r["ep"]).max() + 1e-4
+
+
 def test_refine_loop_reduces_chi2_on_the_gpu():
     """The GPU refiner against a target the oracle simulated with a planted repulsive bump
     (1.5 kJ/mol at 4.5 A) in an argon-like liquid: chi^2 falls to under half its first value
