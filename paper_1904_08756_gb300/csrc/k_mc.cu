@@ -317,6 +317,77 @@ __device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const i
     return acc;
 }
 
+// Near rows of one move against the partners of types ta (rows nra) and tb (rows nrb; tb < 0:
+// none) found by a cell query: the ncell cells of the CTA's 8^3 grid that meet the cube around
+// old atom 0 are taken one per lane, their runs for both types prefix-summed together (two
+// independent shuffle chains), and the candidates of type ta, then of type tb, dealt out to the
+// lanes; each candidate inside the cube (half width hw) adds its pair changes to acc.
+template <int M, bool CUT>
+__device__ __forceinline__ float cell_pairs(float acc, const int4 (&pn)[M], const int4 (&po)[M], int m, int a0,
+                                            int hw, int4 o0, int ta, unsigned nra, int tb, unsigned nrb,
+                                            const int4 *slice, const int *blk, const CellIndex &ci, int k0x, int nx,
+                                            int k0y, int ny, int k0z, int ncell, const BoxDev &bx,
+                                            const long long *T, const float *ep, int lane)
+{
+    const int L = bx.L;
+    int fa = 0, na = 0, fb = 0, nb = 0;
+    if (lane < ncell) {
+        const int ix = lane % nx, iy = (lane / nx) % ny, iz = lane / (nx * ny);
+        const unsigned code = cell_code((k0x + ix) & 7, (k0y + iy) & 7, (k0z + iz) & 7);
+        const unsigned *ca = ci.cst + ta * (kMcCells + 1);
+        fa = ca[code];
+        na = ca[code + 1] - fa;
+        if (tb >= 0) {
+            const unsigned *cb = ci.cst + tb * (kMcCells + 1);
+            fb = cb[code];
+            nb = cb[code + 1] - fb;
+        }
+    }
+    int ia = na, ib = nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ya = __shfl_up_sync(0xffffffffu, ia, o);
+        const int yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ya;
+            ib += yb;
+        }
+    }
+    const int ea = ia - na, eb = ib - nb;
+    const int tota = __shfl_sync(0xffffffffu, ia, 31), totb = __shfl_sync(0xffffffffu, ib, 31);
+    const int total = tota + totb;
+    for (int q0 = 0; q0 < total; q0 += 32) {
+        const int q = q0 + lane;
+        const bool isb = q >= tota;
+        const int qq = isb ? q - tota : q;
+        int c = 0;                                       // last cell whose run starts at or before qq
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int xa = __shfl_sync(0xffffffffu, ea, c + step);
+            const int xb = __shfl_sync(0xffffffffu, eb, c + step);
+            if (c + step < ncell && (isb ? xb : xa) <= qq) c += step;
+        }
+        const int cfa = __shfl_sync(0xffffffffu, fa, c), cea = __shfl_sync(0xffffffffu, ea, c);
+        const int cfb = __shfl_sync(0xffffffffu, fb, c), ceb = __shfl_sync(0xffffffffu, eb, c);
+        if (q < total) {
+            const int t = isb ? tb : ta;
+            const unsigned nr = isb ? nrb : nra;
+            const int4 pj = slice[blk[t] + (isb ? cfb + (qq - ceb) : cfa + (qq - cea))];
+            const int jatom = (pj.w & 0x7fffffff) >> 3;
+            const bool take = pj.w >= 0 && !(jatom >= a0 && jatom < a0 + m) && mi_abs(pj.x - o0.x, L) < hw &&
+                              mi_abs(pj.y - o0.y, L) < hw && mi_abs(pj.z - o0.z, L) < hw;
+            if (take) {
+#pragma unroll
+                for (int a = 0; a < M; ++a)
+                    if (a < m && ((nr >> a) & 1u))
+                        acc += pair_du<CUT>(sep(pn[a], pj, L), sep(po[a], pj, L), bx.row[pn[a].w * kMaxTypes + t], bx,
+                                            T, ep);
+            }
+        }
+    }
+    return acc;
+}
+
 // Partial dU of one move (atoms np/op, m <= M) against the partners of this CTA, lane-
 // strided. Per partner type the kind of each moved atom's pair row is uniform across the
 // warp: a Lennard-Jones row (LJ is not cut) is evaluated against every partner of the type;
@@ -348,6 +419,8 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
     const int ncell = nx * ny * nz;
     const bool use_cells = CELLS && ci.on && ncell <= 32;
     unsigned cell_types = 0u;
+    int pend_t = -1;                                     // a type whose cell query waits for a second
+    unsigned pend_nr = 0u;
     float acc = 0.f;
     for (int t = 0; t < bx.n_types; ++t) {
         unsigned lj = 0u, nr = 0u;
@@ -382,49 +455,21 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
             }
         }
         if (CELLS && cells) {
+            // cell queries of two partner types share one enumeration of the cells
             cell_types |= 1u << t;
-            const unsigned *cst = ci.cst + t * (kMcCells + 1);
-            int first = 0, cnt = 0;
-            if (lane < ncell) {
-                const int ix = lane % nx, iy = (lane / nx) % ny, iz = lane / (nx * ny);
-                const unsigned code = cell_code((k0x + ix) & 7, (k0y + iy) & 7, (k0z + iz) & 7);
-                first = cst[code];
-                cnt = cst[code + 1] - first;
-            }
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int excl = incl - cnt;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int q0 = 0; q0 < total; q0 += 32) {
-                const int q = q0 + lane;
-                int c = 0;                               // last cell whose run starts at or before q
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int e = __shfl_sync(0xffffffffu, excl, c + step);
-                    if (c + step < ncell && e <= q) c += step;
-                }
-                const int cf = __shfl_sync(0xffffffffu, first, c);
-                const int ce = __shfl_sync(0xffffffffu, excl, c);
-                if (q < total) {
-                    const int4 pj = slice[blk[t] + cf + (q - ce)];
-                    const int jatom = (pj.w & 0x7fffffff) >> 3;
-                    const bool take = pj.w >= 0 && !(jatom >= a0 && jatom < a0 + m) &&
-                                      mi_abs(pj.x - o0.x, L) < hw && mi_abs(pj.y - o0.y, L) < hw &&
-                                      mi_abs(pj.z - o0.z, L) < hw;
-                    if (take) {
-#pragma unroll
-                        for (int a = 0; a < M; ++a)
-                            if (a < m && ((nr >> a) & 1u))
-                                acc += pair_du<CUT>(sep(pn[a], pj, L), sep(po[a], pj, L), *pr[a], bx, T, ep);
-                    }
-                }
+            if (pend_t < 0) {
+                pend_t = t;
+                pend_nr = nr;
+            } else {
+                acc = cell_pairs<M, CUT>(acc, pn, po, m, a0, hw, o0, pend_t, pend_nr, t, nr, slice, blk, ci, k0x, nx,
+                                         k0y, ny, k0z, ncell, bx, T, ep, lane);
+                pend_t = -1;
             }
         }
     }
+    if (CELLS && pend_t >= 0)
+        acc = cell_pairs<M, CUT>(acc, pn, po, m, a0, hw, o0, pend_t, pend_nr, -1, 0u, slice, blk, ci, k0x, nx, k0y,
+                                 ny, k0z, ncell, bx, T, ep, lane);
     // escapees of the types answered by cell queries (their LJ rows were in the full scans)
     if (CELLS && cell_types)
         for (int e = lane; e < ci.n_esc; e += 32) {
