@@ -337,6 +337,29 @@ def test_mc_replay_lj_cutoff_small_water(batch):
     assert abs((U1 - U0) - stats[0][3]) <= 1e-4 * abs(U0) + 1.0
 
 
+def test_mc_replay_mixed_cutoff_batch_with_ep():
+    """One handle mixing boxes with and without the LJ cutoff (the cut instantiation reads each
+    box's setting) and an empirical potential on a cut box: replay parity of every box."""
+    a = synth.water_box(400, seed=24, L_A=23.0)
+    a.r_lj = 6.5
+    b = synth.silica_box(500, seed=25)
+    c = synth.silica_box(700, seed=26)
+    c.r_lj = 5.0
+    systems = [a, b, c]
+    rng = np.random.default_rng(27)
+    ep = (rng.normal(size=(3, c.n_bins)) * 0.3).astype(np.float32)
+    box = epsr.Box(systems)
+    box.epsr_box_set_ep(2, ep)
+    stats, log = run_logged(box, 1500, seed=28)
+    xyz = box.epsr_box_get_coords()
+    for k, s in enumerate(systems):
+        _, a0 = box.epsr_box_offsets(k)
+        ob, checked, _, flips = replay(s, s.xyz, log[k], 28, box_index=k,
+                                       ep=ep.astype(np.float64) if k == 2 else None)
+        assert flips <= 2
+        assert np.array_equal(xyz[a0:a0 + s.n_atoms], ob.xyz), k
+
+
 def test_mc_replay_global_memory_slices():
     """Slices too large for shared memory (8 CTAs for 99,999 atoms) run the global-memory
     variant of the sweep: same bit-exact trial coordinates and final state."""
