@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -269,6 +270,10 @@ static void fill_boxdev(const epsr_box_desc &d, const int *type, BoxDev &b)
     b.volume = LA * LA * LA;
     b.dr_A = (double)d.bin_p / (double)d.bin_q;
     b.inv_s2 = (float)std::ldexp(1.0, -2 * d.scale_log2);
+    b.sc_rcp = UINT64_MAX / (uint64_t)d.L_fx;
+    const double unit = (double)d.L_fx * 0x1p-32;                  // grid units per 2^32-grid unit
+    b.sc_s2 = (float)(unit * unit * std::ldexp(1.0, -2 * d.scale_log2));
+    b.sc_k2 = (float)(1.0 / (unit * unit));
     b.inv_dr_fx = (float)((double)d.bin_q / ((double)d.bin_p * S));
     for (long long i = 0; i < d.n_atoms; ++i) b.count[type[i]]++;
     const double ke = coulomb_k();
@@ -343,7 +348,7 @@ static void plan_mc_groups(epsr_box *h)
 
 // Shared-memory layout of the sweep for the current CTA split: thresholds, EP table, cell
 // index [types][513] (uint32), correction items, and, when they fit, the partner slice (int4 per
-// slot) and the home cell of every slot (uint16); otherwise the slices and home cells live in
+// slot, and its copy on the 2^32-periodic grid) and the home cell of every slot (uint16); otherwise the slices and home cells live in
 // global memory and a chunk of partners is staged.
 struct McLayout {
     int slice_cap = 0, types_cap = 1;
@@ -358,7 +363,7 @@ static int mc_layout(const epsr_box *h, McLayout *L)
     const size_t tables = (size_t)h->tbl_cap * sizeof(long long) + (size_t)h->ep_cap * sizeof(float) +
                           (size_t)L->types_cap * (kMcCells + 1) * sizeof(unsigned) +
                           (size_t)kMcBatchMax * kMcBatchMax * sizeof(float) + (size_t)kMcCorrItems * sizeof(float);
-    const size_t per_slot = sizeof(int4) + sizeof(unsigned short);
+    const size_t per_slot = 2 * sizeof(int4) + sizeof(unsigned short);   // slot, its 2^32-grid copy, home cell
     L->smem = (((size_t)L->slice_cap * per_slot + tables) + 15) & ~(size_t)15;
     L->gslice = L->smem > kMcMaxDynSmem;
     if (L->gslice) {

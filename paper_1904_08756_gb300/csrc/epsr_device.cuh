@@ -65,6 +65,9 @@ struct BoxDev {
     int32_t gc_n;         // cell-list histogram: cells per side (>= 3, each at least the
                           // histogram range wide), or 0 when the box is too small for it
     int32_t gc0;          // first key of this box in the cell-list sort
+    uint64_t sc_rcp;      // floor((2^64 - 1) / L): grid coordinate -> 2^32-periodic coordinate
+    float sc_s2;          // A^2 per squared unit of the 2^32-periodic grid, (L / 2^32)^2 inv_s2
+    float sc_k2;          // squared units of the 2^32-periodic grid per grid unit^2, (2^32 / L)^2
     int32_t type_start[kMaxTypes];  // first type-major sorted position of each type (box-local)
     int64_t count[kMaxTypes];   // atoms per type
     PairRow row[kMaxTypes * kMaxTypes];
@@ -98,6 +101,17 @@ __device__ __forceinline__ Sep sep(int4 a, int4 b, int L)
     s.y = mi_abs(a.y - b.y, L);
     s.z = mi_abs(a.z - b.z, L);
     return s;
+}
+
+// floor(x 2^32 / L) for 0 <= x < L: the coordinate on the 2^32-periodic grid, on which the
+// 32-bit difference of two coordinates wraps to the minimum image by itself. The product with
+// rcp = floor((2^64 - 1) / L) is that quotient or one less; one exact test corrects it.
+__device__ __forceinline__ unsigned scale32(int x, int L, uint64_t rcp)
+{
+    const uint64_t n = (uint64_t)(unsigned)x << 32;
+    uint64_t q = __umul64hi(n, rcp);
+    if ((q + 1) * (uint64_t)(unsigned)L <= n) ++q;
+    return (unsigned)q;
 }
 
 // Exact squared distance (grid units^2); 64-bit products, used only off the fast path.

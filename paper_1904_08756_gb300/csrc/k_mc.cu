@@ -125,6 +125,9 @@ struct McShared {
     int a0[kBatchMax];
     int spos[kBatchMax][kMaxMolAtoms];   // type-major sorted position of each moved atom
     int hw[kBatchMax];                   // half width of the near cube around old atom 0
+    // first three atoms of each move on the 2^32-periodic grid, new and old: [move][atom][axis]
+    unsigned scn[kBatchMax][3][3];
+    unsigned sco[kBatchMax][3][3];
     // this CTA's partners: per type t, sorted positions [rs[t], rs[t] + rl[t]) held at
     // slice slots [blk[t], blk[t + 1])
     int rs[kMaxTypes];
@@ -317,6 +320,108 @@ __device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const i
     return acc;
 }
 
+// Two FP32 values in one 64-bit register, operated on by the packed f32x2 instructions of
+// sm_100 and later: one instruction for the same operation on the two partners of a lane.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// The Lennard-Jones rows of lj_rows on the 2^32-periodic copy of the slice (sx: {X, Y, Z,
+// atom}, the moved atoms at qn/qo, [atom][axis]): a 32-bit difference wraps to the minimum
+// image, so a separation component costs one subtraction and one conversion, and the two
+// partners of a lane share every FP32 instruction (f32x2). A far pair (both squared distances
+// beyond the Coulomb cutoff and the EP table) has only the Lennard-Jones term, taken as the
+// direct difference u(r') - u(r): its rounding is a few ulp of |u| there, where |u| is small.
+// A pair that is not far takes pair_du on the exact grid slots (the cancellation-free form).
+// The moved atoms with a Lennard-Jones row take the slice one after the other (water and
+// single atoms have one such atom).
+template <int M, bool CUT>
+__device__ __forceinline__ float lj_rows_sc(float acc, const int4 *np, const int4 *op, const unsigned *qnp,
+                                            const unsigned *qop, unsigned lj, int a0, int m, const int4 *slice,
+                                            const uint4 *sx, int j0, int j1, int t, const BoxDev &bx,
+                                            const long long *T, const float *ep, int lane)
+{
+    const int L = bx.L;
+    const float far2 = fmaxf(bx.rc2_hi, bx.has_ep ? bx.tmax_hi : 0.f) * bx.sc_k2;
+    const uint64_t S2 = f2_pack(bx.sc_s2, bx.sc_s2);
+    for (int a = 0; a < m; ++a) {
+        if (!((lj >> a) & 1u)) continue;
+        const unsigned nx = qnp[3 * a], ny = qnp[3 * a + 1], nz = qnp[3 * a + 2];
+        const unsigned ox = qop[3 * a], oy = qop[3 * a + 1], oz = qop[3 * a + 2];
+        const PairRow &r = bx.row[np[a].w * kMaxTypes + t];
+        const uint64_t C12 = f2_pack(r.c12, r.c12), NC6 = f2_pack(-r.c6, -r.c6);
+        for (int j = j0 + lane; j < j1; j += 64) {
+            const bool in1 = j + 32 < j1;
+            const int jb = in1 ? j + 32 : j;
+            const uint4 p0 = sx[j];
+            const uint4 p1 = sx[jb];
+            const bool v0 = (unsigned)((int)p0.w - a0) >= (unsigned)m;
+            const bool v1 = in1 && (unsigned)((int)p1.w - a0) >= (unsigned)m;
+            const uint64_t XN = f2_pack((float)(int)(p0.x - nx), (float)(int)(p1.x - nx));
+            const uint64_t YN = f2_pack((float)(int)(p0.y - ny), (float)(int)(p1.y - ny));
+            const uint64_t ZN = f2_pack((float)(int)(p0.z - nz), (float)(int)(p1.z - nz));
+            const uint64_t XO = f2_pack((float)(int)(p0.x - ox), (float)(int)(p1.x - ox));
+            const uint64_t YO = f2_pack((float)(int)(p0.y - oy), (float)(int)(p1.y - oy));
+            const uint64_t ZO = f2_pack((float)(int)(p0.z - oz), (float)(int)(p1.z - oz));
+            const uint64_t G2N = f2_fma(XN, XN, f2_fma(YN, YN, f2_mul(ZN, ZN)));
+            const uint64_t G2O = f2_fma(XO, XO, f2_fma(YO, YO, f2_mul(ZO, ZO)));
+            float g2n0, g2n1, g2o0, g2o1;
+            f2_unpack(G2N, g2n0, g2n1);
+            f2_unpack(G2O, g2o0, g2o1);
+            float r2n0, r2n1, r2o0, r2o1;
+            f2_unpack(f2_mul(G2N, S2), r2n0, r2n1);
+            f2_unpack(f2_mul(G2O, S2), r2o0, r2o1);
+            const uint64_t AN = f2_pack(rsqrtf(r2n0), rsqrtf(r2n1)), AO = f2_pack(rsqrtf(r2o0), rsqrtf(r2o1));
+            const uint64_t IN = f2_mul(AN, AN), IO = f2_mul(AO, AO);
+            const uint64_t S6N = f2_mul(f2_mul(IN, IN), IN), S6O = f2_mul(f2_mul(IO, IO), IO);
+            const uint64_t D = f2_sub(f2_mul(f2_fma(C12, S6N, NC6), S6N), f2_mul(f2_fma(C12, S6O, NC6), S6O));
+            float d0, d1;
+            f2_unpack(D, d0, d1);
+            const bool s0 = v0 && !(g2n0 > far2 && g2o0 > far2);
+            const bool s1 = v1 && !(g2n1 > far2 && g2o1 > far2);
+            if (s0 || s1) {
+                const int4 pn = np[a], po = op[a];
+                if (s0) {
+                    const int4 pj = slice[j];
+                    d0 = pair_du<CUT>(sep(pn, pj, L), sep(po, pj, L), r, bx, T, ep);
+                }
+                if (s1) {
+                    const int4 pj = slice[jb];
+                    d1 = pair_du<CUT>(sep(pn, pj, L), sep(po, pj, L), r, bx, T, ep);
+                }
+            }
+            if (v0) acc += d0;
+            if (v1) acc += d1;
+        }
+    }
+    return acc;
+}
+
 // Near rows of one move against the partners of types ta (rows nra) and tb (rows nrb; tb < 0:
 // none) found by a cell query: the ncell cells of the CTA's 8^3 grid that meet the cube around
 // old atom 0 are taken one per lane, their runs for both types prefix-summed together (two
@@ -394,12 +499,14 @@ __device__ __forceinline__ float cell_pairs(float acc, const int4 (&pn)[M], cons
 // a row without LJ has Coulomb or empirical-potential terms only inside the near cube
 // around old atom 0 (half width hw), so its partners come from a cell query when the cube
 // meets at most 32 cells, else from the full scan with the cube test. M is a compile-time
-// bound so the atom loop unrolls into independent dependency chains.
-template <int M, bool CELLS, bool CUT, bool SKIP_LJ = false>
+// bound so the atom loop unrolls into independent dependency chains. SC: the slice has its
+// 2^32-periodic copy sx and the moved atoms theirs (qn, qo), used by the Lennard-Jones rows.
+template <int M, bool CELLS, bool CUT, bool SKIP_LJ = false, bool SC = false>
 __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int m, int a0, int hw,
                                              const int4 *slice, const int *blk, const CellIndex &ci,
                                              const BoxDev &bx, const long long *T, const float *ep,
-                                             int lane)
+                                             int lane, const uint4 *sx = nullptr, const unsigned *qn = nullptr,
+                                             const unsigned *qo = nullptr)
 {
     const int L = bx.L;
     const int4 o0 = op[0];
@@ -437,7 +544,11 @@ __device__ __forceinline__ float partner_sum(const int4 *np, const int4 *op, int
         const bool cells = nr && use_cells;
         const unsigned scan_nr = cells ? 0u : nr;
         if (lj && !scan_nr) {
-            acc = lj_rows<M, CUT>(acc, pn, po, lj, a0, m, slice, blk[t], blk[t + 1], t, bx, T, ep, lane);
+            if (SC)
+                acc = lj_rows_sc<M, CUT>(acc, np, op, qn, qo, lj, a0, m, slice, sx, blk[t], blk[t + 1], t, bx, T, ep,
+                                         lane);
+            else
+                acc = lj_rows<M, CUT>(acc, pn, po, lj, a0, m, slice, blk[t], blk[t + 1], t, bx, T, ep, lane);
         } else if (lj | scan_nr) {
             const int jb = blk[t + 1];
 #pragma unroll 2
@@ -591,8 +702,10 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
     __syncthreads();
 
     // shared memory: partner slice {x, y, z, type | atom << 3}, thresholds, empirical potential
+    // (shared-memory slices: the slice, then its 2^32-periodic copy {X, Y, Z, atom})
     int4 *slice = GSLICE ? A.slice_g + (size_t)cta * A.slice_cap : reinterpret_cast<int4 *>(dyn);
-    long long *T = GSLICE ? reinterpret_cast<long long *>(dyn) : reinterpret_cast<long long *>(slice + A.slice_cap);
+    uint4 *sx = GSLICE ? nullptr : reinterpret_cast<uint4 *>(slice + A.slice_cap);
+    long long *T = GSLICE ? reinterpret_cast<long long *>(dyn) : reinterpret_cast<long long *>(sx + A.slice_cap);
     float *ep = reinterpret_cast<float *>(T + A.tbl_cap);
     for (int t = 0; t < nt; ++t)
         for (int i = tid; i < sh.rl[t]; i += kMcThreads) {
@@ -600,6 +713,9 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             int4 c = A.coords[bx.atom0 + atom];
             c.w = c.w | (atom << 3);
             slice[sh.blk[t] + i] = c;
+            if (!GSLICE)
+                sx[sh.blk[t] + i] = make_uint4(scale32(c.x, L, bx.sc_rcp), scale32(c.y, L, bx.sc_rcp),
+                                               scale32(c.z, L, bx.sc_rcp), (unsigned)atom);
         }
     for (int k = tid; k <= bx.n_bins; k += kMcThreads) T[k] = A.thresholds[bx.tbl_off + k];
     if (bx.has_ep)
@@ -764,6 +880,10 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 int *dst = reinterpret_cast<int *>(&sh.newp[par][k][kk]);
                 dst[a] = coord;
                 if (a == 0) dst[3] = op[kk].w;
+                if (!GSLICE && kk < 3) {
+                    sh.scn[k][kk][a] = scale32(coord, L, bx.sc_rcp);
+                    sh.sco[k][kk][a] = scale32(reinterpret_cast<const int *>(op)[4 * kk + a], L, bx.sc_rcp);
+                }
             }
             __syncwarp();
             if (act && sl == 0) {
@@ -909,16 +1029,21 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             ci.n_esc = min(sh.n_esc, A.esc_cap);
             ci.margin = A.cell_margin;
             ci.on = sh.cells_on != 0;
+            const unsigned *qn = &sh.scn[k][0][0], *qo = &sh.sco[k][0][0];
             if (m == 1)
-                acc = ci.on ? partner_sum<1, true, CUT>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
-                                                   slice, sh.blk, ci, bx, T, ep, lane)
-                            : partner_sum<1, false, CUT>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k], sh.hw[k],
-                                                    slice, sh.blk, ci, bx, T, ep, lane);
+                acc = ci.on ? partner_sum<1, true, CUT, false, !GSLICE>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k],
+                                                                      sh.hw[k], slice, sh.blk, ci, bx, T, ep, lane,
+                                                                      sx, qn, qo)
+                            : partner_sum<1, false, CUT, false, !GSLICE>(sh.newp[par][k], sh.oldp[k], 1, sh.a0[k],
+                                                                       sh.hw[k], slice, sh.blk, ci, bx, T, ep, lane,
+                                                                       sx, qn, qo);
             else if (m <= 3)
-                acc = ci.on ? partner_sum<3, true, CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
-                                                   slice, sh.blk, ci, bx, T, ep, lane)
-                            : partner_sum<3, false, CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
-                                                    slice, sh.blk, ci, bx, T, ep, lane);
+                acc = ci.on ? partner_sum<3, true, CUT, false, !GSLICE>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k],
+                                                                      sh.hw[k], slice, sh.blk, ci, bx, T, ep, lane,
+                                                                      sx, qn, qo)
+                            : partner_sum<3, false, CUT, false, !GSLICE>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k],
+                                                                       sh.hw[k], slice, sh.blk, ci, bx, T, ep, lane,
+                                                                       sx, qn, qo);
             else
                 acc = partner_sum_any<CUT>(sh.newp[par][k], sh.oldp[k], m, sh.a0[k], sh.hw[k],
                                       slice, sh.blk, bx, T, ep, lane);
@@ -1123,6 +1248,9 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     if (esc) w |= kEscFlag;
                 }
                 slice[slot] = make_int4(p.x, p.y, p.z, w);
+                if (!GSLICE)
+                    sx[slot] = make_uint4(scale32(p.x, L, bx.sc_rcp), scale32(p.y, L, bx.sc_rcp),
+                                          scale32(p.z, L, bx.sc_rcp), (unsigned)ja);
             }
             if (rank == 0) A.coords[bx.atom0 + ja] = p;
         }
