@@ -42,7 +42,6 @@ static_assert(kMcCorrPerCta == kBatchMax * (kBatchMax - 1) / 2 && kMcSlotStride 
               "barrier slot layout");
 static_assert(kMcThreads == 8 * kBatchMax, "gather: 8 threads per move");
 constexpr int kGatherLoads = 20;                // partials per gather thread in flight (CTA groups up to 160)
-constexpr int kCorrLoads = (kMcCorrPerCta + kMcThreads - 1) / kMcThreads;   // corrections per thread
 static_assert(kPerWarp == 4 && kBatchMax == 64, "phase A / F: two moves per lane of warp 0; phase B: pairs of moves per warp");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
@@ -797,18 +796,30 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         const int nb = min(kmax, sh.nb_min);
         if (tid == 0) sh.nb[par] = nb;
         // ---- B. current and trial coordinates of each moved molecule (integer arithmetic) ----
-        // Current coordinates of a warp's two molecules, loaded together: from the previous
-        // batch's accepted move of the molecule if there is one (its global update may not be
-        // visible yet), else from the global coordinates.
+        // Current coordinates of a warp's four molecules: from the previous batch's accepted move
+        // of the molecule if there is one (its global update may not be visible yet), else from
+        // the global coordinates. The global loads of all four go out first (one round trip;
+        // a value that a pending move replaces is loaded and dropped).
         {
-            int4 oc[kPerWarp];
-            int sp[kPerWarp];
+            int4 gc[kPerWarp];
+            int gp[kPerWarp];
             const int q = par ^ 1;
 #pragma unroll
             for (int h = 0; h < kPerWarp; ++h) {
                 const int k = warp + h * kMcWarps;
-                oc[h] = make_int4(0, 0, 0, 0);
-                sp[h] = 0;
+                gc[h] = make_int4(0, 0, 0, 0);
+                gp[h] = 0;
+                if (k < nb) {
+                    const MoveRec &mr = sh.mv[t0 + k - mv_base];
+                    if (lane < mr.m) {
+                        gc[h] = __ldcg(&A.coords[bx.atom0 + mr.a0 + lane]);
+                        gp[h] = A.pos_of[bx.atom0 + mr.a0 + lane];
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < kPerWarp; ++h) {
+                const int k = warp + h * kMcWarps;
                 if (k < nb) {
                     const MoveRec &mr = sh.mv[t0 + k - mv_base];
                     const int mol = sh.mol[par][k];
@@ -818,17 +829,9 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                     // molecules of a batch are distinct: at most one hit
                     const int pidx = h1 ? 63 - __clz(h1) : h0 ? 31 - __clz(h0) : -1;
                     if (lane < mr.m) {
-                        oc[h] = pidx >= 0 ? sh.newp[q][pidx][lane] : __ldcg(&A.coords[bx.atom0 + mr.a0 + lane]);
-                        sp[h] = A.pos_of[bx.atom0 + mr.a0 + lane] - (int)bx.atom0;
+                        sh.oldp[k][lane] = pidx >= 0 ? sh.newp[q][pidx][lane] : gc[h];
+                        sh.spos[k][lane] = gp[h] - (int)bx.atom0;
                     }
-                }
-            }
-#pragma unroll
-            for (int h = 0; h < kPerWarp; ++h) {
-                const int k = warp + h * kMcWarps;
-                if (k < nb && lane < sh.mv[t0 + k - mv_base].m) {
-                    sh.oldp[k][lane] = oc[h];
-                    sh.spos[k][lane] = sp[h];
                 }
             }
             __syncwarp();
@@ -1059,6 +1062,12 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
         // barrier orders the other lanes' writes before the release, which is cumulative; the
         // CTA barrier after the poll orders every thread's reads after the acquire).
         ++seq;
+        const int gk = tid >> 3, gsub = tid & 7;     // gather group: move gk, member gsub
+        const bool gin = gk < nb;
+        float cv[8];                                  // corrections (j, gk), j = gsub + 8 i < gk
+        float gv = 0.f, gw = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cv[i] = 0.f;
         if (G > 1) {
             float *ps = A.slots + (size_t)(seq & 1u) * A.grid * kMcSlotStride;
             float *cs = ps + (size_t)kBatchMax * A.grid + (size_t)bx.cta0 * kMcCorrPerCta;
@@ -1091,91 +1100,79 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             }
             __syncthreads();
             if (sh.abort_flag) return;
-            {
-                // 8 threads per move, each summing every 8th CTA's partial, then a fixed
-                // shuffle tree: the order of the FP32 sum is the same in every run
-                // (the loads of a thread are all issued before the first add: one L2 round trip)
-                const int k = tid >> 3, sub = tid & 7;
-                float v = 0.f;
-                if (k < nb) {
-                    const float *pk = ps + (size_t)k * A.grid + bx.cta0;
-                    float pv[kGatherLoads];
+            // 8 threads per move k: every 8th CTA's partial and every 8th correction (j, k),
+            // j < k, all loads in flight at once (one L2 round trip)
+            if (gin) {
+                const float *pk = ps + (size_t)gk * A.grid + bx.cta0;
+                const float *ck = cs + gk * (gk - 1) / 2;
+                float pv[kGatherLoads];
 #pragma unroll
-                    for (int i = 0; i < kGatherLoads; ++i) {
-                        const int r = sub + 8 * i;
-                        pv[i] = r < G ? __ldcg(&pk[r]) : 0.f;
-                    }
-#pragma unroll
-                    for (int i = 0; i < kGatherLoads; ++i) v += pv[i];
-                    for (int r = sub + 8 * kGatherLoads; r < G; r += 8) v += __ldcg(&pk[r]);
+                for (int i = 0; i < kGatherLoads; ++i) {
+                    const int r = gsub + 8 * i;
+                    pv[i] = r < G ? __ldcg(&pk[r]) : 0.f;
                 }
 #pragma unroll
-                for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (sub == 0 && k < nb) sh.base[k] = v;
+                for (int i = 0; i < 8; ++i) {
+                    const int j = gsub + 8 * i;
+                    cv[i] = j < gk ? __ldcg(&ck[j]) : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < kGatherLoads; ++i) gv += pv[i];
+                for (int r = gsub + 8 * kGatherLoads; r < G; r += 8) gv += __ldcg(&pk[r]);
             }
-            {
-                float cv[kCorrLoads];
+        } else if (gin) {
+            gv = gsub == 0 ? sh.part[gk] : 0.f;
 #pragma unroll
-                for (int i = 0; i < kCorrLoads; ++i) {
-                    const int pq = tid + i * kMcThreads;
-                    cv[i] = pq < npq ? __ldcg(&cs[pq]) : 0.f;
-                }
-#pragma unroll
-                for (int i = 0; i < kCorrLoads; ++i) {
-                    const int pq = tid + i * kMcThreads;
-                    if (pq < npq) {
-                        const int k = pair_hi(pq);
-                        corr[pq - k * (k - 1) / 2][k] = cv[i];
-                    }
-                }
-            }
-        } else {
-            for (int k = tid; k < nb; k += kMcThreads) sh.base[k] = sh.part[k];
-            for (int pq = tid; pq < npq; pq += kMcThreads) {
-                const int k = pair_hi(pq);
-                corr[pq - k * (k - 1) / 2][k] = corr_sum(corr_part, pq, mm, fine);
+            for (int i = 0; i < 8; ++i) {
+                const int j = gsub + 8 * i;
+                cv[i] = j < gk ? corr_sum(corr_part, gk * (gk - 1) / 2 + j, mm, fine) : 0.f;
             }
         }
-        __syncthreads();
-        // ---- F. Metropolis decisions of the batch, in order (warp 0: lane l holds moves l
-        // and l + 32); move j's dU includes the corrections of every earlier accepted move.
-        // Fast path: when no move's decision can change with any subset of the earlier
-        // corrections (|dU - threshold| beyond the sum of their magnitudes plus the FP32
-        // rounding of that many additions), every decision is taken at once and each dU is
-        // summed in the chain's order; otherwise the decisions run one after the other.
-        if (warp == 0) {
-            const bool in0 = lane < nb, in1 = lane + 32 < nb;
-            float d0 = in0 ? sh.base[lane] + sh.intra[lane] : 0.f;
-            float d1 = in1 ? sh.base[lane + 32] + sh.intra[lane + 32] : 0.f;
-            const float thr0 = in0 ? sh.thr[lane] : 0.f, thr1 = in1 ? sh.thr[lane + 32] : 0.f;
-            int acc0 = 0, acc1 = 0;
-            float s0 = 0.f, s1 = 0.f, s0b = 0.f, s1b = 0.f;   // two accumulators each: shorter chains
+        // the group's sums in a fixed shuffle tree (the same order in every run): the move's
+        // partial dU and the magnitude sum of its corrections
 #pragma unroll
-            for (int j = 0; j < kBatchMax - 1; j += 2) {
-                const float c0 = corr[j][lane], c1 = corr[j][lane + 32];
-                const float e0 = corr[j + 1][lane], e1 = corr[j + 1][lane + 32];
-                if (j < lane) s0 += fabsf(c0);
-                if (j < lane + 32) s1 += fabsf(c1);
-                if (j + 1 < lane) s0b += fabsf(e0);
-                if (j + 1 < lane + 32) s1b += fabsf(e1);
-            }
-            s0 += s0b;
-            s1 += s1b;
-            const float w0 = s0 + (fabsf(d0) + s0) * 0x1p-16f, w1 = s1 + (fabsf(d1) + s1) * 0x1p-16f;
-            const bool sure0 = !in0 || metropolis(d0 + w0, thr0) || !metropolis(d0 - w0, thr0);
-            const bool sure1 = !in1 || metropolis(d1 + w1, thr1) || !metropolis(d1 - w1, thr1);
-            if (__all_sync(0xffffffffu, sure0 && sure1)) {
-                acc0 = in0 && metropolis(d0, thr0);
-                acc1 = in1 && metropolis(d1, thr1);
-                const unsigned a0 = __ballot_sync(0xffffffffu, acc0), a1 = __ballot_sync(0xffffffffu, acc1);
+        for (int i = 0; i < 8; ++i) {
+            const int j = gsub + 8 * i;
+            if (gin && j < gk) corr[j][gk] = cv[i];
+            gw += fabsf(cv[i]);
+        }
 #pragma unroll
-                for (int j = 0; j < kBatchMax - 1; ++j) {
-                    const float c0 = corr[j][lane], c1 = corr[j][lane + 32];
-                    const bool aj = j < 32 ? (a0 >> j) & 1u : (a1 >> (j - 32)) & 1u;
-                    if (aj && j < lane) d0 += c0;
-                    if (aj && j < lane + 32) d1 += c1;
+        for (int o = 4; o > 0; o >>= 1) {
+            gv += __shfl_xor_sync(0xffffffffu, gv, o);
+            gw += __shfl_xor_sync(0xffffffffu, gw, o);
+        }
+        // ---- F. Metropolis decisions of the batch, in order: move k's dU includes the
+        // corrections of every earlier accepted move. Fast path: when no move's decision can
+        // change with any subset of its earlier corrections (|dU - threshold| beyond the sum of
+        // their magnitudes plus the FP32 rounding of that many additions), every group decides
+        // its move at once and then adds its accepted corrections (fixed tree order); otherwise
+        // warp 0 decides one move after the other (lane l holds moves l and l + 32) and adds
+        // the corrections in the chain's order. Both give the same decisions.
+        {
+            const float d = gin ? gv + sh.intra[gk] : 0.f;
+            const float thr = gin ? sh.thr[gk] : 0.f;
+            const float wv = gw + (fabsf(d) + gw) * 0x1p-16f;
+            const bool sure = !gin || metropolis(d + wv, thr) || !metropolis(d - wv, thr);
+            if (gin && gsub == 0) sh.base[gk] = gv;
+            if (__syncthreads_and(sure)) {
+                const bool acc = gin && metropolis(d, thr);
+                if (gin && gsub == 0) sh.acc[par][gk] = acc;
+                __syncthreads();
+                float c = 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int j = gsub + 8 * i;
+                    if (j < gk && sh.acc[par][j]) c += cv[i];
                 }
-            } else {
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                if (gin && gsub == 0) sh.dU[gk] = d + c;
+            } else if (warp == 0) {
+                const bool in0 = lane < nb, in1 = lane + 32 < nb;
+                float d0 = in0 ? sh.base[lane] + sh.intra[lane] : 0.f;
+                float d1 = in1 ? sh.base[lane + 32] + sh.intra[lane + 32] : 0.f;
+                const float thr0 = in0 ? sh.thr[lane] : 0.f, thr1 = in1 ? sh.thr[lane + 32] : 0.f;
+                int acc0 = 0, acc1 = 0;
 #pragma unroll 8
                 for (int j = 0; j < 32; ++j) {
                     if (j < nb) {
@@ -1197,31 +1194,33 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                         if (aj && lane + 32 > j) d1 += c1;
                     }
                 }
-            }
-            if (in0) {
-                sh.dU[lane] = d0;
-                sh.acc[par][lane] = acc0;
-            }
-            if (in1) {
-                sh.dU[lane + 32] = d1;
-                sh.acc[par][lane + 32] = acc1;
-            }
-            if (rank == 0) {
-                // counts now; the FP64 sum of accepted dU once per staged block of moves
-                const unsigned b_acc = __ballot_sync(0xffffffffu, in0 && acc0) ,
-                               b_acc1 = __ballot_sync(0xffffffffu, in1 && acc1);
-                const unsigned b_nf = __ballot_sync(0xffffffffu, in0 && !isfinite(d0)),
-                               b_nf1 = __ballot_sync(0xffffffffu, in1 && !isfinite(d1));
-                if (in0) sh.acc_du[t0 - mv_base + lane] = acc0 ? d0 : 0.f;
-                if (in1) sh.acc_du[t0 - mv_base + lane + 32] = acc1 ? d1 : 0.f;
-                if (lane == 0) {
-                    sh.st_att += nb;
-                    sh.st_acc += __popc(b_acc) + __popc(b_acc1);
-                    sh.st_nonfinite += __popc(b_nf) + __popc(b_nf1);
+                if (in0) {
+                    sh.dU[lane] = d0;
+                    sh.acc[par][lane] = acc0;
+                }
+                if (in1) {
+                    sh.dU[lane + 32] = d1;
+                    sh.acc[par][lane + 32] = acc1;
                 }
             }
         }
         __syncthreads();
+        if (rank == 0 && warp == 0) {
+            // counts now; the FP64 sum of accepted dU once per staged block of moves
+            const bool in0 = lane < nb, in1 = lane + 32 < nb;
+            const bool acc0 = in0 && sh.acc[par][lane], acc1 = in1 && sh.acc[par][lane + 32];
+            const float d0 = in0 ? sh.dU[lane] : 0.f, d1 = in1 ? sh.dU[lane + 32] : 0.f;
+            const unsigned b_acc = __ballot_sync(0xffffffffu, acc0), b_acc1 = __ballot_sync(0xffffffffu, acc1);
+            const unsigned b_nf = __ballot_sync(0xffffffffu, in0 && !isfinite(d0)),
+                           b_nf1 = __ballot_sync(0xffffffffu, in1 && !isfinite(d1));
+            if (in0) sh.acc_du[t0 - mv_base + lane] = acc0 ? d0 : 0.f;
+            if (in1) sh.acc_du[t0 - mv_base + lane + 32] = acc1 ? d1 : 0.f;
+            if (lane == 0) {
+                sh.st_att += nb;
+                sh.st_acc += __popc(b_acc) + __popc(b_acc1);
+                sh.st_nonfinite += __popc(b_nf) + __popc(b_nf1);
+            }
+        }
         // ---- G. apply accepted moves: shared slice, global coordinates, log ------------------
         for (int it = tid; it < nb * kMaxMolAtoms; it += kMcThreads) {
             const int k = it / kMaxMolAtoms, a = it % kMaxMolAtoms;
