@@ -350,15 +350,49 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
     return d;
 }
 
+// Lennard-Jones change of two far partners p and q (one f32x2 lane pair) against a moved
+// atom at n (new) and o (old) on the 2^32-periodic grid: the direct difference u(r') - u(r).
+// Also returns both squared distances of each partner (2^32-grid units).
+struct FarLJ {
+    float d0, d1, g2n0, g2n1, g2o0, g2o1;
+};
+__device__ __forceinline__ FarLJ far_lj2(uint4 p, uint4 q, unsigned nx, unsigned ny, unsigned nz, unsigned ox,
+                                        unsigned oy, unsigned oz, uint64_t S2, uint64_t C12, uint64_t NC6)
+{
+    const uint64_t XN = f2_pack((float)(int)(p.x - nx), (float)(int)(q.x - nx));
+    const uint64_t YN = f2_pack((float)(int)(p.y - ny), (float)(int)(q.y - ny));
+    const uint64_t ZN = f2_pack((float)(int)(p.z - nz), (float)(int)(q.z - nz));
+    const uint64_t XO = f2_pack((float)(int)(p.x - ox), (float)(int)(q.x - ox));
+    const uint64_t YO = f2_pack((float)(int)(p.y - oy), (float)(int)(q.y - oy));
+    const uint64_t ZO = f2_pack((float)(int)(p.z - oz), (float)(int)(q.z - oz));
+    const uint64_t G2N = f2_fma(XN, XN, f2_fma(YN, YN, f2_mul(ZN, ZN)));
+    const uint64_t G2O = f2_fma(XO, XO, f2_fma(YO, YO, f2_mul(ZO, ZO)));
+    FarLJ f;
+    f2_unpack(G2N, f.g2n0, f.g2n1);
+    f2_unpack(G2O, f.g2o0, f.g2o1);
+    float r2n0, r2n1, r2o0, r2o1;
+    f2_unpack(f2_mul(G2N, S2), r2n0, r2n1);
+    f2_unpack(f2_mul(G2O, S2), r2o0, r2o1);
+    const uint64_t AN = f2_pack(rsqrtf(r2n0), rsqrtf(r2n1)), AO = f2_pack(rsqrtf(r2o0), rsqrtf(r2o1));
+    const uint64_t IN = f2_mul(AN, AN), IO = f2_mul(AO, AO);
+    const uint64_t S6N = f2_mul(f2_mul(IN, IN), IN), S6O = f2_mul(f2_mul(IO, IO), IO);
+    const uint64_t D = f2_sub(f2_mul(f2_fma(C12, S6N, NC6), S6N), f2_mul(f2_fma(C12, S6O, NC6), S6O));
+    f2_unpack(D, f.d0, f.d1);
+    return f;
+}
+
 // The Lennard-Jones rows of lj_rows on the 2^32-periodic copy of the slice (sx: {X, Y, Z,
 // atom}, the moved atoms at qn/qo, [atom][axis]): a 32-bit difference wraps to the minimum
-// image, so a separation component costs one subtraction and one conversion, and the two
-// partners of a lane share every FP32 instruction (f32x2). A far pair (both squared distances
-// beyond the Coulomb cutoff and the EP table) has only the Lennard-Jones term, taken as the
-// direct difference u(r') - u(r): its rounding is a few ulp of |u| there, where |u| is small.
-// A pair that is not far takes pair_du on the exact grid slots (the cancellation-free form).
-// The moved atoms with a Lennard-Jones row take the slice one after the other (water and
-// single atoms have one such atom).
+// image, so a separation component costs one subtraction and one conversion, and two
+// partners share every FP32 instruction (f32x2). For single-atom moves a lane takes four
+// partners per step (two independent packed pairs: the scan is latency-bound at 16 warps per
+// SM), then two in the tail; for molecules (whose larger partner_sum the four-partner body
+// slowed) two per step throughout. A far pair (both squared distances beyond the Coulomb cutoff and the EP table) has
+// only the Lennard-Jones term, taken as the direct difference u(r') - u(r): its rounding is a
+// few ulp of |u| there, where |u| is small. A pair that is not far takes pair_du on the exact
+// grid slots (the cancellation-free form), one such partner of the lane after the other. The
+// moved atoms with a Lennard-Jones row take the slice one after the other (water and single
+// atoms have one such atom).
 template <int M, bool CUT>
 __device__ __forceinline__ float lj_rows_sc(float acc, const int4 *np, const int4 *op, const unsigned *qnp,
                                             const unsigned *qop, unsigned lj, int a0, int m, const int4 *slice,
@@ -374,35 +408,46 @@ __device__ __forceinline__ float lj_rows_sc(float acc, const int4 *np, const int
         const unsigned ox = qop[3 * a], oy = qop[3 * a + 1], oz = qop[3 * a + 2];
         const PairRow &r = bx.row[np[a].w * kMaxTypes + t];
         const uint64_t C12 = f2_pack(r.c12, r.c12), NC6 = f2_pack(-r.c6, -r.c6);
-        for (int j = j0 + lane; j < j1; j += 64) {
+        int j = j0 + lane;
+        for (; M == 1 && j + 96 < j1; j += 128) {        // four partners: j, j + 32, j + 64, j + 96
+            const uint4 p0 = sx[j], p1 = sx[j + 32], p2 = sx[j + 64], p3 = sx[j + 96];
+            const FarLJ f = far_lj2(p0, p1, nx, ny, nz, ox, oy, oz, S2, C12, NC6);
+            const FarLJ g = far_lj2(p2, p3, nx, ny, nz, ox, oy, oz, S2, C12, NC6);
+            float d[4] = {f.d0, f.d1, g.d0, g.d1};
+            const bool v0 = (unsigned)((int)p0.w - a0) >= (unsigned)m, v1 = (unsigned)((int)p1.w - a0) >= (unsigned)m;
+            const bool v2 = (unsigned)((int)p2.w - a0) >= (unsigned)m, v3 = (unsigned)((int)p3.w - a0) >= (unsigned)m;
+            unsigned nm = (v0 && !(f.g2n0 > far2 && f.g2o0 > far2) ? 1u : 0u) |
+                          (v1 && !(f.g2n1 > far2 && f.g2o1 > far2) ? 2u : 0u) |
+                          (v2 && !(g.g2n0 > far2 && g.g2o0 > far2) ? 4u : 0u) |
+                          (v3 && !(g.g2n1 > far2 && g.g2o1 > far2) ? 8u : 0u);
+            if (nm) {                                    // per lane: the loop's trip count differs by lane
+                const int4 pn = np[a], po = op[a];
+                while (nm) {
+                    const int q = __ffs(nm) - 1;
+                    nm &= nm - 1u;
+                    const int4 pj = slice[j + 32 * q];
+                    const float v = pair_du<CUT>(sep(pn, pj, L), sep(po, pj, L), r, bx, T, ep);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (u == q) d[u] = v;
+                }
+            }
+            if (v0) acc += d[0];
+            if (v1) acc += d[1];
+            if (v2) acc += d[2];
+            if (v3) acc += d[3];
+        }
+        for (; j < j1; j += 64) {                        // tail: two partners, j and j + 32
             const bool in1 = j + 32 < j1;
             const int jb = in1 ? j + 32 : j;
             const uint4 p0 = sx[j];
             const uint4 p1 = sx[jb];
             const bool v0 = (unsigned)((int)p0.w - a0) >= (unsigned)m;
             const bool v1 = in1 && (unsigned)((int)p1.w - a0) >= (unsigned)m;
-            const uint64_t XN = f2_pack((float)(int)(p0.x - nx), (float)(int)(p1.x - nx));
-            const uint64_t YN = f2_pack((float)(int)(p0.y - ny), (float)(int)(p1.y - ny));
-            const uint64_t ZN = f2_pack((float)(int)(p0.z - nz), (float)(int)(p1.z - nz));
-            const uint64_t XO = f2_pack((float)(int)(p0.x - ox), (float)(int)(p1.x - ox));
-            const uint64_t YO = f2_pack((float)(int)(p0.y - oy), (float)(int)(p1.y - oy));
-            const uint64_t ZO = f2_pack((float)(int)(p0.z - oz), (float)(int)(p1.z - oz));
-            const uint64_t G2N = f2_fma(XN, XN, f2_fma(YN, YN, f2_mul(ZN, ZN)));
-            const uint64_t G2O = f2_fma(XO, XO, f2_fma(YO, YO, f2_mul(ZO, ZO)));
-            float g2n0, g2n1, g2o0, g2o1;
-            f2_unpack(G2N, g2n0, g2n1);
-            f2_unpack(G2O, g2o0, g2o1);
-            float r2n0, r2n1, r2o0, r2o1;
-            f2_unpack(f2_mul(G2N, S2), r2n0, r2n1);
-            f2_unpack(f2_mul(G2O, S2), r2o0, r2o1);
-            const uint64_t AN = f2_pack(rsqrtf(r2n0), rsqrtf(r2n1)), AO = f2_pack(rsqrtf(r2o0), rsqrtf(r2o1));
-            const uint64_t IN = f2_mul(AN, AN), IO = f2_mul(AO, AO);
-            const uint64_t S6N = f2_mul(f2_mul(IN, IN), IN), S6O = f2_mul(f2_mul(IO, IO), IO);
-            const uint64_t D = f2_sub(f2_mul(f2_fma(C12, S6N, NC6), S6N), f2_mul(f2_fma(C12, S6O, NC6), S6O));
-            float d0, d1;
-            f2_unpack(D, d0, d1);
-            const bool s0 = v0 && !(g2n0 > far2 && g2o0 > far2);
-            const bool s1 = v1 && !(g2n1 > far2 && g2o1 > far2);
+            const FarLJ f = far_lj2(p0, p1, nx, ny, nz, ox, oy, oz, S2, C12, NC6);
+            float d0 = f.d0, d1 = f.d1;
+            const bool s0 = v0 && !(f.g2n0 > far2 && f.g2o0 > far2);
+            const bool s1 = v1 && !(f.g2n1 > far2 && f.g2o1 > far2);
             if (s0 || s1) {
                 const int4 pn = np[a], po = op[a];
                 if (s0) {
