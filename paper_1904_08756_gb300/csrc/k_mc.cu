@@ -279,46 +279,6 @@ __device__ __noinline__ float pair_du_cold(Sep sn, Sep so, const PairRow &pr, co
     return pair_du<CUT>(sn, so, pr, bx, T, ep);
 }
 
-// Lennard-Jones rows (bit a of lj: atom a of the move) against partners [j0, j1) of type t,
-// added to acc in the order of a lane-strided scan. A lane takes two partners, j and j + 32,
-// per step. A pair whose squared distances both exceed far2 has no Coulomb and no EP term,
-// so its dU is the Lennard-Jones change alone, computed as straight-line code for both
-// partners at once; a pair that is not that far takes the full pair_du (same value).
-template <int M, bool CUT>
-__device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const int4 (&po)[M], unsigned lj, int a0,
-                                         int m, const int4 *part, int j0, int j1, int t, const BoxDev &bx,
-                                         const long long *T, const float *ep, int lane)
-{
-    const int L = bx.L;
-    const float far2 = fmaxf(bx.rc2_hi, bx.has_ep ? bx.tmax_hi : 0.f);
-    for (int j = j0 + lane; j < j1; j += 64) {
-        const bool in1 = j + 32 < j1;
-        const int4 p0 = part[j];
-        const int4 p1 = part[in1 ? j + 32 : j];
-        const int i0 = (p0.w & 0x7fffffff) >> 3, i1 = (p1.w & 0x7fffffff) >> 3;
-        const bool v0 = !(i0 >= a0 && i0 < a0 + m);
-        const bool v1 = in1 && !(i1 >= a0 && i1 < a0 + m);
-#pragma unroll
-        for (int a = 0; a < M; ++a) {
-            if (a >= m || !((lj >> a) & 1u)) continue;
-            const PairRow &r = bx.row[pn[a].w * kMaxTypes + t];
-            const Sep n0 = sep(pn[a], p0, L), o0 = sep(po[a], p0, L);
-            const Sep n1 = sep(pn[a], p1, L), o1 = sep(po[a], p1, L);
-            const DuCore c0 = du_core(n0, o0, bx.inv_s2), c1 = du_core(n1, o1, bx.inv_s2);
-            float d0 = lj_du(c0, r.c12, r.c6), d1 = lj_du(c1, r.c12, r.c6);
-            const bool s0 = v0 && !(c0.g2n > far2 && c0.g2o > far2);
-            const bool s1 = v1 && !(c1.g2n > far2 && c1.g2o > far2);
-            if (s0 || s1) {
-                if (s0) d0 = pair_du<CUT>(n0, o0, r, bx, T, ep);
-                if (s1) d1 = pair_du<CUT>(n1, o1, r, bx, T, ep);
-            }
-            if (v0) acc += d0;
-            if (v1) acc += d1;
-        }
-    }
-    return acc;
-}
-
 // Two FP32 values in one 64-bit register, operated on by the packed f32x2 instructions of
 // sm_100 and later: one instruction for the same operation on the two partners of a lane.
 __device__ __forceinline__ uint64_t f2_pack(float lo, float hi)
@@ -350,21 +310,16 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
     return d;
 }
 
-// Lennard-Jones change of two far partners p and q (one f32x2 lane pair) against a moved
-// atom at n (new) and o (old) on the 2^32-periodic grid: the direct difference u(r') - u(r).
-// Also returns both squared distances of each partner (2^32-grid units).
+// Lennard-Jones change of two far partners (one f32x2 lane pair) from their packed separation
+// components against a moved atom's new (XN, YN, ZN) and old (XO, YO, ZO) position, in units whose
+// square S2 converts to A^2: the direct difference u(r') - u(r), and both squared distances of
+// each partner in those units.
 struct FarLJ {
     float d0, d1, g2n0, g2n1, g2o0, g2o1;
 };
-__device__ __forceinline__ FarLJ far_lj2(uint4 p, uint4 q, unsigned nx, unsigned ny, unsigned nz, unsigned ox,
-                                        unsigned oy, unsigned oz, uint64_t S2, uint64_t C12, uint64_t NC6)
+__device__ __forceinline__ FarLJ far_lj2_xyz(uint64_t XN, uint64_t YN, uint64_t ZN, uint64_t XO, uint64_t YO,
+                                            uint64_t ZO, uint64_t S2, uint64_t C12, uint64_t NC6)
 {
-    const uint64_t XN = f2_pack((float)(int)(p.x - nx), (float)(int)(q.x - nx));
-    const uint64_t YN = f2_pack((float)(int)(p.y - ny), (float)(int)(q.y - ny));
-    const uint64_t ZN = f2_pack((float)(int)(p.z - nz), (float)(int)(q.z - nz));
-    const uint64_t XO = f2_pack((float)(int)(p.x - ox), (float)(int)(q.x - ox));
-    const uint64_t YO = f2_pack((float)(int)(p.y - oy), (float)(int)(q.y - oy));
-    const uint64_t ZO = f2_pack((float)(int)(p.z - oz), (float)(int)(q.z - oz));
     const uint64_t G2N = f2_fma(XN, XN, f2_fma(YN, YN, f2_mul(ZN, ZN)));
     const uint64_t G2O = f2_fma(XO, XO, f2_fma(YO, YO, f2_mul(ZO, ZO)));
     FarLJ f;
@@ -379,6 +334,63 @@ __device__ __forceinline__ FarLJ far_lj2(uint4 p, uint4 q, unsigned nx, unsigned
     const uint64_t D = f2_sub(f2_mul(f2_fma(C12, S6N, NC6), S6N), f2_mul(f2_fma(C12, S6O, NC6), S6O));
     f2_unpack(D, f.d0, f.d1);
     return f;
+}
+
+// The same for two partners p and q on the 2^32-periodic grid (signed 32-bit differences).
+__device__ __forceinline__ FarLJ far_lj2(uint4 p, uint4 q, unsigned nx, unsigned ny, unsigned nz, unsigned ox,
+                                        unsigned oy, unsigned oz, uint64_t S2, uint64_t C12, uint64_t NC6)
+{
+    return far_lj2_xyz(f2_pack((float)(int)(p.x - nx), (float)(int)(q.x - nx)),
+                       f2_pack((float)(int)(p.y - ny), (float)(int)(q.y - ny)),
+                       f2_pack((float)(int)(p.z - nz), (float)(int)(q.z - nz)),
+                       f2_pack((float)(int)(p.x - ox), (float)(int)(q.x - ox)),
+                       f2_pack((float)(int)(p.y - oy), (float)(int)(q.y - oy)),
+                       f2_pack((float)(int)(p.z - oz), (float)(int)(q.z - oz)), S2, C12, NC6);
+}
+
+// Lennard-Jones rows (bit a of lj: atom a of the move) against partners [j0, j1) of type t,
+// added to acc in the order of a lane-strided scan, on the grid coordinates (integer minimum
+// image). A lane takes two partners, j and j + 32, per step. A pair whose squared distances both
+// exceed far2 has no Coulomb and no EP term, so its dU is the Lennard-Jones change alone, the
+// direct difference computed for both partners at once in packed f32x2 arithmetic; a pair that
+// is not that far takes the full pair_du (the cancellation-free form).
+template <int M, bool CUT>
+__device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const int4 (&po)[M], unsigned lj, int a0,
+                                         int m, const int4 *part, int j0, int j1, int t, const BoxDev &bx,
+                                         const long long *T, const float *ep, int lane)
+{
+    const int L = bx.L;
+    const float far2 = fmaxf(bx.rc2_hi, bx.has_ep ? bx.tmax_hi : 0.f);
+    const uint64_t S2 = f2_pack(bx.inv_s2, bx.inv_s2);
+    for (int j = j0 + lane; j < j1; j += 64) {
+        const bool in1 = j + 32 < j1;
+        const int4 p0 = part[j];
+        const int4 p1 = part[in1 ? j + 32 : j];
+        const int i0 = (p0.w & 0x7fffffff) >> 3, i1 = (p1.w & 0x7fffffff) >> 3;
+        const bool v0 = !(i0 >= a0 && i0 < a0 + m);
+        const bool v1 = in1 && !(i1 >= a0 && i1 < a0 + m);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            if (a >= m || !((lj >> a) & 1u)) continue;
+            const PairRow &r = bx.row[pn[a].w * kMaxTypes + t];
+            const Sep n0 = sep(pn[a], p0, L), o0 = sep(po[a], p0, L);
+            const Sep n1 = sep(pn[a], p1, L), o1 = sep(po[a], p1, L);
+            const FarLJ f = far_lj2_xyz(f2_pack((float)n0.x, (float)n1.x), f2_pack((float)n0.y, (float)n1.y),
+                                        f2_pack((float)n0.z, (float)n1.z), f2_pack((float)o0.x, (float)o1.x),
+                                        f2_pack((float)o0.y, (float)o1.y), f2_pack((float)o0.z, (float)o1.z), S2,
+                                        f2_pack(r.c12, r.c12), f2_pack(-r.c6, -r.c6));
+            float d0 = f.d0, d1 = f.d1;
+            const bool s0 = v0 && !(f.g2n0 > far2 && f.g2o0 > far2);
+            const bool s1 = v1 && !(f.g2n1 > far2 && f.g2o1 > far2);
+            if (s0 || s1) {
+                if (s0) d0 = pair_du<CUT>(n0, o0, r, bx, T, ep);
+                if (s1) d1 = pair_du<CUT>(n1, o1, r, bx, T, ep);
+            }
+            if (v0) acc += d0;
+            if (v1) acc += d1;
+        }
+    }
+    return acc;
 }
 
 // The Lennard-Jones rows of lj_rows on the 2^32-periodic copy of the slice (sx: {X, Y, Z,
