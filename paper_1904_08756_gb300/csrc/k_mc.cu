@@ -42,7 +42,8 @@ static_assert(kMcCorrPerCta == kBatchMax * (kBatchMax - 1) / 2 && kMcSlotStride 
               "barrier slot layout");
 static_assert(kMcThreads == 8 * kBatchMax, "gather: 8 threads per move");
 constexpr int kGatherLoads = 20;                // partials per gather thread in flight (CTA groups up to 160)
-static_assert(kPerWarp == 4 && kBatchMax == 64, "phase A / F: two moves per lane of warp 0; phase B: pairs of moves per warp");
+static_assert(kPerWarp == 4 && kBatchMax == 64, "phase A / F: two moves per lane of warp 0; phase B: the four moves of a warp in 8-lane groups");
+static_assert(kMaxMolAtoms <= 8, "phase B: one lane per atom in 8-lane groups");
 
 // ---- 1. configuration-independent part of each move ----------------------------------------
 __global__ void mc_moves_kernel(const BoxDev *boxes, const int *mol_start, int n_boxes,
@@ -893,26 +894,21 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
             }
             __syncwarp();
         }
-        // Trial coordinates: with molecules of at most 5 atoms the moves of a warp run two at a
-        // time in its half-warps, otherwise one after the other with the whole warp.
-        int m_max = 0;
-#pragma unroll
-        for (int h = 0; h < kPerWarp; ++h)
-            if (warp + h * kMcWarps < nb) m_max = max(m_max, (int)sh.mv[t0 + warp + h * kMcWarps - mv_base].m);
-        const bool halves = m_max <= 5;
-        for (int rr = 0; rr < (halves ? kPerWarp / 2 : kPerWarp); ++rr) {
-            const int k = warp + (halves ? 2 * rr + (lane >> 4) : rr) * kMcWarps;
-            const int sl = halves ? lane & 15 : lane;
+        // Trial coordinates: the four moves of a warp at once, one per 8-lane group, one lane per
+        // atom of the molecule (all three axes in the lane).
+        {
+            const int k = warp + (lane >> 3) * kMcWarps;
+            const int kk = lane & 7;
             const bool act = k < nb;
             const MoveRec &mr = sh.mv[t0 + (act ? k : 0) - mv_base];
             const int a0 = mr.a0, m = act ? mr.m : 0;
-            if (sl < 3 * m) {
-                const int kk = sl / 3, a = sl - 3 * kk;
+            int4 np4 = make_int4(0, 0, 0, 0), op4 = make_int4(0, 0, 0, 0);
+            if (kk < m) {
                 const int4 *op = sh.oldp[k];
-                int coord;
+                op4 = op[kk];
+                int nx, ny, nz;
                 if (mr.kind == 1) {
-                    // minimum-image offsets from atom 0, summed over the molecule, and this atom's
-                    // own (per-axis scalars, so that the lane's axis a selects without an array)
+                    // minimum-image offsets from atom 0, summed over the molecule, and this atom's own
                     const int4 b0 = op[0];
                     long long sx = 0, sy = 0, sz = 0, ox = 0, oy = 0, oz = 0;
                     for (int i = 0; i < m; ++i) {
@@ -923,30 +919,40 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                         sx += dx; sy += dy; sz += dz;
                         if (i == kk) { ox = dx; oy = dy; oz = dz; }
                     }
-                    const int *Ra = mr.R + 3 * a;
-                    long long num = (a == 0 ? sx : a == 1 ? sy : sz) * 1073741824LL;
-                    num += (long long)Ra[0] * ((long long)m * ox - sx);
-                    num += (long long)Ra[1] * ((long long)m * oy - sy);
-                    num += (long long)Ra[2] * ((long long)m * oz - sz);
-                    // floor((num + m 2^29) / 2^30) fits in 32 bits; then floor division by m
-                    const int hi = (int)((num + (long long)m * 536870912LL) >> 30);
-                    const int base_a = reinterpret_cast<const int *>(op)[a];
-                    coord = wrap_coord((long long)base_a + floordiv32(hi, m) + mr.shift[a], L);
+                    const long long ux = (long long)m * ox - sx, uy = (long long)m * oy - sy,
+                                    uz = (long long)m * oz - sz;
+                    const int *R = mr.R;
+                    // per axis: s 2^30 + R (m o - s), then floor((. + m 2^29) / 2^30) (32 bits) and
+                    // floor division by m
+                    const long long numx = sx * 1073741824LL + (long long)R[0] * ux + (long long)R[1] * uy +
+                                           (long long)R[2] * uz;
+                    const long long numy = sy * 1073741824LL + (long long)R[3] * ux + (long long)R[4] * uy +
+                                           (long long)R[5] * uz;
+                    const long long numz = sz * 1073741824LL + (long long)R[6] * ux + (long long)R[7] * uy +
+                                           (long long)R[8] * uz;
+                    const long long half = (long long)m * 536870912LL;
+                    nx = wrap_coord((long long)b0.x + floordiv32((int)((numx + half) >> 30), m) + mr.shift[0], L);
+                    ny = wrap_coord((long long)b0.y + floordiv32((int)((numy + half) >> 30), m) + mr.shift[1], L);
+                    nz = wrap_coord((long long)b0.z + floordiv32((int)((numz + half) >> 30), m) + mr.shift[2], L);
                 } else {
-                    const int c_a = reinterpret_cast<const int *>(op)[4 * kk + a];
                     const bool moved = mr.kind != 2 || kk == mr.atom;
-                    coord = wrap_coord((long long)c_a + (moved ? mr.shift[a] : 0), L);
+                    nx = wrap_coord((long long)op4.x + (moved ? mr.shift[0] : 0), L);
+                    ny = wrap_coord((long long)op4.y + (moved ? mr.shift[1] : 0), L);
+                    nz = wrap_coord((long long)op4.z + (moved ? mr.shift[2] : 0), L);
                 }
-                int *dst = reinterpret_cast<int *>(&sh.newp[par][k][kk]);
-                dst[a] = coord;
-                if (a == 0) dst[3] = op[kk].w;
+                np4 = make_int4(nx, ny, nz, op4.w);
+                sh.newp[par][k][kk] = np4;
                 if (!GSLICE && kk < 3) {
-                    sh.scn[k][kk][a] = scale32(coord, L, bx.sc_rcp);
-                    sh.sco[k][kk][a] = scale32(reinterpret_cast<const int *>(op)[4 * kk + a], L, bx.sc_rcp);
+                    sh.scn[k][kk][0] = scale32(nx, L, bx.sc_rcp);
+                    sh.scn[k][kk][1] = scale32(ny, L, bx.sc_rcp);
+                    sh.scn[k][kk][2] = scale32(nz, L, bx.sc_rcp);
+                    sh.sco[k][kk][0] = scale32(op4.x, L, bx.sc_rcp);
+                    sh.sco[k][kk][1] = scale32(op4.y, L, bx.sc_rcp);
+                    sh.sco[k][kk][2] = scale32(op4.z, L, bx.sc_rcp);
                 }
             }
             __syncwarp();
-            if (act && sl == 0) {
+            if (act && kk == 0) {
                 // flexible molecules: change of the intra-molecular springs, written without
                 // cancellation: k[(r' - d)^2 - (r - d)^2] = k (r' - r)(r' + r - 2d), with
                 // r' - r = (r'^2 - r^2) / (r' + r) from the exact integer squared distances
@@ -970,18 +976,16 @@ __global__ void __launch_bounds__(kMcThreads, 1) mc_sweep_kernel(McArgs A)
                 sh.thr[k] = mr.thr;
                 sh.u_acc[k] = mr.u_acc;
             }
-            __syncwarp();
             // near cube: every old and new atom position lies within `reach` of old atom 0
             int reach = 0;
-            if (sl < 2 * m) {
-                const int4 p = sl < m ? sh.oldp[k][sl] : sh.newp[par][k][sl - m];
+            if (kk < m) {
                 const int4 o = sh.oldp[k][0];
-                reach = max(mi_abs(p.x - o.x, L), max(mi_abs(p.y - o.y, L), mi_abs(p.z - o.z, L)));
+                reach = max(max(mi_abs(op4.x - o.x, L), max(mi_abs(op4.y - o.y, L), mi_abs(op4.z - o.z, L))),
+                            max(mi_abs(np4.x - o.x, L), max(mi_abs(np4.y - o.y, L), mi_abs(np4.z - o.z, L))));
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                if (o < 16 || !halves) reach = max(reach, __shfl_xor_sync(0xffffffffu, reach, o));
-            if (act && sl == 0) sh.hw[k] = bx.near_fx + reach + 2;
+            for (int o = 4; o > 0; o >>= 1) reach = max(reach, __shfl_xor_sync(0xffffffffu, reach, o));
+            if (act && kk == 0) sh.hw[k] = bx.near_fx + reach + 2;
         }
         __syncthreads();
         // ---- E. pair-energy corrections between the batch's moved molecules -----------------
