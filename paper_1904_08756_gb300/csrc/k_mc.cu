@@ -400,12 +400,12 @@ __device__ __forceinline__ float lj_rows(float acc, const int4 (&pn)[M], const i
 // partners share every FP32 instruction (f32x2). For single-atom moves a lane takes four
 // partners per step (two independent packed pairs: the scan is latency-bound at 16 warps per
 // SM), then two in the tail; for molecules (whose larger partner_sum the four-partner body
-// slowed) two per step throughout. A far pair (both squared distances beyond the Coulomb cutoff and the EP table) has
-// only the Lennard-Jones term, taken as the direct difference u(r') - u(r): its rounding is a
-// few ulp of |u| there, where |u| is small. A pair that is not far takes pair_du on the exact
-// grid slots (the cancellation-free form), one such partner of the lane after the other. The
-// moved atoms with a Lennard-Jones row take the slice one after the other (water and single
-// atoms have one such atom).
+// slowed) two per step throughout. A far pair (both squared distances beyond the Coulomb
+// cutoff and the EP table) has only the Lennard-Jones term, taken as the direct difference
+// u(r') - u(r): its rounding is a few ulp of |u| there, where |u| is small. A pair that is not
+// far takes pair_du on the exact grid slots (the cancellation-free form), one such partner of
+// the lane after the other. The moved atoms with a Lennard-Jones row take the slice one after
+// the other (water and single atoms have one such atom).
 template <int M, bool CUT>
 __device__ __forceinline__ float lj_rows_sc(float acc, const int4 *np, const int4 *op, const unsigned *qnp,
                                             const unsigned *qop, unsigned lj, int a0, int m, const int4 *slice,
